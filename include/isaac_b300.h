@@ -1,0 +1,171 @@
+/*
+ * isaac_b300.h -- C ABI of the B300-native ISAAC volume ray caster.
+ *
+ * ISAAC (Matthes et al., 2016) renders simulation fields in situ: the
+ * application keeps its data where it is, describes each field as a "source"
+ * (Sec. 3.2: a scalar or vector of up to 4 components per regularly spaced
+ * cell, read through an accessor, optionally surrounded by guard cells), and
+ * calls one render function that ray casts every pixel front to back over all
+ * active sources (Sec. 3.2), each passed through its functor chain (Sec. 3.3)
+ * and a transfer function.
+ *
+ * Everything here is plain C: device pointers, host structs, sizes.  The
+ * library never allocates, frees or copies the caller's field data (Sec. 3.1
+ * "zero copy"); every call is ordered on the caller's CUDA stream and returns
+ * once the work is enqueued.  All entry points return ISAAC_OK (0) or a
+ * negative isaac_status; isaac_last_error() then describes the failure (per
+ * calling thread).  Invalid arguments are rejected on the host before any
+ * launch, so a rejected call touches no device memory.
+ */
+#ifndef ISAAC_B300_H
+#define ISAAC_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISAAC_ABI_VERSION 1
+#define ISAAC_MAX_SOURCES 8   /* sources described per call */
+#define ISAAC_MAX_ACTIVE 4    /* sources rendered per call (active_mask bits) */
+#define ISAAC_MAX_FUNCTORS 8  /* functors per chain */
+#define ISAAC_MAX_CLIP 6      /* clipping planes per call */
+
+typedef enum {
+    ISAAC_OK = 0,
+    ISAAC_EINVAL = -1,   /* malformed argument (sizes, dimensions, chain, NaN weight ...) */
+    ISAAC_EGUARD = -2,   /* a source's reachable cells leave its allocation */
+    ISAAC_ENOMEM = -3,   /* a caller-provided buffer or budget is too small */
+    ISAAC_ECUDA = -4,    /* a CUDA launch or runtime call failed */
+    ISAAC_ENOTSUP = -5   /* valid but outside what this build supports */
+} isaac_status;
+
+typedef enum { ISAAC_F32 = 0, ISAAC_BF16 = 1, ISAAC_F16 = 2, ISAAC_E4M3 = 3 } isaac_dtype;
+
+/* Functors of Sec. 3.3, Table 1, plus the user functor LOG (Sec. 3.3 allows
+ * application-defined functors).
+ *   ADD(v), MUL(v): componentwise with v; one argument is broadcast to every
+ *                   component (Sec. 3.3: add(1) adds (1,1,1)).
+ *   LENGTH, SUM:    reduce the vector to a scalar.
+ *   POW(v):         componentwise x^v; a non-positive base gives 0.
+ *   LOG:            componentwise log(max(x, 1e-30)).
+ * A chain that ends on a vector is reduced to its first component (Sec. 3.3). */
+typedef enum {
+    ISAAC_OP_ADD = 1, ISAAC_OP_MUL = 2, ISAAC_OP_LENGTH = 3,
+    ISAAC_OP_SUM = 4, ISAAC_OP_POW = 5, ISAAC_OP_LOG = 6
+} isaac_op;
+
+/* One source (Sec. 3.2).  Element (x, y, z, c) of the interior, with x, y, z
+ * in [0, n) and c in [0, f_dim), lives at
+ *     ptr[offset + x*stride[0] + y*stride[1] + z*stride[2] + c*comp_stride]
+ * (elements of the source's dtype; strides may have any sign, so any pitch
+ * or axis order is described without a copy, Sec. 3.1 accessors).  Guard
+ * cells (Sec. 3.1/3.2) extend every axis by `guard` cells on both sides with
+ * the neighbour's data; with guard = 0 interpolation clamps at the border.
+ * `extent` is the number of elements addressable from `ptr`; every cell the
+ * renderer can reach must lie in [0, extent) or the call fails with
+ * ISAAC_EGUARD.  Sources whose active_mask bit is clear are never read and
+ * may be NULL (Sec. 3.2, "a deactivated source is not touched at all"). */
+typedef struct {
+    const void *ptr;         /* device memory, owned by the caller */
+    int64_t extent;
+    int64_t offset;
+    int64_t stride[3];
+    int64_t comp_stride;
+    int32_t f_dim;           /* 1..4 */
+    int32_t guard;           /* >= 0 */
+} isaac_source;
+
+typedef struct {
+    int32_t op;              /* isaac_op */
+    int32_t n_args;          /* 0 for LENGTH/SUM/LOG; 1 (broadcast) or the current dimension */
+    float arg[4];
+} isaac_functor;
+
+typedef struct {
+    int32_t n_ops;           /* 0..ISAAC_MAX_FUNCTORS; 0 = identity (first component) */
+    isaac_functor ops[ISAAC_MAX_FUNCTORS];
+} isaac_chain;
+
+/* Clipping plane (Sec. 3 feature list): points p (global voxel coordinates)
+ * with n . p + d >= 0 are kept. */
+typedef struct {
+    double n[3];
+    double d;
+} isaac_plane;
+
+/* OpenGL-style column-major matrices (element (r, c) at [4*c + r]).  World
+ * coordinates are global voxel coordinates minus global_n / 2, so the global
+ * box is centred on the origin with one world unit per cell.  Pixel (x, y),
+ * row 0 at the top, shoots the ray from NDC (2(x+1/2)/W - 1, 1 - 2(y+1/2)/H,
+ * -1) to the same point at depth +1. */
+typedef struct {
+    double modelview[16];
+    double projection[16];
+    int32_t width;
+    int32_t height;
+} isaac_camera;
+
+typedef struct {
+    int64_t n[3];            /* interior cells of the local volume (all sources share it) */
+    int64_t global_n[3];     /* cells of the global volume; {0,0,0} = equal to n */
+    int64_t offset[3];       /* first cell of the local volume inside the global one */
+    float step;              /* sample spacing along the ray, in voxels, > 0 */
+    int32_t interp;          /* 1 = trilinear (Sec. 3 "data interpolation"), 0 = nearest cell */
+    float term_alpha;        /* a ray stops once its opacity A >= term_alpha; > 1 disables */
+    float bg[4];             /* background RGBA (premultiplied) blended behind the volume */
+    uint32_t active_mask;    /* bit s set: source s is rendered (Sec. 3.2) */
+} isaac_render_opts;
+
+/* Output buffers (device, owned by the caller), row-major, row 0 at the top. */
+typedef struct {
+    uint8_t *rgba8;          /* required: width*height*4 bytes */
+    float *rgba32;           /* optional: width*height*4 floats before quantisation */
+    int32_t *nsamples;       /* optional: width*height composited-sample counts */
+    /* optional footprint: one bit per cell of [-1, n]^3 that any composited
+     * sample read, cell (x,y,z) at bit ((z+1)*(ny+2) + (y+1))*(nx+2) + (x+1)
+     * of an array of ceil((nx+2)(ny+2)(nz+2)/32) words.  Bits are OR-ed in;
+     * the caller clears the array.  Measurement aid (slower path). */
+    uint32_t *touched;
+} isaac_framebuffer;
+
+/*
+ * isaac_render -- one frame of the volume ray caster (Sec. 3.2: "for every
+ * scan point ... iterates over all sources ... applies a functor chain ...
+ * classifies it to a color and opacity ... global color and opacity ...
+ * classical front to back ray cast").  Per pixel:
+ *   ray through the pixel centre; entry t0 into the global box (not before
+ *   the near plane); the local box and the clip planes bound [t_in, t_out];
+ *   samples t0 + k*step with t_in <= t < t_out (one global sample grid); per
+ *   active source the value at the sample (trilinear with guards, or nearest),
+ *   the source's functor chain, the source's 256-entry RGBA LUT (entries at
+ *   j/255, linear in between, input clamped to [0,1]); the sample colour is
+ *   sum_s weights[s] * rgba_s with alpha clamped to [0,1]; front-to-back
+ *   C += (1-A) a rgb, A += (1-A) a until A >= term_alpha; output
+ *   (C, A) + (1-A) bg, quantised to round(255 * clamp(x, 0, 1)).
+ *
+ * sources, chains, weights: host arrays of n_sources (1..ISAAC_MAX_SOURCES).
+ * luts: DEVICE array of n_sources * 256 * 4 floats (RGBA, source-major),
+ *       16-byte aligned, owned by the caller.
+ * camera, clip (n_clip <= ISAAC_MAX_CLIP, may be NULL if 0), opts, fb: host
+ *       structs, read before the call returns; the caller may reuse them.
+ * stream: cudaStream_t to order the work on (NULL = legacy default stream).
+ * The current CUDA device must own every device pointer.
+ */
+int isaac_render(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                 const float *luts, const float *weights, const isaac_camera *camera,
+                 const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
+                 const isaac_framebuffer *fb, void *stream);
+
+/* Text of the last error reported to the calling thread ("" if none). */
+const char *isaac_last_error(void);
+
+/* ISAAC_ABI_VERSION of the loaded library. */
+int isaac_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISAAC_B300_H */

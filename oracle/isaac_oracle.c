@@ -352,7 +352,11 @@ static int64_t orc_march(const orc_frame *F, const double o[3], const double d[3
         double pos[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         if (!p->interp && m_near)
             for (int a = 0; a < 3; ++a) {
-                double m = orc_dist_int(pos[a]);
+                /* only boundaries between two interior cells are decisions: at
+                 * the faces 0 and n both sides clamp to the same cell */
+                double r = floor(pos[a] + 0.5);
+                if (r <= 0.0 || r >= (double)p->n[a]) continue;
+                double m = fabs(pos[a] - r);
                 if (m < *m_near) *m_near = m;
             }
         double acc[4] = {0.0, 0.0, 0.0, 0.0};

@@ -1,0 +1,25 @@
+// common.h -- host helpers shared by the library's translation units.
+#pragma once
+
+#include "isaac_b300.h"
+
+namespace isaac {
+
+struct KParams;
+struct KSource;
+struct KChain;
+
+// Record an error message for isaac_last_error() and return `code`.
+int fail(int code, const char *fmt, ...);
+void clear_error();
+// Turn the last CUDA error (if any) into ISAAC_ECUDA.
+int check_cuda(const char *what);
+
+int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_clip,
+                  const isaac_render_opts *opt, KParams &p);
+int prepare_source(const isaac_source &src, int s, const int64_t n[3], int interp, float weight,
+                   int elem, KSource &ks, unsigned *nib, bool *wide);
+int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
+int prepare_fb(const isaac_framebuffer *fb, KParams &p);
+
+}  // namespace isaac

@@ -1,0 +1,412 @@
+// raycast.cuh -- device code of the FP32 volume ray caster (sm_103a).
+//
+// One thread per pixel/ray (Sec. 3.2: "for every scan point ... iterates over
+// all sources ..."), warps cover 8x4-pixel patches so that neighbouring rays
+// walk neighbouring cells, LUTs of the active sources sit in shared memory,
+// functor chains and source descriptors are read from the kernel's constant
+// parameter block (Sec. 3.3 keeps chains and their parameters in constant
+// memory for the same reason).  The per-source loop is unrolled at compile
+// time (Sec. 3.2) over a compacted list of the active sources, so inactive
+// sources are never touched.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <cuda_runtime.h>
+
+#include "isaac_b300.h"
+
+namespace isaac {
+
+// Internal functor codes: the public ones plus SQRT (POW with every
+// exponent 1/2, rewritten on the host).
+enum : int { K_ADD = 1, K_MUL = 2, K_LENGTH = 3, K_SUM = 4, K_POW = 5, K_LOG = 6, K_SQRT = 7 };
+
+struct KOp {
+    int code;
+    int dim;          // dimension of the value the op consumes
+    float a[4];       // arguments, scalar already broadcast
+};
+
+struct KChain {
+    int n;
+    KOp op[ISAAC_MAX_FUNCTORS];
+};
+
+struct KSource {
+    const float *base;   // element of interior cell (0,0,0), component 0
+    long long sx, sy, sz, sc;
+    int fdim;
+    int lo;              // lowest readable cell index per axis (-1 with guards, else 0)
+    int hi_pad;          // highest readable cell index = n - 1 + hi_pad
+    float w;             // blend weight
+};
+
+struct KParams {
+    double minv[16];                 // inverse of projection * modelview, column-major
+    double half_g[3];                // global_n / 2 (world -> global voxel)
+    double gn[3];                    // global box [0, gn)
+    double llo[3], lhi[3];           // local box in global voxel coordinates
+    double clip[ISAAC_MAX_CLIP][4];
+    double ndc_sx, ndc_sy;           // 2 / W, 2 / H
+    double step_d;
+    float step;
+    float term;
+    float bg[4];
+    int n_clip;
+    int nx, ny, nz;
+    int W, H;
+    int rx0, ry0, rx1, ry1, tiles_x; // rectangle of pixels that can hit the box
+    int max_steps;                   // samples on the longest chord of the local box
+    KSource src[ISAAC_MAX_ACTIVE];
+    KChain ch[ISAAC_MAX_ACTIVE];
+    const float4 *lut[ISAAC_MAX_ACTIVE];
+    uchar4 *fb8;
+    float4 *fb32;
+    int *nsamp;
+    unsigned *touched;               // optional footprint bitmap over [-1, n]^3
+};
+
+// Source signature: 4 bits per active source, bits 0-2 = f_dim (0 = read at
+// run time), bit 3 = components adjacent in memory (comp_stride == 1).
+__host__ __device__ constexpr int sig_fdim(unsigned sig, int i) { return int((sig >> (4 * i)) & 7u); }
+__host__ __device__ constexpr bool sig_aos(unsigned sig, int i) { return ((sig >> (4 * i + 3)) & 1u) != 0; }
+
+__device__ __forceinline__ float lerp1(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }  // NaN -> 0
+
+__device__ __forceinline__ unsigned char quant8(float x)
+{
+    float q = floorf(fmaf(255.0f, clamp01(x), 0.5f));
+    return (unsigned char)fminf(q, 255.0f);
+}
+
+// Functor chain of one source (Sec. 3.3, Table 1).  The op list is uniform
+// across the launch, so every branch below is uniform across the warp.
+__device__ __forceinline__ float run_chain(const KChain &ch, float v[4])
+{
+#pragma unroll
+    for (int i = 0; i < ISAAC_MAX_FUNCTORS; ++i) {
+        if (i >= ch.n) break;
+        const KOp &o = ch.op[i];
+        const int d = o.dim;
+        switch (o.code) {
+        case K_ADD:
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] += o.a[c];
+            break;
+        case K_MUL:
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] *= o.a[c];
+            break;
+        case K_LENGTH: {
+            float s = v[0] * v[0];
+            if (d > 1) s = fmaf(v[1], v[1], s);
+            if (d > 2) s = fmaf(v[2], v[2], s);
+            if (d > 3) s = fmaf(v[3], v[3], s);
+            v[0] = sqrtf(s);
+        } break;
+        case K_SUM: {
+            float s = v[0];
+            if (d > 1) s += v[1];
+            if (d > 2) s += v[2];
+            if (d > 3) s += v[3];
+            v[0] = s;
+        } break;
+        case K_SQRT:
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < d) v[c] = v[c] > 0.0f ? sqrtf(v[c]) : 0.0f;
+            break;
+        case K_POW:
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < d) v[c] = v[c] > 0.0f ? powf(v[c], o.a[c]) : 0.0f;
+            break;
+        case K_LOG:
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (c < d) v[c] = logf(fmaxf(v[c], 1e-30f));
+            break;
+        default:
+            break;
+        }
+    }
+    return v[0];
+}
+
+// Transfer function: clamp to [0,1], entries at j/255, linear in between.
+__device__ __forceinline__ float4 classify(const float4 *lut, float x)
+{
+    const float pos = clamp01(x) * 255.0f;
+    const int j = min((int)pos, 254);
+    const float f = pos - (float)j;
+    const float4 a = lut[j], b = lut[j + 1];
+    return make_float4(lerp1(a.x, b.x, f), lerp1(a.y, b.y, f), lerp1(a.z, b.z, f),
+                       lerp1(a.w, b.w, f));
+}
+
+// Geometry of one sample shared by all sources.
+struct Geo {
+    int ix, iy, iz;      // lower corner (trilinear) or the cell (nearest), unclamped
+    float fx, fy, fz;    // trilinear weights
+};
+
+template <typename Idx>
+__device__ __forceinline__ float ld(const float *b, Idx o) { return __ldg(b + o); }
+
+// Value of source I at the sample: 8-corner gather + trilinear blend per
+// component, or the nearest cell.  Indices are clamped to the readable range
+// the host validated against the source's extent, so no access can leave it.
+template <int I, unsigned SIG, int INTERP, typename Idx>
+__device__ __forceinline__ void fetch_source(const KParams &p, const Geo &g, float v[4])
+{
+    constexpr int FD = sig_fdim(SIG, I);
+    constexpr bool AOS = sig_aos(SIG, I);
+    const KSource &s = p.src[I];
+    const int fd = FD ? FD : s.fdim;
+    const Idx cs = AOS ? Idx(1) : Idx(s.sc);
+    const float *base = s.base;
+    if (INTERP) {
+        const int x0 = min(max(g.ix, s.lo), p.nx - 1 + s.hi_pad);
+        const int x1 = min(max(g.ix + 1, s.lo), p.nx - 1 + s.hi_pad);
+        const int y0 = min(max(g.iy, s.lo), p.ny - 1 + s.hi_pad);
+        const int y1 = min(max(g.iy + 1, s.lo), p.ny - 1 + s.hi_pad);
+        const int z0 = min(max(g.iz, s.lo), p.nz - 1 + s.hi_pad);
+        const int z1 = min(max(g.iz + 1, s.lo), p.nz - 1 + s.hi_pad);
+        const Idx sx = Idx(s.sx), sy = Idx(s.sy), sz = Idx(s.sz);
+        const Idx ox0 = Idx(x0) * sx, ox1 = Idx(x1) * sx;
+        const Idx o00 = Idx(y0) * sy + Idx(z0) * sz, o10 = Idx(y1) * sy + Idx(z0) * sz;
+        const Idx o01 = Idx(y0) * sy + Idx(z1) * sz, o11 = Idx(y1) * sy + Idx(z1) * sz;
+        const float *p000 = base + (ox0 + o00), *p100 = base + (ox1 + o00);
+        const float *p010 = base + (ox0 + o10), *p110 = base + (ox1 + o10);
+        const float *p001 = base + (ox0 + o01), *p101 = base + (ox1 + o01);
+        const float *p011 = base + (ox0 + o11), *p111 = base + (ox1 + o11);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c < fd) {
+                const Idx co = Idx(c) * cs;
+                const float c00 = lerp1(ld(p000, co), ld(p100, co), g.fx);
+                const float c10 = lerp1(ld(p010, co), ld(p110, co), g.fx);
+                const float c01 = lerp1(ld(p001, co), ld(p101, co), g.fx);
+                const float c11 = lerp1(ld(p011, co), ld(p111, co), g.fx);
+                v[c] = lerp1(lerp1(c00, c10, g.fy), lerp1(c01, c11, g.fy), g.fz);
+            } else {
+                v[c] = 0.0f;
+            }
+        }
+    } else {
+        const int x = min(max(g.ix, 0), p.nx - 1);
+        const int y = min(max(g.iy, 0), p.ny - 1);
+        const int z = min(max(g.iz, 0), p.nz - 1);
+        const float *pc = base + (Idx(x) * Idx(s.sx) + Idx(y) * Idx(s.sy) + Idx(z) * Idx(s.sz));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = (c < fd) ? ld(pc, Idx(c) * cs) : 0.0f;
+    }
+}
+
+template <int I, unsigned SIG, int INTERP, typename Idx>
+__device__ __forceinline__ void shade_source(const KParams &p, const Geo &g, const float4 *s_lut,
+                                             float4 &acc)
+{
+    float v[4];
+    fetch_source<I, SIG, INTERP, Idx>(p, g, v);
+    const float x = run_chain(p.ch[I], v);
+    const float4 c = classify(s_lut + I * 256, x);
+    const float w = p.src[I].w;
+    acc.x = fmaf(w, c.x, acc.x);
+    acc.y = fmaf(w, c.y, acc.y);
+    acc.z = fmaf(w, c.z, acc.z);
+    acc.w = fmaf(w, c.w, acc.w);
+}
+
+template <unsigned SIG, int INTERP, typename Idx, int... Is>
+__device__ __forceinline__ void shade_all(const KParams &p, const Geo &g, const float4 *s_lut,
+                                          float4 &acc, std::integer_sequence<int, Is...>)
+{
+    (shade_source<Is, SIG, INTERP, Idx>(p, g, s_lut, acc), ...);
+}
+
+// Ray setup in FP64 (camera unprojection, box and clip-plane intervals, the
+// sample index range).  The discrete decisions (first/last sample) are taken
+// in double so they match an FP64 reference except at exact ties; the entry
+// point and direction are then rounded to FP32 for the march.
+struct Ray {
+    float ex, ey, ez;    // local voxel position of the first sample
+    float dx, dy, dz;    // unit direction
+    int nsteps;          // samples in [t_in, t_out) on the global grid (0 = miss)
+};
+
+__device__ __forceinline__ Ray setup_ray(const KParams &p, int px, int py)
+{
+    Ray r;
+    r.nsteps = 0;
+    r.ex = r.ey = r.ez = 0.0f;
+    r.dx = r.dy = r.dz = 0.0f;
+    const double *m = p.minv;
+    const double xn = ((double)px + 0.5) * p.ndc_sx - 1.0;
+    const double yn = 1.0 - ((double)py + 0.5) * p.ndc_sy;
+    double nb[4], fb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double b = fma(m[i], xn, fma(m[4 + i], yn, m[12 + i]));
+        nb[i] = b - m[8 + i];
+        fb[i] = b + m[8 + i];
+    }
+    const double inw = 1.0 / nb[3], ifw = 1.0 / fb[3];
+    double o[3], d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double nv = nb[a] * inw;
+        o[a] = nv + p.half_g[a];
+        d[a] = fb[a] * ifw - nv;
+    }
+    const double il = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    d[0] *= il;
+    d[1] *= il;
+    d[2] *= il;
+    // a degenerate pixel (point at infinity, zero direction) cannot be cast
+    if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]) && isfinite(d[0]) &&
+          isfinite(d[1]) && isfinite(d[2])))
+        return r;
+
+    double t0 = 0.0, tg1 = 1e300, tl0 = 0.0, tout = 1e300;
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0) {
+            const double inv = 1.0 / d[a];
+            double ta = (0.0 - o[a]) * inv, tb = (p.gn[a] - o[a]) * inv;
+            t0 = fmax(t0, fmin(ta, tb));
+            tg1 = fmin(tg1, fmax(ta, tb));
+            ta = (p.llo[a] - o[a]) * inv;
+            tb = (p.lhi[a] - o[a]) * inv;
+            tl0 = fmax(tl0, fmin(ta, tb));
+            tout = fmin(tout, fmax(ta, tb));
+        } else if (o[a] < p.llo[a] || o[a] >= p.lhi[a]) {
+            miss = true;
+        }
+    }
+    if (t0 >= tg1) miss = true;
+    double tin = fmax(t0, tl0);
+    for (int i = 0; i < p.n_clip; ++i) {
+        const double *pl = p.clip[i];
+        const double s = fma(pl[0], o[0], fma(pl[1], o[1], fma(pl[2], o[2], pl[3])));
+        const double rr = fma(pl[0], d[0], fma(pl[1], d[1], pl[2] * d[2]));
+        if (rr > 0.0) {
+            tin = fmax(tin, -s / rr);
+        } else if (rr < 0.0) {
+            tout = fmin(tout, -s / rr);
+        } else if (s < 0.0) {
+            miss = true;
+        }
+    }
+    // the local box is bounded, so a ray inside it has a finite exit
+    if (miss || !(tin < tout) || !(tout < 1e299)) return r;
+    const long long kf = (tin > t0) ? (long long)ceil((tin - t0) / p.step_d) : 0LL;
+    const long long ke = (long long)ceil((tout - t0) / p.step_d);
+    if (ke <= kf) return r;
+    const double tf = t0 + (double)kf * p.step_d;
+    r.ex = (float)(fma(tf, d[0], o[0]) - p.llo[0]);
+    r.ey = (float)(fma(tf, d[1], o[1]) - p.llo[1]);
+    r.ez = (float)(fma(tf, d[2], o[2]) - p.llo[2]);
+    r.dx = (float)d[0];
+    r.dy = (float)d[1];
+    r.dz = (float)d[2];
+    r.nsteps = (int)min(ke - kf, (long long)p.max_steps);
+    return r;
+}
+
+// Footprint: mark the cells a sample reads in the [-1, n]^3 bitmap.
+template <int INTERP>
+__device__ __forceinline__ void mark_footprint(const KParams &p, const Geo &g)
+{
+    const int W = p.nx + 2, H = p.ny + 2;
+#pragma unroll
+    for (int c = 0; c < (INTERP ? 8 : 1); ++c) {
+        const int x = min(max(g.ix + (c & 1), -1), p.nx) + 1;
+        const int y = min(max(g.iy + ((c >> 1) & 1), -1), p.ny) + 1;
+        const int z = min(max(g.iz + ((c >> 2) & 1), -1), p.nz) + 1;
+        const long long bit = ((long long)z * H + y) * W + x;
+        atomicOr(p.touched + (bit >> 5), 1u << (bit & 31));
+    }
+}
+
+// The frame kernel: 128 threads = 16x8 pixels, each warp an 8x4 patch.
+template <int NACT, unsigned SIG, int INTERP, typename Idx, bool TOUCH = false>
+__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ KParams p)
+{
+    __shared__ float4 s_lut[NACT * 256];
+    for (int i = threadIdx.x; i < NACT * 256; i += blockDim.x) s_lut[i] = __ldg(p.lut[i >> 8] + (i & 255));
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ty = blockIdx.x / p.tiles_x, tx = blockIdx.x - ty * p.tiles_x;
+    const int px = p.rx0 + tx * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = p.ry0 + ty * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= p.rx1 || py >= p.ry1) return;
+
+    const Ray ray = setup_ray(p, px, py);
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    int ns = 0;
+    for (int k = 0; k < ray.nsteps; ++k) {
+        const float s = (float)k * p.step;
+        const float x = fmaf(s, ray.dx, ray.ex);
+        const float y = fmaf(s, ray.dy, ray.ey);
+        const float z = fmaf(s, ray.dz, ray.ez);
+        Geo g;
+        if (INTERP) {
+            const float qx = x - 0.5f, qy = y - 0.5f, qz = z - 0.5f;
+            const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+            g.ix = (int)flx;
+            g.iy = (int)fly;
+            g.iz = (int)flz;
+            g.fx = qx - flx;
+            g.fy = qy - fly;
+            g.fz = qz - flz;
+        } else {
+            g.ix = (int)floorf(x);
+            g.iy = (int)floorf(y);
+            g.iz = (int)floorf(z);
+            g.fx = g.fy = g.fz = 0.0f;
+        }
+        if (TOUCH) mark_footprint<INTERP>(p, g);
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        shade_all<SIG, INTERP, Idx>(p, g, s_lut, acc, std::make_integer_sequence<int, NACT>{});
+        const float a = clamp01(acc.w);
+        const float t = (1.0f - A) * a;
+        C0 = fmaf(t, acc.x, C0);
+        C1 = fmaf(t, acc.y, C1);
+        C2 = fmaf(t, acc.z, C2);
+        A += t;
+        ++ns;
+        if (A >= p.term) break;
+    }
+    const float T = 1.0f - A;
+    const float o0 = fmaf(T, p.bg[0], C0), o1 = fmaf(T, p.bg[1], C1);
+    const float o2 = fmaf(T, p.bg[2], C2), o3 = fmaf(T, p.bg[3], A);
+    const size_t pix = (size_t)py * (size_t)p.W + (size_t)px;
+    p.fb8[pix] = make_uchar4(quant8(o0), quant8(o1), quant8(o2), quant8(o3));
+    if (p.fb32) p.fb32[pix] = make_float4(o0, o1, o2, o3);
+    if (p.nsamp) p.nsamp[pix] = ns;
+}
+
+// Background for every pixel outside the rectangle the ray kernel covers.
+__global__ void k_fill_background(const __grid_constant__ KParams p)
+{
+    const size_t total = (size_t)p.W * (size_t)p.H;
+    const float T = 1.0f;
+    const uchar4 q = make_uchar4(quant8(fmaf(T, p.bg[0], 0.0f)), quant8(fmaf(T, p.bg[1], 0.0f)),
+                                 quant8(fmaf(T, p.bg[2], 0.0f)), quant8(fmaf(T, p.bg[3], 0.0f)));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / (size_t)p.W), x = (int)(i - (size_t)y * p.W);
+        if (x >= p.rx0 && x < p.rx1 && y >= p.ry0 && y < p.ry1) continue;
+        p.fb8[i] = q;
+        if (p.fb32) p.fb32[i] = make_float4(p.bg[0], p.bg[1], p.bg[2], p.bg[3]);
+        if (p.nsamp) p.nsamp[i] = 0;
+    }
+}
+
+}  // namespace isaac

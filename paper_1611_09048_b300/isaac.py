@@ -1,0 +1,228 @@
+"""Thin ctypes binding of ``libisaac_b300.so`` (the C ABI in include/isaac_b300.h).
+
+Argument marshalling only: every step of a frame runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The binding refuses to
+run without the compiled library -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libisaac_b300.so")
+
+MAX_SOURCES = 8
+MAX_ACTIVE = 4
+MAX_FUNCTORS = 8
+MAX_CLIP = 6
+
+OK, EINVAL, EGUARD, ENOMEM, ECUDA, ENOTSUP = 0, -1, -2, -3, -4, -5
+F32, BF16, F16, E4M3 = 0, 1, 2, 3
+OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
+
+# every C symbol declared in include/isaac_b300.h
+EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version")
+
+
+class Source(C.Structure):
+    _fields_ = [("ptr", C.c_void_p), ("extent", C.c_int64), ("offset", C.c_int64),
+                ("stride", C.c_int64 * 3), ("comp_stride", C.c_int64), ("f_dim", C.c_int32),
+                ("guard", C.c_int32)]
+
+
+class Functor(C.Structure):
+    _fields_ = [("op", C.c_int32), ("n_args", C.c_int32), ("arg", C.c_float * 4)]
+
+
+class Chain(C.Structure):
+    _fields_ = [("n_ops", C.c_int32), ("ops", Functor * MAX_FUNCTORS)]
+
+
+class Plane(C.Structure):
+    _fields_ = [("n", C.c_double * 3), ("d", C.c_double)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("modelview", C.c_double * 16), ("projection", C.c_double * 16),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("n", C.c_int64 * 3), ("global_n", C.c_int64 * 3), ("offset", C.c_int64 * 3),
+                ("step", C.c_float), ("interp", C.c_int32), ("term_alpha", C.c_float),
+                ("bg", C.c_float * 4), ("active_mask", C.c_uint32)]
+
+
+class Framebuffer(C.Structure):
+    _fields_ = [("rgba8", C.c_void_p), ("rgba32", C.c_void_p), ("nsamples", C.c_void_p),
+                ("touched", C.c_void_p)]
+
+
+class IsaacError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"isaac error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with "
+                               "`python -m paper_1611_09048_b300.build` (no CPU fallback exists)")
+        lib = C.CDLL(p)
+        lib.isaac_render.restype = C.c_int
+        lib.isaac_render.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32, C.c_void_p,
+                                     C.c_void_p, C.POINTER(Camera), C.POINTER(Plane), C.c_int32,
+                                     C.POINTER(RenderOpts), C.POINTER(Framebuffer), C.c_void_p]
+        lib.isaac_last_error.restype = C.c_char_p
+        lib.isaac_abi_version.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def check(rc: int):
+    if rc != OK:
+        raise IsaacError(rc, load().isaac_last_error().decode())
+
+
+# ----------------------------------------------------------- marshalling
+
+def make_chain(spec) -> Chain:
+    """[("length",), ("mul", (a,)), ...] -> Chain (Sec. 3.3)."""
+    ch = Chain()
+    if len(spec) > MAX_FUNCTORS:
+        raise ValueError(f"chain longer than {MAX_FUNCTORS}")
+    ch.n_ops = len(spec)
+    for i, f in enumerate(spec):
+        args = tuple(f[1]) if len(f) > 1 else ()
+        ch.ops[i].op = OPS[f[0]]
+        ch.ops[i].n_args = len(args)
+        for j, a in enumerate(args[:4]):
+            ch.ops[i].arg[j] = float(a)
+    return ch
+
+
+def make_camera(mv, proj, width, height) -> Camera:
+    cam = Camera()
+    for i in range(16):
+        cam.modelview[i] = float(mv[i])
+        cam.projection[i] = float(proj[i])
+    cam.width, cam.height = int(width), int(height)
+    return cam
+
+
+def make_opts(scene, mask=None) -> RenderOpts:
+    o = RenderOpts()
+    for a in range(3):
+        o.n[a] = int(scene.n[a])
+        o.global_n[a] = int(scene.gn[a])
+        o.offset[a] = int(scene.off[a])
+    o.step = float(scene.step)
+    o.interp = int(scene.interp)
+    o.term_alpha = float(scene.term)
+    for c in range(4):
+        o.bg[c] = float(scene.bg[c])
+    o.active_mask = int(scene.mask if mask is None else mask)
+    return o
+
+
+def make_planes(clip):
+    if len(clip) > MAX_CLIP:
+        raise ValueError(f"more than {MAX_CLIP} clip planes")
+    arr = (Plane * max(1, len(clip)))()
+    for i, pl in enumerate(clip):
+        arr[i].n[0], arr[i].n[1], arr[i].n[2] = (float(v) for v in pl[:3])
+        arr[i].d = float(pl[3])
+    return arr, len(clip)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class DeviceScene:
+    """A synth.Scene whose sources and LUTs are resident in device memory.
+
+    The fields are copied to the GPU once (standing in for simulation data that
+    already lives there); ``render`` then launches frames against them."""
+
+    def __init__(self, scene, device="cuda"):
+        import torch
+        self.scene = scene
+        self.device = torch.device(device)
+        self.data = []
+        n_src = len(scene.sources)
+        self.sources = (Source * n_src)()
+        self.chains = (Chain * n_src)()
+        for s, src in enumerate(scene.sources):
+            t = torch.from_numpy(np.ascontiguousarray(src.data, np.float32)).to(self.device)
+            self.data.append(t)
+            self._describe(s, src, t)
+            self.chains[s] = make_chain(scene.chains[s])
+        self.luts = torch.from_numpy(np.ascontiguousarray(scene.luts, np.float32)).to(self.device)
+        self.weights = (C.c_float * n_src)(*[float(w) for w in scene.weights])
+
+    def _describe(self, s, src, t):
+        d = self.sources[s]
+        d.ptr = t.data_ptr()
+        d.extent = t.numel()
+        d.offset = int(src.offset)
+        for a in range(3):
+            d.stride[a] = int(src.strides[a])
+        d.comp_stride = int(src.cstride)
+        d.f_dim = int(src.fdim)
+        d.guard = int(src.guard)
+
+    def set_luts(self, luts):
+        self.luts.copy_(self.luts.new_tensor(np.asarray(luts, np.float32)).reshape(self.luts.shape))
+
+    def set_chain(self, s, spec):
+        self.chains[s] = make_chain(spec)
+
+    def footprint_words(self):
+        nx, ny, nz = self.scene.n
+        return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
+
+    def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
+               mask=None, want_f32=False, want_nsamp=False, touched=None):
+        """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
+        as device tensors."""
+        import torch
+        sc = self.scene
+        W, H = sc.width, sc.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
+        if rgba32 is None and want_f32:
+            rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
+        if nsamples is None and want_nsamp:
+            nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
+        cam = make_camera(sc.modelview if mv is None else mv,
+                          sc.projection if proj is None else proj, W, H)
+        planes, n_clip = make_planes(sc.clip)
+        fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
+                         nsamples.data_ptr() if nsamples is not None else None,
+                         touched.data_ptr() if touched is not None else None)
+        opts = make_opts(sc, mask)
+        rc = load().isaac_render(self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
+                                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip,
+                                 C.byref(opts), C.byref(fb), _stream_handle(stream))
+        check(rc)
+        return out, rgba32, nsamples
+
+
+def render(scene, **kw):
+    """One-shot convenience: upload ``scene`` and render it on the current GPU."""
+    return DeviceScene(scene).render(**kw)

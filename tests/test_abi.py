@@ -1,0 +1,187 @@
+"""The C-ABI library loads, exports every symbol the header declares, and
+rejects malformed calls on the host (no GPU work is issued by these calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1611_09048_b300 import isaac
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(isaac_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = isaac.load()
+    declared = _declared_functions()
+    assert "isaac_render" in declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(isaac.EXPORTS) <= declared
+
+
+def test_abi_version():
+    assert isaac.load().isaac_abi_version() == 1
+
+
+def test_struct_sizes_match_header_layout():
+    # sizes implied by the header's field order on LP64
+    assert C.sizeof(isaac.Source) == 8 + 8 + 8 + 24 + 8 + 4 + 4
+    assert C.sizeof(isaac.Functor) == 4 + 4 + 16
+    assert C.sizeof(isaac.Chain) == 4 + 24 * isaac.MAX_FUNCTORS
+    assert C.sizeof(isaac.Camera) == 256 + 8
+    assert C.sizeof(isaac.RenderOpts) == 72 + 4 + 4 + 4 + 16 + 4
+
+
+FAKE = 0x7F0000000000  # never dereferenced: every call below fails validation first
+
+
+def _valid_call_args(n=8, fdim=1, guard=0, width=16, height=16):
+    S = n + 2 * guard
+    src = (isaac.Source * 1)()
+    src[0].ptr = FAKE
+    src[0].extent = S ** 3 * fdim
+    src[0].offset = guard * (fdim + fdim * S + fdim * S * S)
+    src[0].stride[0], src[0].stride[1], src[0].stride[2] = fdim, fdim * S, fdim * S * S
+    src[0].comp_stride = 1
+    src[0].f_dim = fdim
+    src[0].guard = guard
+    chains = (isaac.Chain * 1)()
+    weights = (C.c_float * 1)(1.0)
+    mv = np.eye(4).reshape(16)
+    mv[14] = -3.0 * n
+    from paper_1611_09048_b300 import synth
+    proj = synth.perspective(60.0, 1.0, 0.1, 10.0 * n)
+    cam = isaac.make_camera(mv, proj, width, height)
+    opts = isaac.RenderOpts()
+    for a in range(3):
+        opts.n[a] = n
+    opts.step = 0.5
+    opts.interp = 1
+    opts.term_alpha = 0.99
+    opts.active_mask = 1
+    fb = isaac.Framebuffer(FAKE, None, None, None)
+    return dict(src=src, chains=chains, n_src=1, luts=FAKE, weights=weights, cam=cam,
+                clip=None, n_clip=0, opts=opts, fb=fb)
+
+
+def _call(a):
+    lib = isaac.load()
+    return lib.isaac_render(a["src"], a["chains"], a["n_src"], a["luts"],
+                            C.cast(a["weights"], C.c_void_p), C.byref(a["cam"]), a["clip"],
+                            a["n_clip"], C.byref(a["opts"]), C.byref(a["fb"]), None)
+
+
+def _expect(a, code, fragment):
+    rc = _call(a)
+    msg = isaac.load().isaac_last_error().decode()
+    assert rc == code, (rc, msg)
+    assert fragment in msg, msg
+
+
+def test_rejects_bad_fdim():
+    a = _valid_call_args()
+    a["src"][0].f_dim = 5
+    _expect(a, isaac.EINVAL, "f_dim")
+
+
+def test_rejects_guard_beyond_allocation():
+    a = _valid_call_args(guard=0)
+    a["src"][0].guard = 2          # declares guards the storage does not hold
+    _expect(a, isaac.EGUARD, "extent")
+
+
+def test_rejects_extent_too_small():
+    a = _valid_call_args()
+    a["src"][0].extent -= 1
+    _expect(a, isaac.EGUARD, "extent")
+
+
+def test_rejects_chain_argument_count():
+    a = _valid_call_args(fdim=3)
+    a["chains"][0] = isaac.make_chain([("mul", (1.0, 2.0))])
+    _expect(a, isaac.EINVAL, "arguments")
+
+
+def test_rejects_unknown_functor():
+    a = _valid_call_args()
+    a["chains"][0].n_ops = 1
+    a["chains"][0].ops[0].op = 42
+    _expect(a, isaac.EINVAL, "unknown op")
+
+
+def test_rejects_nan_weight():
+    a = _valid_call_args()
+    a["weights"][0] = float("nan")
+    _expect(a, isaac.EINVAL, "weight")
+
+
+def test_rejects_singular_camera():
+    a = _valid_call_args()
+    for i in range(16):
+        a["cam"].projection[i] = 0.0
+    _expect(a, isaac.EINVAL, "singular")
+
+
+def test_rejects_bad_step_and_sizes():
+    a = _valid_call_args()
+    a["opts"].step = 0.0
+    _expect(a, isaac.EINVAL, "step")
+    a = _valid_call_args()
+    a["cam"].width = 0
+    _expect(a, isaac.EINVAL, "image size")
+    a = _valid_call_args()
+    a["opts"].global_n[0], a["opts"].global_n[1], a["opts"].global_n[2] = 8, 8, 8
+    a["opts"].offset[0] = 1
+    _expect(a, isaac.EINVAL, "global size")
+
+
+def test_rejects_mask_bits_beyond_sources():
+    a = _valid_call_args()
+    a["opts"].active_mask = 0b11
+    _expect(a, isaac.EINVAL, "active_mask")
+
+
+def test_rejects_too_many_active_sources():
+    a = _valid_call_args()
+    n = 5
+    src = (isaac.Source * n)(*[a["src"][0]] * n)
+    a["src"] = src
+    a["chains"] = (isaac.Chain * n)()
+    a["weights"] = (C.c_float * n)(*([1.0] * n))
+    a["n_src"] = n
+    a["opts"].active_mask = (1 << n) - 1
+    _expect(a, isaac.ENOTSUP, "active sources")
+
+
+def test_disabled_source_may_be_null():
+    """A NULL inactive source passes validation (it is never read); the call
+    then fails only on the deliberately missing framebuffer."""
+    a = _valid_call_args()
+    src = (isaac.Source * 2)(a["src"][0], isaac.Source())
+    a["src"] = src
+    a["chains"] = (isaac.Chain * 2)()
+    a["weights"] = (C.c_float * 2)(1.0, 1.0)
+    a["n_src"] = 2
+    a["opts"].active_mask = 0b01
+    a["fb"] = isaac.Framebuffer(None, None, None, None)
+    _expect(a, isaac.EINVAL, "rgba8")
+
+
+def test_rejects_misaligned_lut():
+    a = _valid_call_args()
+    a["luts"] = FAKE + 4
+    _expect(a, isaac.EINVAL, "16-byte")

@@ -238,6 +238,17 @@ def test_bruteforce_tiny_volume_columns(interp, n):
     r = oracle.render(sc)
     w = [float(np.float32(x)) for x in w]       # the scene stores float32 weights
     ks = np.arange(int(math.ceil(nz / step)))
+    if interp == 0:
+        # nearest-cell margin: distance of a sample to the closest boundary
+        # between two interior cells (x, y sit on cell centres: 0.5)
+        pz = nz - step * ks
+        near_int = np.floor(pz + 0.5)
+        inner = (near_int > 0) & (near_int < nz)
+        want_m = min(0.5, float(np.abs(pz - near_int)[inner].min()))
+        stopped = r["nsamp"] < len(ks)
+        np.testing.assert_allclose(r["margin"][..., 3][~stopped], want_m, rtol=0, atol=1e-9)
+    else:
+        assert np.all(r["margin"][..., 3] == oracle.oracle.INF)
     for py in range(ny):
         iy = ny - 1 - py
         for px in range(nx):

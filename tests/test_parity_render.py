@@ -1,0 +1,174 @@
+"""GPU parity: isaac_render (CUDA, through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_09048_b300 import isaac, synth
+from parity_util import TOL_F32, assert_parity, compare
+from scenes_util import const_lut, make_scene, ortho_down_z, small_pic_scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(scene, **kw):
+    import torch
+    ds = isaac.DeviceScene(scene)
+    out, f32, ns = ds.render(want_f32=True, want_nsamp=True, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), f32.cpu().numpy(), ns.cpu().numpy()
+
+
+def _check(scene, what, max_excluded=1e-3, **cmp):
+    g8, g32, gns = _gpu(scene)
+    r = oracle.render(scene)
+    rep = compare(g32, g8, gns, r, interp=scene.interp, **cmp)
+    assert_parity(rep, max_excluded, what)
+    return rep, r, (g8, g32, gns)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blobs_64_full_frame(cuda_ok, seed):
+    """One scalar 64^3 field of Gaussian blobs, 256x256, trilinear, step 0.5,
+    termination at 0.99, black background."""
+    sc = synth.scene_blobs(64, 256, 256, seed=seed)
+    rep, r, _ = _check(sc, f"blobs seed {seed}")
+    assert rep.hit > 1000
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("dist", [2.0, 1.0, 0.45])
+def test_pic_small(cuda_ok, layout, dist):
+    """E, B (3 components) and density with guards, functor chains, three
+    LUTs, weights, a clip plane; AoS and component-plane layouts; far, near
+    and inside-the-box cameras (the last covers the whole screen)."""
+    sc = small_pic_scene(n=24, guard=2, width=53, height=37, seed=3, layout=layout,
+                         dist_factor=dist)
+    rep, _, _ = _check(sc, f"pic {layout} {dist}")
+    assert rep.hit > 50
+
+
+def test_pic_nearest(cuda_ok):
+    sc = small_pic_scene(n=24, guard=2, width=64, height=48, seed=4, dist_factor=1.0)
+    sc.interp = 0
+    # nearest-cell sampling flips cells where FP32 positions sit within
+    # rounding of a boundary; those pixels are excluded and counted
+    rep, _, _ = _check(sc, "nearest", max_excluded=0.2)
+    assert rep.hit - rep.excluded > 200
+
+
+def test_generic_kernel_four_sources_mixed_guards(cuda_ok):
+    """Four sources (f_dim 2, 4, 1, 3), one without guards, run the generic
+    kernel (run-time f_dim, per-source border handling)."""
+    rng = np.random.default_rng(11)
+    n = (20, 18, 22)
+    g = [1, 0, 2, 1]
+    fd = [2, 4, 1, 3]
+    fields = []
+    for gi, f in zip(g, fd):
+        shape = tuple(k + 2 * gi for k in n[::-1]) + ((f,) if f > 1 else ())
+        fields.append(rng.uniform(-1, 1, shape).astype(np.float32))
+    srcs = [synth.source_from_zyx(fl, gi) for fl, gi in zip(fields, g)]
+    chains = [[("length",), ("mul", (0.6,))], [("mul", (0.5, 1.0, 0.25, 2.0)), ("sum",),
+                                                 ("add", (0.5,))],
+              [("add", (1.0,)), ("pow", (1.5,)), ("mul", (0.3,))], [("pow", (2.0, 1.0, 0.5)), ("sum",), ("log",), ("add", (1.0,))]]
+    luts = np.stack([synth.lut_from_points(40 + i, alpha_max=0.08) for i in range(4)])
+    mv, proj = synth.random_orbit_camera(n, 61, 47, seed=9, dist_factor=1.2)
+    sc = synth.Scene(n=n, sources=srcs, chains=chains, luts=luts,
+                     weights=np.array([0.3, 0.3, 0.2, 0.2], np.float32), modelview=mv,
+                     projection=proj, width=61, height=47, clip=[(0.3, -0.5, 0.2, 3.0)])
+    rep, _, _ = _check(sc, "generic 4 sources")
+    assert rep.hit > 300
+
+
+def test_disabled_source_poisoned_on_gpu(cuda_ok):
+    sc = small_pic_scene(dist_factor=1.0)
+    sc.active_mask = 0b101
+    sc.sources[1].data = np.full_like(sc.sources[1].data, np.nan)
+    rep, _, _ = _check(sc, "mask 101 with NaN in the disabled source")
+    assert rep.hit > 100
+
+
+def test_single_active_of_three(cuda_ok):
+    sc = small_pic_scene(dist_factor=1.0)
+    sc.active_mask = 0b010
+    _check(sc, "mask 010")
+
+
+def test_domain_split_on_gpu(cuda_ok):
+    """Two halves rendered separately on the GPU on the same global sample
+    grid, over-composited, equal the oracle's whole-volume image."""
+    n, g = 20, 2
+    E, B, rho = synth.pic_fields(n, g, seed=5)
+    whole = synth.scene_pic(n=n, guard=g, width=40, height=32, seed=5, fields=(E, B, rho),
+                            dist_factor=1.0)
+    whole.term = 2.0
+    ref = oracle.render(whole)
+    parts = []
+    for lo in (0, n // 2):
+        part = synth.scene_pic(n=n, guard=g, width=40, height=32, seed=5, fields=(E, B, rho),
+                               dist_factor=1.0)
+        part.term = 2.0
+        part.global_n = (n, n, n)
+        part.off = (lo, 0, 0)
+        part.n = (n // 2, n, n)
+        for s in part.sources:
+            s.offset = s.offset + lo * s.strides[0]
+        g8, g32, gns = _gpu(part)
+        po = oracle.render(part)
+        assert_parity(compare(g32, g8, gns, po), 1e-3, f"half at {lo}")
+        parts.append((g32.astype(np.float64), po["kfirst"]))
+    first0 = (parts[0][1] >= 0) & ((parts[1][1] < 0) | (parts[0][1] < parts[1][1]))
+    f = np.where(first0[..., None], parts[0][0], parts[1][0])
+    b = np.where(first0[..., None], parts[1][0], parts[0][0])
+    comp = f + (1 - f[..., 3:4]) * b
+    assert np.abs(comp - ref["rgba"]).max() <= 2 * TOL_F32
+
+
+def test_edge_cases(cuda_ok):
+    base = small_pic_scene(n=16, guard=1, width=37, height=23, dist_factor=1.0)
+    # ragged image size, 1x1 image, a single huge step, termination disabled
+    for kw in ({}, {"width": 1, "height": 1}, {"step": 40.0}, {"term": 2.0},
+               {"bg": (0.2, 0.4, 0.6, 1.0)}):
+        sc = dataclasses.replace(base, **kw)
+        _check(sc, f"edge {kw}")
+    # no active source: background only
+    sc = dataclasses.replace(base, active_mask=0, bg=(0.1, 0.2, 0.3, 0.5))
+    g8, g32, gns = _gpu(sc)
+    assert np.all(gns == 0)
+    np.testing.assert_allclose(g32, np.broadcast_to(np.float32([0.1, 0.2, 0.3, 0.5]), g32.shape))
+    # camera looking away from the volume: every pixel misses
+    mv = synth.look_at((0.0, 0.0, 60.0), (0.0, 0.0, 120.0), (0.0, 1.0, 0.0))
+    sc = dataclasses.replace(base, modelview=mv)
+    g8, g32, gns = _gpu(sc)
+    assert np.all(gns == 0) and np.all(g8 == 0)
+
+
+def test_constant_slab_closed_form_on_gpu(cuda_ok):
+    """The closed form A = 1 - (1-a)^n checked directly on the GPU output."""
+    n = (8, 8, 8)
+    a = float(np.float32(0.05))
+    field = np.full(n[::-1], 42.0, np.float32)
+    sc = make_scene([field], [[("mul", (1.0 / 84.0,))]], [const_lut((0.25, 0.5, 0.75, a))], [1.0],
+                    n, ortho_down_z(n, 8, 8), 8, 8, term=2.0, step=0.5,
+                    clip=[(0.0, 0.0, 1.0, -2.3)])
+    g8, g32, gns = _gpu(sc)
+    assert np.all(gns == 12)
+    np.testing.assert_allclose(g32[..., 3], 1 - (1 - a) ** 12, rtol=0, atol=1e-6)
+
+
+def test_pic_256_1080p_sampled(cuda_ok):
+    """PIConGPU-shaped frame at full size (256^3 + 4 guards, 1920x1080):
+    the whole frame on the GPU, the oracle on sampled pixels."""
+    sc = synth.scene_pic(n=256, guard=4, width=1920, height=1080, seed=0)
+    g8, g32, gns = _gpu(sc)
+    rng = np.random.default_rng(0)
+    hit = np.flatnonzero(gns.reshape(-1) > 0)
+    assert hit.size > 50000
+    pix = np.concatenate([rng.choice(hit, 2500, replace=False),
+                          rng.choice(gns.size, 500, replace=False)])
+    r = oracle.render(sc, pixels=pix)
+    rep = compare(g32, g8, gns, r, sel=pix)
+    assert_parity(rep, 2e-3, "pic 256 1080p sampled")
