@@ -1,0 +1,384 @@
+"""Benchmark of the ISAAC volume ray caster on one B300 (or N replicas).
+
+Workload (default ``pic512``): E and B (3-component) and a density (scalar)
+on 512^3 interior cells + 4 guard cells per side, float32, AoS, the
+PIConGPU-shaped chains, LUTs, weights and clip plane of the multi-source
+configuration, rendered at 1920x1080 with step 0.5 voxel from 32 cameras on a
+Fibonacci sphere at twice the box diagonal.  One step = one frame (the whole
+plain path: ray setup, sampling, chains, classification, blend, compositing,
+quantisation) for the next camera.
+
+Reports ray samples/s (device-timed, CUDA events on the render stream, L2
+flushed between steps), frames/s, an end-to-end figure through the C ABI with
+host-side inputs and the image read back, the roofline of the ray-cast kernel,
+and the FP64 CPU oracle as the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray samples/s & fps at 1080p/512^3; learned+lowprec vs plain at ≤1 LSB; p99 ms"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+
+def make_workload(name):
+    from paper_1611_09048_b300 import synth
+    if name == "pic512":
+        n, W, H = 512, 1920, 1080
+    elif name == "pic256":
+        n, W, H = 256, 1920, 1080
+    elif name == "blobs64":
+        sc = synth.scene_blobs(64, 256, 256, seed=0)
+        cams = [synth.random_orbit_camera((64,) * 3, 256, 256, seed=1000 + i) for i in range(32)]
+        return sc, cams, {"workload": "blobs64_256x256", "n": 64, "guard": 0,
+                          "sources": "blobs(1)", "width": 256, "height": 256}
+    else:
+        raise ValueError(name)
+    sc = synth.scene_pic(n=n, guard=4, width=W, height=H, seed=0)
+    cams = synth.fibonacci_cameras((n, n, n), W, H, count=32, seed=0)
+    cfg = {"workload": f"pic{n}_fp32_{W}x{H}", "n": n, "guard": 4,
+           "sources": "E(3) B(3) rho(1), float32 AoS, zero-copy", "width": W, "height": H,
+           "step": sc.step, "interp": "trilinear", "term_alpha": sc.term, "clip_planes": 1,
+           "cameras": len(cams), "camera_distance": "2x box diagonal, Fibonacci sphere"}
+    return sc, cams, cfg
+
+
+def bytes_per_cell(scene):
+    return sum(4 * s.fdim for i, s in enumerate(scene.sources) if (scene.mask >> i) & 1)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1611_09048_b300 import isaac
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sc, cams, cfg = make_workload(args.workload)
+    ds = isaac.DeviceScene(sc, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    W, H = sc.width, sc.height
+    fb = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+
+    # untimed pre-pass per camera: composited samples and the cells read
+    samples, touched_cells, ray_stats = [], [], []
+    ns = torch.empty((H, W), dtype=torch.int32, device=dev)
+    bits = torch.zeros(ds.footprint_words(), dtype=torch.int32, device=dev)
+    with torch.cuda.stream(stream):
+        for mv, proj in cams:
+            bits.zero_()
+            ds.render(mv, proj, out=fb, nsamples=ns, touched=bits, stream=stream)
+            samples.append(int(ns.sum(dtype=torch.int64).item()))
+            hit = ns[ns > 0].float()
+            ray_stats.append((int(hit.numel()), float(hit.max().item()) if hit.numel() else 0.0))
+            popc = torch.bitwise_and(bits.view(torch.int32).unsqueeze(-1),
+                                     torch.tensor([1 << i for i in range(31)] + [-(1 << 31)],
+                                                  dtype=torch.int32, device=dev)) != 0
+            touched_cells.append(int(popc.sum().item()))
+    del bits
+    torch.cuda.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    prepared = [ds.prepare(mv, proj, out=fb) for mv, proj in cams]
+
+    def frame(i):
+        ds.launch(prepared[i % len(cams)], stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            frame(i)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    # The clock sampler (200 ms period) runs over a window that starts with
+    # >= 1 s of further untimed frames (GPU under the same load) and ends
+    # after the timed steps, so short timed regions still get clock samples.
+    with ClockSampler(local_rank) as clocks:
+        t_pre = time.perf_counter()
+        i = 0
+        while time.perf_counter() - t_pre < args.preroll:
+            with torch.cuda.stream(stream):
+                for _ in range(8):
+                    frame(i)
+                    i += 1
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed")
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()                      # evict L2 between timed frames
+                ev[i][0].record(stream)
+                frame(args.warmup + i)
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        t_wall = time.perf_counter() - t_wall0
+        if world > 1:
+            torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = sum(step_ms)
+    timed_idx = [(args.warmup + i) % len(cams) for i in range(args.steps)]
+    n_samp = sum(samples[j] for j in timed_idx)
+    cells = [touched_cells[j] for j in timed_idx]
+
+    # end to end through the C ABI: host LUTs in, image out, every step
+    luts_host = torch.from_numpy(np.ascontiguousarray(sc.luts, np.float32)).pin_memory()
+    img_host = torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(args.steps):
+            ds.luts.copy_(luts_host, non_blocking=True)
+            frame(args.warmup + i)
+            img_host.copy_(fb, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    # max over ranks
+    vals = torch.tensor([dev_ms, e2e_ms, t_wall], dtype=torch.float64, device=dev)
+    tot = torch.tensor([float(n_samp)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
+    dev_ms, e2e_ms, t_wall = (float(v) for v in vals.tolist())
+    all_samp = float(tot.item())
+    if rank != 0:
+        return None
+
+    hbm_peak, peak_kind = _peaks()
+    bpc = bytes_per_cell(sc)
+    alg_bytes = [c * bpc + W * H * 4 for c in cells]
+    mean_launch_ms = dev_ms / args.steps
+    achieved = (sum(alg_bytes) / args.steps) / (mean_launch_ms * 1e-3) / 1e9
+    traffic = _ncu_traffic(cfg["workload"])
+    res = {
+        "metric": METRIC,
+        "value": all_samp / (dev_ms * 1e-3),
+        "unit": "samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dev_ms / args.steps,
+        "fps": world * args.steps / (dev_ms * 1e-3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded plane-wave E/B fields + log-normal density, PIConGPU-shaped)",
+        "config": dict(cfg, parallelism=f"replicas{world}",
+                       l2="flushed between timed steps (256 MiB write, untimed)",
+                       samples_per_frame_mean=n_samp / args.steps,
+                       hit_rays_per_frame_mean=sum(ray_stats[j][0] for j in timed_idx) / args.steps,
+                       samples_per_ray_max=max(ray_stats[j][1] for j in timed_idx),
+                       cells_read_per_frame_mean=sum(cells) / len(cells)),
+        "wall_s_timed_region": t_wall,
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "kernel": "k_raycast (+ k_fill_background, same render call)",
+                     "algorithmic_bytes": "distinct cells read x 28 B (E,B,rho) + W*H*4 B image"},
+        "e2e": {"value": all_samp / (e2e_ms * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(luts_host.numel() * 4),
+                "d2h_bytes_per_step": int(W * H * 4)},
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_seconds)
+    return res
+
+
+def _ncu_traffic(workload):
+    """DRAM bytes per k_raycast launch from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    return d.get(workload)
+
+
+# ------------------------------------------------------------ CPU oracle arm
+
+def cpu_baseline(sc, cams, budget_s):
+    """The FP64 oracle, as it stands, on the host cores: whole frames of the
+    same workload, camera after camera, until ``budget_s`` seconds of work."""
+    import oracle
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    total, frames = 0, 0
+    for mv, proj in cams:
+        r = oracle.render(sc.with_camera(mv, proj), threads=threads)
+        total += int(r["nsamp"].sum())
+        frames += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": total / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
+            "sample": f"{frames} full {sc.width}x{sc.height} frame(s) of the same workload "
+                      f"({total} samples, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    sc, cams, cfg = make_workload(args.workload)
+    threads = oracle.max_threads()
+    # each step: a bounded sample of one frame -- the centre rows of the image
+    rows = max(1, int(sc.height * args.ref_rows))
+    y0 = (sc.height - rows) // 2
+    pix = np.arange(y0 * sc.width, (y0 + rows) * sc.width, dtype=np.int64)
+
+    def step(i):
+        mv, proj = cams[i % len(cams)]
+        r = oracle.render(sc.with_camera(mv, proj), pixels=pix, threads=threads)
+        return int(r["nsamp"].sum())
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    total = sum(step(args.warmup + i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = total / dt
+    sample = (f"{rows} centre rows x {sc.width} px of each frame ({len(pix)} rays), "
+              f"one camera per step, {total} samples")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, parallelism="cpu"),
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pic512", choices=["pic512", "pic256", "blobs64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-rows", type=float, default=0.25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--preroll", type=float, default=1.0,
+                    help="seconds of untimed frames inside the clock-sampling window")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        res = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

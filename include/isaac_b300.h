@@ -158,6 +158,59 @@ int isaac_render(const isaac_source *sources, const isaac_chain *chains, int32_t
                  const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
                  const isaac_framebuffer *fb, void *stream);
 
+/*
+ * Reduced-precision storage.  Not part of the paper, whose renderer always
+ * reads the application's own arrays (Sec. 3.1 zero copy): these calls make a
+ * packed copy of the active sources when memory bandwidth matters more than
+ * the copy.  One record per cell over the cells [-1, n]^3 holds every packed
+ * source's components in order (guard cells where a source has them, else
+ * the border cell repeated, which is what clamping reads), `pad` components
+ * per record (the next power of two of the component total for the
+ * source lists the library specialises, else 8), stored as:
+ *   ISAAC_F32   float32;
+ *   ISAAC_BF16  bfloat16, round to nearest even;
+ *   ISAAC_F16   IEEE binary16, round to nearest even;
+ *   ISAAC_E4M3  FP8 E4M3 codes of value / scale, round to nearest even,
+ *               saturating at +-448, with one float32 scale per 8^3 brick of
+ *               the [-1, n]^3 box (bricks counted from cell -1) and component:
+ *               scale = absmax / 448 over the brick, 1 for an all-zero brick.
+ * Sampling dequantises to float32 and interpolates, classifies and
+ * composites in float32 exactly as isaac_render does.
+ */
+typedef struct {
+    void *data;              /* device records, owned by the caller */
+    float *scales;           /* device brick scales (E4M3), owned by the caller; else NULL */
+    int64_t n[3];            /* interior cells */
+    int32_t dtype;           /* isaac_dtype */
+    int32_t n_src;           /* packed sources, in their original order */
+    int32_t f_dim[ISAAC_MAX_ACTIVE];
+    int32_t n_comp;          /* sum of f_dim, <= 8 */
+    int32_t pad;             /* components per record: 1, 2, 4 or 8 */
+} isaac_packed;
+
+/* Sizes of the packed copy of the sources selected by `mask` (at most
+ * ISAAC_MAX_ACTIVE, together at most 8 components): fills layout (everything
+ * but data/scales) and the device bytes the caller must provide. */
+int isaac_pack_layout(const isaac_source *sources, int32_t n_sources, uint32_t mask,
+                      const int64_t n[3], int32_t dtype, isaac_packed *layout,
+                      int64_t *data_bytes, int64_t *scale_bytes);
+
+/* Fill the packed copy (one kernel, stream-ordered).  data (16-byte aligned,
+ * data_bytes) and, for E4M3, scales (16-byte aligned, scale_bytes) are
+ * device buffers of at least the sizes isaac_pack_layout reports; sources are
+ * validated as in isaac_render (trilinear reach).  *out describes the copy. */
+int isaac_pack(const isaac_source *sources, int32_t n_sources, uint32_t mask, const int64_t n[3],
+               int32_t dtype, void *data, int64_t data_bytes, float *scales, int64_t scale_bytes,
+               isaac_packed *out, void *stream);
+
+/* isaac_render over a packed copy.  chains, weights (host) and luts (device,
+ * n_src * 256 * 4 floats) are indexed by packed source; opts->n must equal
+ * vol->n and opts->active_mask selects among the packed sources. */
+int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains, const float *luts,
+                        const float *weights, const isaac_camera *camera, const isaac_plane *clip,
+                        int32_t n_clip, const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                        void *stream);
+
 /* Text of the last error reported to the calling thread ("" if none). */
 const char *isaac_last_error(void);
 

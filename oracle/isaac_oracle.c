@@ -564,3 +564,97 @@ void orc_classify_eval(const float *lut, double x, double *rgba)
 {
     orc_classify(lut, x, rgba);
 }
+
+/* ------------------------------------------------- reduced-precision copy */
+
+/* Round x to the nearest value of a binary floating-point format with
+ * `mant` stored mantissa bits, normal exponents down to `emin`, largest finite
+ * value `maxv`; ties to even (the C default rounding mode of nearbyint).
+ * Beyond maxv: +-inf when `saturate` is 0, +-maxv otherwise.  Subnormals keep
+ * the fixed quantum 2^(emin - mant).  Computed in double: every step is exact
+ * for the formats used here (bf16, fp16, e4m3). */
+static double orc_round_format(double x, int mant, int emin, double maxv, int saturate)
+{
+    if (x != x) return x;
+    if (x == 0.0) return x;
+    double ax = fabs(x);
+    int e;
+    frexp(ax, &e);              /* ax = f * 2^e, f in [0.5, 1) -> exponent e - 1 */
+    int ex = e - 1;
+    if (ex < emin) ex = emin;
+    double quantum = ldexp(1.0, ex - mant);
+    double r = nearbyint(ax / quantum) * quantum;
+    if (r > maxv) r = saturate ? maxv : INFINITY;
+    return x < 0 ? -r : r;
+}
+
+enum { ORC_BF16 = 1, ORC_F16 = 2, ORC_E4M3 = 3 };
+
+/* Value a float32 takes after storage in the format (bfloat16: 7 stored
+ * mantissa bits, 8-bit exponent; IEEE binary16: 10 bits, emin -14, max 65504;
+ * E4M3 (OCP fn variant): 3 bits, emin -6, max 448, saturating). */
+float orc_quantize_value(float x, int32_t fmt)
+{
+    switch (fmt) {
+    case ORC_BF16: return (float)orc_round_format((double)x, 7, -126, 3.3895313892515355e38, 0);
+    case ORC_F16: return (float)orc_round_format((double)x, 10, -14, 65504.0, 0);
+    case ORC_E4M3: return (float)orc_round_format((double)x, 3, -6, 448.0, 1);
+    default: return x;
+    }
+}
+
+/* Reduced-precision copy of one source over the cells [-1, n]^3 (a one-cell
+ * apron: guard cells when the source has them, else copies of the border
+ * cell, which is what clamping reads).  out: (n+2)^3 * fdim floats, cell
+ * (x,y,z) component c at ((((z+1)*(ny+2) + y+1)*(nx+2) + x+1)*fdim + c), each
+ * holding the value the stored code represents.  For E4M3 every 8^3 brick of
+ * that apron box (bricks counted from cell -1) and component gets
+ * scale = absmax / 448 (1 if the brick is all zero), computed in float32; the
+ * stored value is quantize(v / scale) * scale, both operations in float32.
+ * scales_out (optional): ceil((n+2)/8)^3 * fdim floats, brick-major. */
+int orc_lowp_copy(const orc_source *s, const int64_t n[3], int32_t fmt, float *out,
+                  float *scales_out)
+{
+    if (!s || !out || s->fdim < 1 || s->fdim > 4) return -1;
+    int64_t P[3] = {n[0] + 2, n[1] + 2, n[2] + 2};
+    int fd = s->fdim;
+    for (int64_t z = 0; z < P[2]; ++z)
+        for (int64_t y = 0; y < P[1]; ++y)
+            for (int64_t x = 0; x < P[0]; ++x) {
+                double v[4];
+                orc_fetch(s, orc_axis_index(x - 1, n[0], s->guard), orc_axis_index(y - 1, n[1], s->guard),
+                          orc_axis_index(z - 1, n[2], s->guard), v);
+                float *o = out + ((z * P[1] + y) * P[0] + x) * fd;
+                for (int c = 0; c < fd; ++c) o[c] = (float)v[c];
+            }
+    if (fmt == ORC_BF16 || fmt == ORC_F16) {
+        int64_t total = P[0] * P[1] * P[2] * fd;
+        for (int64_t i = 0; i < total; ++i) out[i] = orc_quantize_value(out[i], fmt);
+        return 0;
+    }
+    if (fmt != ORC_E4M3) return -1;
+    int64_t B[3] = {(P[0] + 7) / 8, (P[1] + 7) / 8, (P[2] + 7) / 8};
+    for (int64_t bz = 0; bz < B[2]; ++bz)
+        for (int64_t by = 0; by < B[1]; ++by)
+            for (int64_t bx = 0; bx < B[0]; ++bx)
+                for (int c = 0; c < fd; ++c) {
+                    float amax = 0.0f;
+                    for (int64_t z = bz * 8; z < bz * 8 + 8 && z < P[2]; ++z)
+                        for (int64_t y = by * 8; y < by * 8 + 8 && y < P[1]; ++y)
+                            for (int64_t x = bx * 8; x < bx * 8 + 8 && x < P[0]; ++x) {
+                                float a = fabsf(out[((z * P[1] + y) * P[0] + x) * fd + c]);
+                                if (a > amax) amax = a;
+                            }
+                    volatile float scale = amax > 0.0f ? amax / 448.0f : 1.0f;
+                    if (scales_out) scales_out[((bz * B[1] + by) * B[0] + bx) * fd + c] = scale;
+                    for (int64_t z = bz * 8; z < bz * 8 + 8 && z < P[2]; ++z)
+                        for (int64_t y = by * 8; y < by * 8 + 8 && y < P[1]; ++y)
+                            for (int64_t x = bx * 8; x < bx * 8 + 8 && x < P[0]; ++x) {
+                                float *o = &out[((z * P[1] + y) * P[0] + x) * fd + c];
+                                volatile float q = *o / scale;
+                                volatile float deq = orc_quantize_value(q, ORC_E4M3) * scale;
+                                *o = deq;
+                            }
+                }
+    return 0;
+}

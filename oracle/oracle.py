@@ -84,6 +84,11 @@ def _load():
         lib.orc_chain_eval.argtypes = [C.POINTER(_Chain), C.c_void_p, C.c_int32, C.c_void_p]
         lib.orc_classify_eval.restype = None
         lib.orc_classify_eval.argtypes = [C.c_void_p, C.c_double, C.c_void_p]
+        lib.orc_quantize_value.restype = C.c_float
+        lib.orc_quantize_value.argtypes = [C.c_float, C.c_int32]
+        lib.orc_lowp_copy.restype = C.c_int
+        lib.orc_lowp_copy.argtypes = [C.POINTER(_Source), C.c_void_p, C.c_int32, C.c_void_p,
+                                      C.c_void_p]
         _lib = lib
     return _lib
 
@@ -119,6 +124,46 @@ def classify(lut, x: float) -> np.ndarray:
     out = np.zeros(4, np.float64)
     _load().orc_classify_eval(lut.ctypes.data, float(x), out.ctypes.data)
     return out
+
+
+FORMATS = {"bf16": 1, "f16": 2, "e4m3": 3}
+
+
+def quantize(values, fmt: str) -> np.ndarray:
+    """Value each float32 takes after storage in ``fmt`` (bf16, f16, e4m3;
+    round to nearest even; e4m3 saturates at +-448)."""
+    lib = _load()
+    v = np.asarray(values, np.float32).reshape(-1)
+    code = FORMATS[fmt]
+    return np.array([lib.orc_quantize_value(float(x), code) for x in v], np.float32)
+
+
+def lowp_copy(src, n, fmt: str):
+    """Reduced-precision copy of one ``synth.Source`` over cells [-1, n]^3.
+
+    Returns (values, scales): values (nz+2, ny+2, nx+2, fdim) float32 holding
+    what the stored codes represent; scales per 8^3 brick and component for
+    e4m3 (else None)."""
+    lib = _load()
+    data = np.ascontiguousarray(src.data, dtype=np.float32)
+    s = _Source()
+    s.data = data.ctypes.data
+    s.offset = int(src.offset)
+    for a in range(3):
+        s.stride[a] = int(src.strides[a])
+    s.cstride = int(src.cstride)
+    s.fdim = int(src.fdim)
+    s.guard = int(src.guard)
+    nn = np.asarray(n, np.int64)
+    P = [int(k) + 2 for k in n]
+    out = np.zeros((P[2], P[1], P[0], src.fdim), np.float32)
+    B = [(p + 7) // 8 for p in P]
+    scales = np.zeros((B[2], B[1], B[0], src.fdim), np.float32) if fmt == "e4m3" else None
+    rc = lib.orc_lowp_copy(C.byref(s), nn.ctypes.data, FORMATS[fmt], out.ctypes.data,
+                           scales.ctypes.data if scales is not None else None)
+    if rc:
+        raise ValueError("oracle rejected the low-precision copy")
+    return out, scales
 
 
 def _chain(spec, fdim: int) -> _Chain:

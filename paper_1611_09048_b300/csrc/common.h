@@ -1,6 +1,8 @@
 // common.h -- host helpers shared by the library's translation units.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include "isaac_b300.h"
 
 namespace isaac {
@@ -8,6 +10,11 @@ namespace isaac {
 struct KParams;
 struct KSource;
 struct KChain;
+
+using FrameLaunch = void (*)(const KParams &, dim3, cudaStream_t);
+// Fill the background outside the screen rectangle, then launch `fn` over
+// the rectangle's 16x8 tiles (skipped when fn is null or the rectangle empty).
+int launch_with(const KParams &p, FrameLaunch fn, cudaStream_t st);
 
 // Record an error message for isaac_last_error() and return `code`.
 int fail(int code, const char *fmt, ...);

@@ -65,6 +65,12 @@ struct KParams {
     float4 *fb32;
     int *nsamp;
     unsigned *touched;               // optional footprint bitmap over [-1, n]^3
+    // packed (reduced-precision) volume: records over cells [-1, n]^3
+    const unsigned char *rec;        // record of cell (x,y,z) at ((z+1)*PY + y+1)*PX + x+1
+    const float *scales;             // E4M3: per 8^3 brick (from cell -1), `pad` floats
+    int pad;                         // components per record (1, 2, 4 or 8)
+    int bx, by;                      // bricks per axis x, y
+    int comp_off[ISAAC_MAX_ACTIVE];  // first record component of each active source
 };
 
 // Source signature: 4 bits per active source, bits 0-2 = f_dim (0 = read at
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ KParams
 }
 
 // Background for every pixel outside the rectangle the ray kernel covers.
-__global__ void k_fill_background(const __grid_constant__ KParams p)
+static __global__ void k_fill_background(const __grid_constant__ KParams p)
 {
     const size_t total = (size_t)p.W * (size_t)p.H;
     const float T = 1.0f;

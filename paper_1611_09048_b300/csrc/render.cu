@@ -356,22 +356,35 @@ static const LaunchFn k_touch[ISAAC_MAX_ACTIVE][2][2] = {
 };
 #undef ISAAC_T
 
+int launch_with(const KParams &p, FrameLaunch fn, cudaStream_t st)
+{
+    const int fill_blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
+    if (fn) {
+        k_fill_background<<<fill_blocks, 256, 0, st>>>(p);
+    } else {   // nothing to ray cast: the background covers every pixel
+        KParams q = p;
+        q.rx0 = q.rx1 = q.ry0 = q.ry1 = 0;
+        k_fill_background<<<fill_blocks, 256, 0, st>>>(q);
+    }
+    if (fn && p.rx1 > p.rx0 && p.ry1 > p.ry0) {
+        const int tiles_y = (p.ry1 - p.ry0 + 7) / 8;
+        fn(p, dim3((unsigned)(p.tiles_x * tiles_y)), st);
+    }
+    return check_cuda("render launch");
+}
+
 static int launch_frame(const KParams &p, int nact, unsigned sig, bool wide, int interp,
                         cudaStream_t st)
 {
-    const int fill_blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
-    k_fill_background<<<fill_blocks, 256, 0, st>>>(p);
-    if (nact > 0 && p.rx1 > p.rx0 && p.ry1 > p.ry0) {
-        const int tiles_y = (p.ry1 - p.ry0 + 7) / 8;
-        const dim3 grid((unsigned)(p.tiles_x * tiles_y));
-        LaunchFn fn = p.touched ? k_touch[nact - 1][wide ? 1 : 0][interp] : nullptr;
+    LaunchFn fn = nullptr;
+    if (nact > 0) {
+        fn = p.touched ? k_touch[nact - 1][wide ? 1 : 0][interp] : nullptr;
         if (!fn && !wide)
             for (const SigEntry &e : k_sigs)
                 if (e.nact == nact && e.sig == sig) fn = e.fn[interp];
         if (!fn) fn = k_generic[nact - 1][wide ? 1 : 0][interp];
-        fn(p, grid, st);
     }
-    return check_cuda("isaac_render launch");
+    return launch_with(p, fn, st);
 }
 
 // Validate the sources of one call and fill the source part of KParams.

@@ -25,7 +25,8 @@ F32, BF16, F16, E4M3 = 0, 1, 2, 3
 OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 
 # every C symbol declared in include/isaac_b300.h
-EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version")
+EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_layout",
+           "isaac_pack", "isaac_render_packed")
 
 
 class Source(C.Structure):
@@ -62,6 +63,15 @@ class Framebuffer(C.Structure):
                 ("touched", C.c_void_p)]
 
 
+class Packed(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("scales", C.c_void_p), ("n", C.c_int64 * 3),
+                ("dtype", C.c_int32), ("n_src", C.c_int32), ("f_dim", C.c_int32 * MAX_ACTIVE),
+                ("n_comp", C.c_int32), ("pad", C.c_int32)]
+
+
+DTYPES = {"f32": F32, "bf16": BF16, "f16": F16, "e4m3": E4M3}
+
+
 class IsaacError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"isaac error {code}: {msg}")
@@ -84,6 +94,19 @@ def load(path: Optional[str] = None):
         lib.isaac_render.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32, C.c_void_p,
                                      C.c_void_p, C.POINTER(Camera), C.POINTER(Plane), C.c_int32,
                                      C.POINTER(RenderOpts), C.POINTER(Framebuffer), C.c_void_p]
+        lib.isaac_pack_layout.restype = C.c_int
+        lib.isaac_pack_layout.argtypes = [C.POINTER(Source), C.c_int32, C.c_uint32, C.c_void_p,
+                                          C.c_int32, C.POINTER(Packed), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int64)]
+        lib.isaac_pack.restype = C.c_int
+        lib.isaac_pack.argtypes = [C.POINTER(Source), C.c_int32, C.c_uint32, C.c_void_p,
+                                   C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                   C.POINTER(Packed), C.c_void_p]
+        lib.isaac_render_packed.restype = C.c_int
+        lib.isaac_render_packed.argtypes = [C.POINTER(Packed), C.POINTER(Chain), C.c_void_p,
+                                            C.c_void_p, C.POINTER(Camera), C.POINTER(Plane),
+                                            C.c_int32, C.POINTER(RenderOpts),
+                                            C.POINTER(Framebuffer), C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
         lib.isaac_abi_version.restype = C.c_int
         _lib = lib
@@ -196,31 +219,111 @@ class DeviceScene:
         nx, ny, nz = self.scene.n
         return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
 
+    def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
+                touched=None):
+        """Marshal one frame's arguments (camera, opts, framebuffer) once; the
+        returned tuple can be launched repeatedly with ``launch``."""
+        sc = self.scene
+        cam = make_camera(sc.modelview if mv is None else mv,
+                          sc.projection if proj is None else proj, sc.width, sc.height)
+        planes, n_clip = make_planes(sc.clip)
+        fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
+                         nsamples.data_ptr() if nsamples is not None else None,
+                         touched.data_ptr() if touched is not None else None)
+        opts = make_opts(sc, mask)
+        keep = (cam, planes, fb, opts)
+        return (self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
+                C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
+                C.byref(fb)), keep
+
+    @staticmethod
+    def launch(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render(*args, _stream_handle(stream)))
+
     def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
                mask=None, want_f32=False, want_nsamp=False, touched=None):
         """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
         as device tensors."""
         import torch
-        sc = self.scene
-        W, H = sc.width, sc.height
+        W, H = self.scene.width, self.scene.height
         if out is None:
             out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
         if rgba32 is None and want_f32:
             rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         if nsamples is None and want_nsamp:
             nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
+        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched), stream)
+        return out, rgba32, nsamples
+
+
+    # ----------------------------------------------------- packed copies
+
+    def pack(self, dtype="bf16", mask=None, stream=None):
+        """Packed copy of the active sources (device buffers owned by the
+        returned PackedVolume)."""
+        import torch
+        sc = self.scene
+        mask = sc.mask if mask is None else int(mask)
+        n = (C.c_int64 * 3)(*[int(v) for v in sc.n])
+        lay = Packed()
+        db, sb = C.c_int64(), C.c_int64()
+        lib = load()
+        check(lib.isaac_pack_layout(self.sources, len(sc.sources), mask, C.cast(n, C.c_void_p),
+                                    DTYPES[dtype], C.byref(lay), C.byref(db), C.byref(sb)))
+        data = torch.empty(max(16, db.value), dtype=torch.uint8, device=self.device)
+        scales = torch.empty(max(4, sb.value // 4), dtype=torch.float32, device=self.device) \
+            if sb.value else None
+        out = Packed()
+        check(lib.isaac_pack(self.sources, len(sc.sources), mask, C.cast(n, C.c_void_p),
+                             DTYPES[dtype], data.data_ptr(), db.value,
+                             scales.data_ptr() if scales is not None else None, sb.value,
+                             C.byref(out), _stream_handle(stream)))
+        srcs = [s for i, s in enumerate(range(len(sc.sources))) if (mask >> i) & 1]
+        return PackedVolume(self, out, data, scales, srcs)
+
+
+class PackedVolume:
+    """A packed (reduced-precision) copy of a DeviceScene's active sources."""
+
+    def __init__(self, ds, desc, data, scales, src_index):
+        self.ds, self.desc, self.data, self.scales = ds, desc, data, scales
+        self.src_index = src_index      # original source index of each packed source
+        n = len(src_index)
+        self.chains = (Chain * n)(*[ds.chains[i] for i in src_index])
+        self.weights = (C.c_float * n)(*[ds.weights[i] for i in src_index])
+        self.luts = ds.luts[src_index].contiguous()
+
+    def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
+                touched=None):
+        sc = self.ds.scene
         cam = make_camera(sc.modelview if mv is None else mv,
-                          sc.projection if proj is None else proj, W, H)
+                          sc.projection if proj is None else proj, sc.width, sc.height)
         planes, n_clip = make_planes(sc.clip)
         fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
-                         nsamples.data_ptr() if nsamples is not None else None,
-                         touched.data_ptr() if touched is not None else None)
-        opts = make_opts(sc, mask)
-        rc = load().isaac_render(self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
-                                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip,
-                                 C.byref(opts), C.byref(fb), _stream_handle(stream))
-        check(rc)
-        return out, rgba32, nsamples
+                         nsamples.data_ptr() if nsamples is not None else None, None)
+        opts = make_opts(sc, (1 << len(self.src_index)) - 1 if mask is None else mask)
+        keep = (cam, planes, fb, opts)
+        return (C.byref(self.desc), self.chains, self.luts.data_ptr(),
+                C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
+                C.byref(fb)), keep
+
+    @staticmethod
+    def launch(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render_packed(*args, _stream_handle(stream)))
+
+    def render(self, mv=None, proj=None, out=None, stream=None, mask=None, want_f32=False,
+               want_nsamp=False):
+        import torch
+        W, H = self.ds.scene.width, self.ds.scene.height
+        dev = self.ds.device
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
+        self.launch(self.prepare(mv, proj, out, f32, ns, mask), stream)
+        return out, f32, ns
 
 
 def render(scene, **kw):
