@@ -225,6 +225,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
+    variants = {} if args.no_variants else \
+        run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
+
     # max over ranks
     vals = torch.tensor([dev_ms, e2e_ms, t_wall], dtype=torch.float64, device=dev)
     tot = torch.tensor([float(n_samp)], dtype=torch.float64, device=dev)
@@ -273,10 +276,70 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(luts_host.numel() * 4),
                 "d2h_bytes_per_step": int(W * H * 4)},
         "clocks": clocks.summary(),
+        "variants": variants,
     }
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_seconds)
     return res
+
+
+def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
+    """Packed copies (FP32, BF16, FP16, E4M3) of the same sources: pack time,
+    samples/s over the same cameras, and the 8-bit difference to the FP32
+    zero-copy frame (mean and max LSB over the image's hit pixels)."""
+    import torch
+    out = {}
+    W, H = ds.scene.width, ds.scene.height
+    n_cam = len(cams)
+    steps = min(args.steps, 4 * n_cam)
+    ref_imgs = []
+    with torch.cuda.stream(stream):
+        for j in range(n_cam):
+            ds.launch(prepared_f32[j], stream)
+            ref_imgs.append(fb_f32.clone())
+    torch.cuda.synchronize()
+    for fmt in ("f32", "bf16", "f16", "e4m3"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0.record(stream)
+        pv = ds.pack(fmt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pack_ms = e0.elapsed_time(e1)
+        fb = torch.empty_like(fb_f32)
+        prep = [pv.prepare(mv, proj, out=fb) for mv, proj in cams]
+        lsb_sum, lsb_max, npx = 0.0, 0, 0
+        with torch.cuda.stream(stream):
+            for j in range(n_cam):
+                pv.launch(prep[j], stream)
+                d = (fb.to(torch.int16) - ref_imgs[j].to(torch.int16)).abs()
+                hit = ref_imgs[j][..., 3] > 0
+                lsb_sum += float(d[hit].float().sum().item())
+                lsb_max = max(lsb_max, int(d.max().item()))
+                npx += int(hit.sum().item()) * 4
+            for i in range(args.warmup):
+                pv.launch(prep[i % n_cam], stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                pv.launch(prep[(args.warmup + i) % n_cam], stream)
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        ns = sum(samples[(args.warmup + i) % n_cam] for i in range(steps))
+        out[fmt] = {"samples_per_s": ns / (ms * 1e-3), "ms_per_frame": ms / steps,
+                    "pack_ms": pack_ms, "bytes": int(pv.data.numel()) +
+                    (int(pv.scales.numel()) * 4 if pv.scales is not None else 0),
+                    "lsb_vs_f32_mean": lsb_sum / max(1, npx), "lsb_vs_f32_max": lsb_max,
+                    "steps": steps}
+        del pv, prep
+        torch.cuda.empty_cache()
+    return out
 
 
 def _ncu_traffic(workload):
@@ -355,6 +418,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rows", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the packed-copy variants (FP32/BF16/FP16/E4M3)")
     ap.add_argument("--preroll", type=float, default=1.0,
                     help="seconds of untimed frames inside the clock-sampling window")
     args = ap.parse_args()

@@ -116,6 +116,9 @@ typedef struct {
     float term_alpha;        /* a ray stops once its opacity A >= term_alpha; > 1 disables */
     float bg[4];             /* background RGBA (premultiplied) blended behind the volume */
     uint32_t active_mask;    /* bit s set: source s is rendered (Sec. 3.2) */
+    int32_t lanes_per_ray;   /* 0 = automatic, else 1, 2 or 4 threads cooperating on one
+                                ray; a hint (the nearest compiled variant is used) that
+                                never changes the image, only the speed */
 } isaac_render_opts;
 
 /* Output buffers (device, owned by the caller), row-major, row 0 at the top. */
@@ -152,6 +155,12 @@ typedef struct {
  *       structs, read before the call returns; the caller may reuse them.
  * stream: cudaStream_t to order the work on (NULL = legacy default stream).
  * The current CUDA device must own every device pointer.
+ * Workspace: the library keeps one device workspace per (device, stream) for
+ * the frame's ray list (32 bytes per pixel of the screen rectangle the box can
+ * cover, plus 256 bytes), allocated on first use and grown (after
+ * synchronising that stream) when a larger rectangle comes; frames on one
+ * stream share it in order, frames on different streams never share.
+ * isaac_release_workspaces() frees them; ISAAC_ENOMEM if allocation fails.
  */
 int isaac_render(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
                  const float *luts, const float *weights, const isaac_camera *camera,
@@ -210,6 +219,26 @@ int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains, cons
                         const float *weights, const isaac_camera *camera, const isaac_plane *clip,
                         int32_t n_clip, const isaac_render_opts *opts, const isaac_framebuffer *fb,
                         void *stream);
+
+/*
+ * isaac_opacity_grid -- the max-opacity grid over macro cells of `cell`^3
+ * cells (a coarse map of where the transfer functions make the volume
+ * visible; the paper has no such structure, it serves empty-space skipping
+ * and the learned interval proposal).  Macro cell (i,j,k) covers the cells
+ * [i*cell-1, (i+1)*cell] per axis, clipped to [-1, n] (the apron trilinear
+ * samples inside it read); its value is the largest blended opacity
+ * clamp(sum_s weights[s] * LUT_s(chain_s(v_s)).alpha, 0, 1) over those cells,
+ * each active source read at the cell itself (clamped without guards).
+ * grid: device, ceil(n/cell) values per axis, x fastest; grid_len its length.
+ * Sources, chains, luts, weights and opts (n, active_mask) as in
+ * isaac_render.
+ */
+int isaac_opacity_grid(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                       const float *luts, const float *weights, const isaac_render_opts *opts,
+                       int32_t cell, float *grid, int64_t grid_len, void *stream);
+
+/* Free the render workspaces of the current device (synchronises the device). */
+int isaac_release_workspaces(void);
 
 /* Text of the last error reported to the calling thread ("" if none). */
 const char *isaac_last_error(void);

@@ -548,6 +548,60 @@ int orc_max_threads(void)
 #endif
 }
 
+/* Max-opacity grid.  Macro cell (i, j, k) of `cell`^3 cells covers the cells
+ * [i*cell - 1, (i+1)*cell] per axis (a one-cell apron, what trilinear
+ * samples inside the macro cell read), clipped to [-1, n]; its value is the
+ * largest blended opacity clamp(sum_s w_s * LUT_s(chain_s(v_s)).alpha, 0, 1)
+ * over those cells, each source read at the cell itself (clamped to the
+ * border when it has no guard cells).  grid: ceil(n/cell) per axis, x fastest. */
+int orc_opacity_grid(const orc_source *src, const orc_chain *ch, const float *luts,
+                     const double *w, int32_t n_src, const int64_t n[3], uint32_t mask,
+                     int32_t cell, double *grid, int32_t n_threads)
+{
+    if (!src || !ch || !luts || !w || !grid || cell < 1 || n_src < 1 || n_src > ORC_MAX_SRC)
+        return -1;
+    for (int s = 0; s < n_src; ++s)
+        if (((mask >> s) & 1u) && (src[s].fdim < 1 || src[s].fdim > 4 || orc_chain_check(&ch[s], src[s].fdim)))
+            return -1;
+    int64_t G[3] = {(n[0] + cell - 1) / cell, (n[1] + cell - 1) / cell, (n[2] + cell - 1) / cell};
+    int64_t total = G[0] * G[1] * G[2];
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(n_threads)
+#endif
+    for (int64_t g = 0; g < total; ++g) {
+        int64_t gi = g % G[0], gj = (g / G[0]) % G[1], gk = g / (G[0] * G[1]);
+        int64_t lo[3] = {gi * cell - 1, gj * cell - 1, gk * cell - 1};
+        int64_t hi[3] = {(gi + 1) * cell, (gj + 1) * cell, (gk + 1) * cell};
+        for (int a = 0; a < 3; ++a) {
+            if (lo[a] < -1) lo[a] = -1;
+            if (hi[a] > n[a]) hi[a] = n[a];
+        }
+        double best = 0.0;
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                    double a = 0.0;
+                    for (int s = 0; s < n_src; ++s) {
+                        if (!((mask >> s) & 1u)) continue;
+                        double v[4];
+                        orc_fetch(&src[s], orc_axis_index(x, n[0], src[s].guard),
+                                  orc_axis_index(y, n[1], src[s].guard),
+                                  orc_axis_index(z, n[2], src[s].guard), v);
+                        double rgba[4];
+                        orc_classify(luts + (size_t)s * 256 * 4, orc_chain_apply(&ch[s], v, src[s].fdim), rgba);
+                        a += w[s] * rgba[3];
+                    }
+                    if (!(a >= 0.0)) a = 0.0;
+                    if (a > 1.0) a = 1.0;
+                    if (a > best) best = a;
+                }
+        grid[g] = best;
+    }
+    (void)n_threads;
+    return 0;
+}
+
 /* Test hook: apply a functor chain to one value of dimension dim (Sec. 3.3).
  * Returns 0, or -1 if the chain is invalid for that dimension. */
 int orc_chain_eval(const orc_chain *ch, const double *v_in, int32_t dim, double *out)
@@ -627,6 +681,7 @@ int orc_lowp_copy(const orc_source *s, const int64_t n[3], int32_t fmt, float *o
                 float *o = out + ((z * P[1] + y) * P[0] + x) * fd;
                 for (int c = 0; c < fd; ++c) o[c] = (float)v[c];
             }
+    if (fmt == 0) return 0;   /* float32 copy: values as stored */
     if (fmt == ORC_BF16 || fmt == ORC_F16) {
         int64_t total = P[0] * P[1] * P[2] * fd;
         for (int64_t i = 0; i < total; ++i) out[i] = orc_quantize_value(out[i], fmt);

@@ -86,6 +86,10 @@ def _load():
         lib.orc_classify_eval.argtypes = [C.c_void_p, C.c_double, C.c_void_p]
         lib.orc_quantize_value.restype = C.c_float
         lib.orc_quantize_value.argtypes = [C.c_float, C.c_int32]
+        lib.orc_opacity_grid.restype = C.c_int
+        lib.orc_opacity_grid.argtypes = [C.POINTER(_Source), C.POINTER(_Chain), C.c_void_p,
+                                         C.c_void_p, C.c_int32, C.c_void_p, C.c_uint32,
+                                         C.c_int32, C.c_void_p, C.c_int32]
         lib.orc_lowp_copy.restype = C.c_int
         lib.orc_lowp_copy.argtypes = [C.POINTER(_Source), C.c_void_p, C.c_int32, C.c_void_p,
                                       C.c_void_p]
@@ -126,7 +130,39 @@ def classify(lut, x: float) -> np.ndarray:
     return out
 
 
-FORMATS = {"bf16": 1, "f16": 2, "e4m3": 3}
+def opacity_grid(scene, cell: int = 16, threads: int = 0, mask=None) -> np.ndarray:
+    """Max-opacity grid of ``scene``'s active sources, shape
+    (ceil(nz/cell), ceil(ny/cell), ceil(nx/cell)), float64."""
+    lib = _load()
+    n_src = len(scene.sources)
+    srcs = (_Source * n_src)()
+    chains = (_Chain * n_src)()
+    keep = []
+    for s, src in enumerate(scene.sources):
+        data = np.ascontiguousarray(src.data, dtype=np.float32)
+        keep.append(data)
+        srcs[s].data = data.ctypes.data
+        srcs[s].offset = int(src.offset)
+        for a in range(3):
+            srcs[s].stride[a] = int(src.strides[a])
+        srcs[s].cstride = int(src.cstride)
+        srcs[s].fdim = int(src.fdim)
+        srcs[s].guard = int(src.guard)
+        chains[s] = _chain(scene.chains[s], src.fdim)
+    luts = np.ascontiguousarray(scene.luts, dtype=np.float32).reshape(n_src, 256, 4)
+    w = np.ascontiguousarray(scene.weights, dtype=np.float64).reshape(n_src)
+    n = np.asarray(scene.n, np.int64)
+    G = [(int(k) + cell - 1) // cell for k in scene.n]
+    out = np.zeros((G[2], G[1], G[0]), np.float64)
+    rc = lib.orc_opacity_grid(srcs, chains, luts.ctypes.data, w.ctypes.data, n_src, n.ctypes.data,
+                              int(scene.mask if mask is None else mask), int(cell),
+                              out.ctypes.data, int(threads))
+    if rc:
+        raise ValueError("oracle rejected the opacity-grid request")
+    return out
+
+
+FORMATS = {"f32": 0, "bf16": 1, "f16": 2, "e4m3": 3}
 
 
 def quantize(values, fmt: str) -> np.ndarray:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "isaac_b300.h"
+#include "kernel_table.h"
 
 namespace isaac {
 
@@ -11,14 +12,10 @@ struct KParams;
 struct KSource;
 struct KChain;
 
-using FrameLaunch = void (*)(const KParams &, dim3, cudaStream_t);
-// Fill the background outside the screen rectangle, then launch `fn` over
-// the rectangle's 16x8 tiles (skipped when fn is null or the rectangle empty).
-int launch_with(const KParams &p, FrameLaunch fn, cudaStream_t st);
-
 // Record an error message for isaac_last_error() and return `code`.
 int fail(int code, const char *fmt, ...);
 void clear_error();
+const char *last_error();
 // Turn the last CUDA error (if any) into ISAAC_ECUDA.
 int check_cuda(const char *what);
 
@@ -28,5 +25,12 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
                    int elem, KSource &ks, unsigned *nib, bool *wide);
 int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
 int prepare_fb(const isaac_framebuffer *fb, KParams &p);
+
+// Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic).
+int choose_lanes(long long rect_pixels, int hint);
+// Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays.
+int bind_workspace(KParams &p, cudaStream_t st);
+// Background + ray setup + march kernel `fn` (null: background only).
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st);
 
 }  // namespace isaac

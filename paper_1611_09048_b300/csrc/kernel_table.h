@@ -1,0 +1,29 @@
+// kernel_table.h -- host-side view of the precompiled frame kernels.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+namespace isaac {
+
+struct KParams;
+using FrameLaunch = void (*)(const KParams &, dim3, cudaStream_t);
+
+struct ZcEntry {
+    int nact;
+    unsigned sig;        // 0 = generic (run-time f_dim)
+    int interp;
+    int rl;              // lanes per ray
+    bool wide;           // 64-bit element offsets
+    bool touch;          // records the footprint bitmap
+    FrameLaunch fn;
+};
+
+extern const ZcEntry *const k_zc_entries;
+extern const int k_n_zc_entries;
+
+void launch_fill(const KParams &p, cudaStream_t st);
+void launch_setup(const KParams &p, cudaStream_t st);
+
+}  // namespace isaac

@@ -365,6 +365,24 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
     const int x0 = min(max(g.ix, -1), p.nx) + 1, x1 = min(max(g.ix + 1, -1), p.nx) + 1;
     const int y0 = min(max(g.iy, -1), p.ny) + 1, y1 = min(max(g.iy + 1, -1), p.ny) + 1;
     const int z0 = min(max(g.iz, -1), p.nz) + 1, z1 = min(max(g.iz + 1, -1), p.nz) + 1;
+    if constexpr (DT == ISAAC_E4M3) {
+        // each corner may lie in another brick: accumulate weight * scale * code
+        // corner by corner (keeps one corner's record live at a time)
+#pragma unroll
+        for (int q = 0; q < PAD; ++q) v[q] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = (k & 1) ? x1 : x0, y = (k & 2) ? y1 : y0, z = (k & 4) ? z1 : z0;
+            const float w = ((k & 1) ? g.fx : 1.0f - g.fx) * ((k & 2) ? g.fy : 1.0f - g.fy) *
+                            ((k & 4) ? g.fz : 1.0f - g.fz);
+            float cv[PAD], s[PAD];
+            IO::load(p.rec, ((long long)z * PY + y) * PX + x, cv);
+            load_scales<PAD>(p.scales, ((long long)(z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
+#pragma unroll
+            for (int q = 0; q < PAD; ++q) v[q] = fmaf(w * s[q], cv[q], v[q]);
+        }
+        return;
+    }
     float c[8][PAD];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -385,65 +403,29 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
     }
 }
 
-// SIG != 0: the first NACT packed sources with compile-time f_dim are all
-// active.  SIG == 0: run-time f_dim and record offsets for NACT sources.
+// Blended RGBA of one sample of the packed copy.  SIG != 0: the NACT packed
+// sources with compile-time f_dim (inactive ones carry weight 0).  SIG == 0:
+// run-time f_dim and record offsets.
 template <int NACT, unsigned SIG, int DT, int PAD, int INTERP>
-__global__ void __launch_bounds__(128) k_raycast_packed(const __grid_constant__ KParams p)
-{
-    __shared__ float4 s_lut[NACT * 256];
-    for (int i = threadIdx.x; i < NACT * 256; i += blockDim.x) s_lut[i] = __ldg(p.lut[i >> 8] + (i & 255));
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ty = blockIdx.x / p.tiles_x, tx = blockIdx.x - ty * p.tiles_x;
-    const int px = p.rx0 + tx * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = p.ry0 + ty * 8 + (warp >> 1) * 4 + (lane >> 3);
-    if (px >= p.rx1 || py >= p.ry1) return;
-
-    const Ray ray = setup_ray(p, px, py);
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-    int ns = 0;
-    for (int k = 0; k < ray.nsteps; ++k) {
-        const float s = (float)k * p.step;
-        const float x = fmaf(s, ray.dx, ray.ex);
-        const float y = fmaf(s, ray.dy, ray.ey);
-        const float z = fmaf(s, ray.dz, ray.ez);
-        Geo g;
-        if (INTERP) {
-            const float qx = x - 0.5f, qy = y - 0.5f, qz = z - 0.5f;
-            const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
-            g.ix = (int)flx;
-            g.iy = (int)fly;
-            g.iz = (int)flz;
-            g.fx = qx - flx;
-            g.fy = qy - fly;
-            g.fz = qz - flz;
-        } else {
-            g.ix = (int)floorf(x);
-            g.iy = (int)floorf(y);
-            g.iz = (int)floorf(z);
-            g.fx = g.fy = g.fz = 0.0f;
-        }
+struct PackedShader {
+    __device__ __forceinline__ static float4 shade(const KParams &p, const float4 *s_lut, float x,
+                                                   float y, float z)
+    {
+        const Geo g = sample_geo<INTERP>(x, y, z);
         float v[PAD];
         sample_packed<DT, PAD, INTERP>(p, g, v);
         float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         shade_packed_all<SIG, PAD>(p, v, s_lut, acc, std::make_integer_sequence<int, NACT>{});
-        const float a = clamp01(acc.w);
-        const float t = (1.0f - A) * a;
-        C0 = fmaf(t, acc.x, C0);
-        C1 = fmaf(t, acc.y, C1);
-        C2 = fmaf(t, acc.z, C2);
-        A += t;
-        ++ns;
-        if (A >= p.term) break;
+        return acc;
     }
-    const float T = 1.0f - A;
-    const float o0 = fmaf(T, p.bg[0], C0), o1 = fmaf(T, p.bg[1], C1);
-    const float o2 = fmaf(T, p.bg[2], C2), o3 = fmaf(T, p.bg[3], A);
-    const size_t pix = (size_t)py * (size_t)p.W + (size_t)px;
-    p.fb8[pix] = make_uchar4(quant8(o0), quant8(o1), quant8(o2), quant8(o3));
-    if (p.fb32) p.fb32[pix] = make_float4(o0, o1, o2, o3);
-    if (p.nsamp) p.nsamp[pix] = ns;
+};
+
+template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL>
+__global__ void __launch_bounds__(128, 8) k_raycast_packed(const __grid_constant__ KParams p)
+{
+    __shared__ float4 s_lut[NACT * 256];
+    load_luts<NACT>(p, s_lut);
+    march<NACT, PackedShader<NACT, SIG, DT, PAD, INTERP>, RL>(p, s_lut);
 }
 
 // ------------------------------------------------------------- dispatch
@@ -451,14 +433,23 @@ __global__ void __launch_bounds__(128) k_raycast_packed(const __grid_constant__ 
 using PackedLaunch = void (*)(const KParams &, dim3, cudaStream_t);
 using PackLaunch = void (*)(const KPack &, cudaStream_t);
 
-// Specialised signatures of the packed path (f_dim per source, all active).
+// Specialised signatures of the packed path (f_dim per packed source).
 constexpr unsigned k_packed_sigs[] = {0x1u, 0x3u, 0x11u, 0x31u, 0x33u, 0x133u};
 constexpr int k_n_packed_sigs = 6;
 
+struct PackedEntry {
+    int nact;
+    unsigned sig;        // 0 = generic (pad 8)
+    int pad;
+    int interp;
+    int rl;
+    PackedLaunch fn;
+};
+
 struct PackedTable {
-    PackedLaunch sig[k_n_packed_sigs][2];          // [sig][interp], pad = next_pow2(ncomp)
-    PackedLaunch generic[ISAAC_MAX_ACTIVE][4][2];  // [nact-1][log2 pad][interp]
-    PackLaunch pack[4];                            // [log2 pad]
+    const PackedEntry *entries;
+    int n_entries;
+    PackLaunch pack[4];  // [log2 pad]
 };
 
 }  // namespace isaac

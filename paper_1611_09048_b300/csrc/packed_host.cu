@@ -2,6 +2,8 @@
 // isaac_pack_layout, isaac_pack, isaac_render_packed.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <cmath>
 #include <cstring>
 
 #include "common.h"
@@ -188,18 +190,24 @@ extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *c
     rc = prepare_fb(fb, p);
     if (rc) return rc;
     if (!luts || ((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
-    int nact = 0, off = 0;
+    // Every packed source is evaluated (its components share the record); an
+    // inactive one gets an identity chain and weight 0, which adds exactly +0.
+    int off = 0;
     for (int s = 0; s < vol->n_src; ++s) {
-        if ((opts->active_mask >> s) & 1u) {
+        const bool on = (opts->active_mask >> s) & 1u;
+        if (on) {
             if (!std::isfinite(weights[s])) return fail(ISAAC_EINVAL, "weight %d is not finite", s);
-            rc = compile_chain(chains[s], vol->f_dim[s], s, p.ch[nact]);
+            rc = compile_chain(chains[s], vol->f_dim[s], s, p.ch[s]);
             if (rc) return rc;
-            p.src[nact].fdim = vol->f_dim[s];
-            p.src[nact].w = weights[s];
-            p.comp_off[nact] = off;
-            p.lut[nact] = reinterpret_cast<const float4 *>(luts) + (size_t)s * 256;
-            ++nact;
+        } else {
+            isaac_chain none;
+            memset(&none, 0, sizeof none);
+            compile_chain(none, vol->f_dim[s], s, p.ch[s]);
         }
+        p.src[s].fdim = vol->f_dim[s];
+        p.src[s].w = on ? weights[s] : 0.0f;
+        p.comp_off[s] = off;
+        p.lut[s] = reinterpret_cast<const float4 *>(luts) + (size_t)s * 256;
         off += vol->f_dim[s];
     }
     p.rec = static_cast<const unsigned char *>(vol->data);
@@ -208,14 +216,25 @@ extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *c
     p.bx = (int)((vol->n[0] + 9) / 8);
     p.by = (int)((vol->n[1] + 9) / 8);
 
-    const int all = (1 << vol->n_src) - 1;
-    const int si = sig_index(packed_sig(vol->f_dim, vol->n_src));
     PackedLaunch fn = nullptr;
-    if (nact > 0) {
-        if ((int)opts->active_mask == all && si >= 0 && vol->pad == next_pow2(nc))
-            fn = T->sig[si][opts->interp];
-        else
-            fn = T->generic[nact - 1][log2i(vol->pad)][opts->interp];
+    int rl = 1;
+    if (opts->active_mask != 0) {
+        const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+        const int want = choose_lanes(rect, opts->lanes_per_ray);
+        const unsigned sig = packed_sig(vol->f_dim, vol->n_src);
+        const bool spec = sig_index(sig) >= 0 && vol->pad == next_pow2(nc);
+        const PackedEntry *best = nullptr;
+        for (int i = 0; i < T->n_entries; ++i) {
+            const PackedEntry &e = T->entries[i];
+            if (e.nact != vol->n_src || e.interp != opts->interp || e.pad != vol->pad) continue;
+            if (e.sig != (spec ? sig : 0u)) continue;
+            if (!best || e.rl == want ||
+                (best->rl != want && std::abs(e.rl - want) < std::abs(best->rl - want)))
+                best = &e;
+        }
+        if (!best) return fail(ISAAC_ENOTSUP, "no packed kernel for this layout");
+        fn = best->fn;
+        rl = best->rl;
     }
-    return launch_with(p, fn, (cudaStream_t)stream);
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream);
 }

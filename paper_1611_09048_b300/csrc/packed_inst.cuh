@@ -5,10 +5,10 @@
 
 namespace isaac {
 
-template <int NACT, unsigned SIG, int DT, int PAD, int INTERP>
+template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL>
 static void launch_packed(const KParams &p, dim3 grid, cudaStream_t st)
 {
-    k_raycast_packed<NACT, SIG, DT, PAD, INTERP><<<grid, 128, 0, st>>>(p);
+    k_raycast_packed<NACT, SIG, DT, PAD, INTERP, RL><<<grid, 128, 0, st>>>(p);
 }
 
 template <int DT, int PAD>
@@ -23,23 +23,24 @@ static void launch_pack(const KPack &p, cudaStream_t st)
     }
 }
 
-#define ISAAC_S(N, S, P) {launch_packed<N, S, ISAAC_DT, P, 0>, launch_packed<N, S, ISAAC_DT, P, 1>}
-#define ISAAC_G(N)                                                                          \
-    {{launch_packed<N, 0u, ISAAC_DT, 1, 0>, launch_packed<N, 0u, ISAAC_DT, 1, 1>},           \
-     {launch_packed<N, 0u, ISAAC_DT, 2, 0>, launch_packed<N, 0u, ISAAC_DT, 2, 1>},           \
-     {launch_packed<N, 0u, ISAAC_DT, 4, 0>, launch_packed<N, 0u, ISAAC_DT, 4, 1>},           \
-     {launch_packed<N, 0u, ISAAC_DT, 8, 0>, launch_packed<N, 0u, ISAAC_DT, 8, 1>}}
+// {nact, sig, pad, interp, rl, launcher}; pad of a specialised signature is
+// next_pow2(component total), the generic kernels use pad 8.
+#define ISAAC_E(N, S, P, I, R) {N, S, P, I, R, launch_packed<N, S, ISAAC_DT, P, I, R>}
+#define ISAAC_E2(N, S, P, R) ISAAC_E(N, S, P, 0, R), ISAAC_E(N, S, P, 1, R)
+static const PackedEntry k_entries[] = {
+    ISAAC_E2(1, 0x1u, 1, 1), ISAAC_E2(1, 0x1u, 1, 2), ISAAC_E2(1, 0x1u, 1, 4),
+    ISAAC_E2(1, 0x3u, 4, 2), ISAAC_E2(2, 0x11u, 2, 2), ISAAC_E2(2, 0x31u, 4, 2),
+    ISAAC_E2(2, 0x33u, 8, 2),
+    ISAAC_E2(3, 0x133u, 8, 1), ISAAC_E2(3, 0x133u, 8, 2), ISAAC_E2(3, 0x133u, 8, 4),
+    ISAAC_E2(1, 0u, 8, 2), ISAAC_E2(2, 0u, 8, 2), ISAAC_E2(3, 0u, 8, 2), ISAAC_E2(4, 0u, 8, 2),
+};
+#undef ISAAC_E2
+#undef ISAAC_E
 
 extern const PackedTable ISAAC_TABLE = {
-    // order of k_packed_sigs: {1}, {3}, {1,1}, {3,1}, {3,3}, {3,3,1}; pad = next_pow2(ncomp)
-    {ISAAC_S(1, 0x1u, 1), ISAAC_S(1, 0x3u, 4), ISAAC_S(2, 0x11u, 2), ISAAC_S(2, 0x31u, 4),
-     ISAAC_S(2, 0x33u, 8), ISAAC_S(3, 0x133u, 8)},
-    {ISAAC_G(1), ISAAC_G(2), ISAAC_G(3), ISAAC_G(4)},
+    k_entries, (int)(sizeof(k_entries) / sizeof(k_entries[0])),
     {launch_pack<ISAAC_DT, 1>, launch_pack<ISAAC_DT, 2>, launch_pack<ISAAC_DT, 4>,
      launch_pack<ISAAC_DT, 8>},
 };
-
-#undef ISAAC_S
-#undef ISAAC_G
 
 }  // namespace isaac

@@ -1,13 +1,26 @@
 // raycast.cuh -- device code of the FP32 volume ray caster (sm_103a).
 //
-// One thread per pixel/ray (Sec. 3.2: "for every scan point ... iterates over
-// all sources ..."), warps cover 8x4-pixel patches so that neighbouring rays
-// walk neighbouring cells, LUTs of the active sources sit in shared memory,
-// functor chains and source descriptors are read from the kernel's constant
-// parameter block (Sec. 3.3 keeps chains and their parameters in constant
-// memory for the same reason).  The per-source loop is unrolled at compile
-// time (Sec. 3.2) over a compacted list of the active sources, so inactive
-// sources are never touched.
+// A frame runs in three kernels on the caller's stream:
+//   k_fill_background  background for every pixel outside the screen
+//                      rectangle the box can cover; resets the workspace
+//                      counters;
+//   k_setup_rays       one thread per rectangle pixel: the ray in FP64 (camera
+//                      unprojection, global/local box and clip-plane interval,
+//                      first and last sample on the global grid); misses write
+//                      the background, hits are appended to a compact ray list
+//                      in the workspace (warp-aggregated, so a chunk of the list
+//                      is one 8x4 pixel patch);
+//   k_raycast          persistent warps pull chunks of the ray list (dynamic
+//                      load balance); RL lanes share one ray and evaluate RL
+//                      consecutive samples at once, which are then composited
+//                      in order (Sec. 3.2: read -> functor chain -> classify ->
+//                      blend -> classical front to back), so the image does not
+//                      depend on RL.
+// LUTs of the active sources sit in shared memory; chains and source
+// descriptors are read from the kernel's constant parameter block (Sec. 3.3
+// keeps chains and their parameters in constant memory).  The per-source loop
+// is unrolled at compile time over the compacted active sources (Sec. 3.2), so
+// inactive sources are never touched.
 #pragma once
 
 #include <cstdint>
@@ -18,14 +31,17 @@
 
 namespace isaac {
 
-// Internal functor codes: the public ones plus SQRT (POW with every
-// exponent 1/2, rewritten on the host).
-enum : int { K_ADD = 1, K_MUL = 2, K_LENGTH = 3, K_SUM = 4, K_POW = 5, K_LOG = 6, K_SQRT = 7 };
+// Internal functor codes: the public ones, SQRT (POW with every exponent 1/2)
+// and AFFINE (a run of ADD/MUL folded into one a*x+b per component).
+enum : int {
+    K_ADD = 1, K_MUL = 2, K_LENGTH = 3, K_SUM = 4, K_POW = 5, K_LOG = 6, K_SQRT = 7, K_AFFINE = 8
+};
 
 struct KOp {
     int code;
     int dim;          // dimension of the value the op consumes
-    float a[4];       // arguments, scalar already broadcast
+    float a[4];       // arguments (scalar already broadcast); AFFINE: scale
+    float b[4];       // AFFINE: offset
 };
 
 struct KChain {
@@ -42,6 +58,21 @@ struct KSource {
     float w;             // blend weight
 };
 
+// One entry of the compact ray list.
+struct RayRec {
+    float ex, ey, ez;    // local voxel position of the first sample
+    int nsteps;          // samples on the global grid inside [t_in, t_out)
+    float dx, dy, dz;    // unit direction
+    int pix;             // y * W + x
+};
+
+// Workspace: counters, then the ray list (one record per rectangle pixel at most).
+constexpr int kWsHeader = 256;
+struct WsCounters {
+    unsigned n_rays;     // appended by k_setup_rays
+    unsigned next;       // next list entry to march (k_raycast)
+};
+
 struct KParams {
     double minv[16];                 // inverse of projection * modelview, column-major
     double half_g[3];                // global_n / 2 (world -> global voxel)
@@ -56,7 +87,7 @@ struct KParams {
     int n_clip;
     int nx, ny, nz;
     int W, H;
-    int rx0, ry0, rx1, ry1, tiles_x; // rectangle of pixels that can hit the box
+    int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
     int max_steps;                   // samples on the longest chord of the local box
     KSource src[ISAAC_MAX_ACTIVE];
     KChain ch[ISAAC_MAX_ACTIVE];
@@ -65,6 +96,8 @@ struct KParams {
     float4 *fb32;
     int *nsamp;
     unsigned *touched;               // optional footprint bitmap over [-1, n]^3
+    WsCounters *ctr;                 // workspace counters
+    RayRec *rays;                    // workspace ray list
     // packed (reduced-precision) volume: records over cells [-1, n]^3
     const unsigned char *rec;        // record of cell (x,y,z) at ((z+1)*PY + y+1)*PX + x+1
     const float *scales;             // E4M3: per 8^3 brick (from cell -1), `pad` floats
@@ -92,12 +125,15 @@ __device__ __forceinline__ unsigned char quant8(float x)
 // across the launch, so every branch below is uniform across the warp.
 __device__ __forceinline__ float run_chain(const KChain &ch, float v[4])
 {
-#pragma unroll
-    for (int i = 0; i < ISAAC_MAX_FUNCTORS; ++i) {
-        if (i >= ch.n) break;
+#pragma unroll 1
+    for (int i = 0; i < ch.n; ++i) {
         const KOp &o = ch.op[i];
         const int d = o.dim;
         switch (o.code) {
+        case K_AFFINE:
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = fmaf(o.a[c], v[c], o.b[c]);
+            break;
         case K_ADD:
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] += o.a[c];
@@ -153,11 +189,41 @@ __device__ __forceinline__ float4 classify(const float4 *lut, float x)
                        lerp1(a.w, b.w, f));
 }
 
+__device__ __forceinline__ void blend(float4 &acc, float w, float4 c)
+{
+    acc.x = fmaf(w, c.x, acc.x);
+    acc.y = fmaf(w, c.y, acc.y);
+    acc.z = fmaf(w, c.z, acc.z);
+    acc.w = fmaf(w, c.w, acc.w);
+}
+
 // Geometry of one sample shared by all sources.
 struct Geo {
     int ix, iy, iz;      // lower corner (trilinear) or the cell (nearest), unclamped
     float fx, fy, fz;    // trilinear weights
 };
+
+template <int INTERP>
+__device__ __forceinline__ Geo sample_geo(float x, float y, float z)
+{
+    Geo g;
+    if (INTERP) {
+        const float qx = x - 0.5f, qy = y - 0.5f, qz = z - 0.5f;
+        const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
+        g.ix = (int)flx;
+        g.iy = (int)fly;
+        g.iz = (int)flz;
+        g.fx = qx - flx;
+        g.fy = qy - fly;
+        g.fz = qz - flz;
+    } else {
+        g.ix = (int)floorf(x);
+        g.iy = (int)floorf(y);
+        g.iz = (int)floorf(z);
+        g.fx = g.fy = g.fz = 0.0f;
+    }
+    return g;
+}
 
 template <typename Idx>
 __device__ __forceinline__ float ld(const float *b, Idx o) { return __ldg(b + o); }
@@ -219,12 +285,7 @@ __device__ __forceinline__ void shade_source(const KParams &p, const Geo &g, con
     float v[4];
     fetch_source<I, SIG, INTERP, Idx>(p, g, v);
     const float x = run_chain(p.ch[I], v);
-    const float4 c = classify(s_lut + I * 256, x);
-    const float w = p.src[I].w;
-    acc.x = fmaf(w, c.x, acc.x);
-    acc.y = fmaf(w, c.y, acc.y);
-    acc.z = fmaf(w, c.z, acc.z);
-    acc.w = fmaf(w, c.w, acc.w);
+    blend(acc, p.src[I].w, classify(s_lut + I * 256, x));
 }
 
 template <unsigned SIG, int INTERP, typename Idx, int... Is>
@@ -234,22 +295,48 @@ __device__ __forceinline__ void shade_all(const KParams &p, const Geo &g, const 
     (shade_source<Is, SIG, INTERP, Idx>(p, g, s_lut, acc), ...);
 }
 
-// Ray setup in FP64 (camera unprojection, box and clip-plane intervals, the
-// sample index range).  The discrete decisions (first/last sample) are taken
-// in double so they match an FP64 reference except at exact ties; the entry
-// point and direction are then rounded to FP32 for the march.
-struct Ray {
-    float ex, ey, ez;    // local voxel position of the first sample
-    float dx, dy, dz;    // unit direction
-    int nsteps;          // samples in [t_in, t_out) on the global grid (0 = miss)
+// Footprint: mark the cells a sample reads in the [-1, n]^3 bitmap.
+template <int INTERP>
+__device__ __forceinline__ void mark_footprint(const KParams &p, const Geo &g)
+{
+    const int W = p.nx + 2, H = p.ny + 2;
+#pragma unroll
+    for (int c = 0; c < (INTERP ? 8 : 1); ++c) {
+        const int x = min(max(g.ix + (c & 1), -1), p.nx) + 1;
+        const int y = min(max(g.iy + ((c >> 1) & 1), -1), p.ny) + 1;
+        const int z = min(max(g.iz + ((c >> 2) & 1), -1), p.nz) + 1;
+        const long long bit = ((long long)z * H + y) * W + x;
+        atomicOr(p.touched + (bit >> 5), 1u << (bit & 31));
+    }
+}
+
+// Blended RGBA of one sample of the zero-copy sources.
+template <int NACT, unsigned SIG, int INTERP, typename Idx, bool TOUCH>
+struct ZeroCopyShader {
+    __device__ __forceinline__ static float4 shade(const KParams &p, const float4 *s_lut, float x,
+                                                   float y, float z)
+    {
+        const Geo g = sample_geo<INTERP>(x, y, z);
+        if (TOUCH) mark_footprint<INTERP>(p, g);
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        shade_all<SIG, INTERP, Idx>(p, g, s_lut, acc, std::make_integer_sequence<int, NACT>{});
+        return acc;
+    }
 };
 
-__device__ __forceinline__ Ray setup_ray(const KParams &p, int px, int py)
+// ------------------------------------------------------------- ray setup
+
+// Ray setup in FP64 (camera unprojection, box and clip-plane intervals, the
+// sample index range).  The discrete decisions (first/last sample) are taken
+// in double so they match an FP64 reference except at exact ties; the first
+// sample's position and the direction are then rounded to FP32 for the march.
+__device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
 {
-    Ray r;
+    RayRec r;
     r.nsteps = 0;
     r.ex = r.ey = r.ez = 0.0f;
     r.dx = r.dy = r.dz = 0.0f;
+    r.pix = py * p.W + px;
     const double *m = p.minv;
     const double xn = ((double)px + 0.5) * p.ndc_sx - 1.0;
     const double yn = 1.0 - ((double)py + 0.5) * p.ndc_sy;
@@ -324,95 +411,132 @@ __device__ __forceinline__ Ray setup_ray(const KParams &p, int px, int py)
     return r;
 }
 
-// Footprint: mark the cells a sample reads in the [-1, n]^3 bitmap.
-template <int INTERP>
-__device__ __forceinline__ void mark_footprint(const KParams &p, const Geo &g)
+__device__ __forceinline__ void write_pixel(const KParams &p, int pix, float C0, float C1, float C2,
+                                            float A, int ns)
 {
-    const int W = p.nx + 2, H = p.ny + 2;
-#pragma unroll
-    for (int c = 0; c < (INTERP ? 8 : 1); ++c) {
-        const int x = min(max(g.ix + (c & 1), -1), p.nx) + 1;
-        const int y = min(max(g.iy + ((c >> 1) & 1), -1), p.ny) + 1;
-        const int z = min(max(g.iz + ((c >> 2) & 1), -1), p.nz) + 1;
-        const long long bit = ((long long)z * H + y) * W + x;
-        atomicOr(p.touched + (bit >> 5), 1u << (bit & 31));
-    }
-}
-
-// The frame kernel: 128 threads = 16x8 pixels, each warp an 8x4 patch.
-template <int NACT, unsigned SIG, int INTERP, typename Idx, bool TOUCH = false>
-__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ KParams p)
-{
-    __shared__ float4 s_lut[NACT * 256];
-    for (int i = threadIdx.x; i < NACT * 256; i += blockDim.x) s_lut[i] = __ldg(p.lut[i >> 8] + (i & 255));
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ty = blockIdx.x / p.tiles_x, tx = blockIdx.x - ty * p.tiles_x;
-    const int px = p.rx0 + tx * 16 + (warp & 1) * 8 + (lane & 7);
-    const int py = p.ry0 + ty * 8 + (warp >> 1) * 4 + (lane >> 3);
-    if (px >= p.rx1 || py >= p.ry1) return;
-
-    const Ray ray = setup_ray(p, px, py);
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-    int ns = 0;
-    for (int k = 0; k < ray.nsteps; ++k) {
-        const float s = (float)k * p.step;
-        const float x = fmaf(s, ray.dx, ray.ex);
-        const float y = fmaf(s, ray.dy, ray.ey);
-        const float z = fmaf(s, ray.dz, ray.ez);
-        Geo g;
-        if (INTERP) {
-            const float qx = x - 0.5f, qy = y - 0.5f, qz = z - 0.5f;
-            const float flx = floorf(qx), fly = floorf(qy), flz = floorf(qz);
-            g.ix = (int)flx;
-            g.iy = (int)fly;
-            g.iz = (int)flz;
-            g.fx = qx - flx;
-            g.fy = qy - fly;
-            g.fz = qz - flz;
-        } else {
-            g.ix = (int)floorf(x);
-            g.iy = (int)floorf(y);
-            g.iz = (int)floorf(z);
-            g.fx = g.fy = g.fz = 0.0f;
-        }
-        if (TOUCH) mark_footprint<INTERP>(p, g);
-        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        shade_all<SIG, INTERP, Idx>(p, g, s_lut, acc, std::make_integer_sequence<int, NACT>{});
-        const float a = clamp01(acc.w);
-        const float t = (1.0f - A) * a;
-        C0 = fmaf(t, acc.x, C0);
-        C1 = fmaf(t, acc.y, C1);
-        C2 = fmaf(t, acc.z, C2);
-        A += t;
-        ++ns;
-        if (A >= p.term) break;
-    }
     const float T = 1.0f - A;
     const float o0 = fmaf(T, p.bg[0], C0), o1 = fmaf(T, p.bg[1], C1);
     const float o2 = fmaf(T, p.bg[2], C2), o3 = fmaf(T, p.bg[3], A);
-    const size_t pix = (size_t)py * (size_t)p.W + (size_t)px;
     p.fb8[pix] = make_uchar4(quant8(o0), quant8(o1), quant8(o2), quant8(o3));
     if (p.fb32) p.fb32[pix] = make_float4(o0, o1, o2, o3);
     if (p.nsamp) p.nsamp[pix] = ns;
 }
 
-// Background for every pixel outside the rectangle the ray kernel covers.
+// Background for every pixel outside the rectangle; resets the counters.
 static __global__ void k_fill_background(const __grid_constant__ KParams p)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.ctr) {
+        p.ctr->n_rays = 0u;
+        p.ctr->next = 0u;
+    }
     const size_t total = (size_t)p.W * (size_t)p.H;
-    const float T = 1.0f;
-    const uchar4 q = make_uchar4(quant8(fmaf(T, p.bg[0], 0.0f)), quant8(fmaf(T, p.bg[1], 0.0f)),
-                                 quant8(fmaf(T, p.bg[2], 0.0f)), quant8(fmaf(T, p.bg[3], 0.0f)));
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / (size_t)p.W), x = (int)(i - (size_t)y * p.W);
         if (x >= p.rx0 && x < p.rx1 && y >= p.ry0 && y < p.ry1) continue;
-        p.fb8[i] = q;
-        if (p.fb32) p.fb32[i] = make_float4(p.bg[0], p.bg[1], p.bg[2], p.bg[3]);
-        if (p.nsamp) p.nsamp[i] = 0;
+        write_pixel(p, (int)i, 0.0f, 0.0f, 0.0f, 0.0f, 0);
     }
+}
+
+// One thread per rectangle pixel, 128-thread blocks over 16x8 tiles whose warps
+// are 8x4 patches; hits are appended warp by warp.
+static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant__ KParams p)
+{
+    const int tiles_x = (p.rx1 - p.rx0 + 15) >> 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const int px = p.rx0 + tx * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = p.ry0 + ty * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = px < p.rx1 && py < p.ry1;
+    RayRec r;
+    r.nsteps = 0;
+    if (inside) r = setup_ray(p, px, py);
+    const bool hit = inside && r.nsteps > 0;
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    unsigned base = 0;
+    if (lane == 0 && m) base = atomicAdd(&p.ctr->n_rays, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        p.rays[base + __popc(m & ((1u << lane) - 1u))] = r;
+    } else if (inside) {
+        write_pixel(p, py * p.W + px, 0.0f, 0.0f, 0.0f, 0.0f, 0);
+    }
+}
+
+// ------------------------------------------------------------------ march
+
+// Persistent warps; each takes chunks of 32/RL rays from the list.  Lanes of a
+// group evaluate samples k+0 .. k+RL-1 of their ray together; every lane then
+// composites the group's RL samples in order, stopping at the termination
+// sample, so all lanes hold the same C and A.
+template <int NACT, class Shader, int RL>
+__device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
+{
+    constexpr int RAYS = 32 / RL;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (RL - 1);
+    const unsigned n_rays = *(volatile unsigned *)&p.ctr->n_rays;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctr->next, (unsigned)RAYS);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_rays) break;
+        const unsigned idx = base + (unsigned)(lane / RL);
+        if (idx < n_rays) {
+            const RayRec r = p.rays[idx];
+            float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+            int ns = 0;
+            const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
+            for (int k = 0; k < r.nsteps; k += RL) {
+                const int kk = k + sub;
+                float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (kk < r.nsteps) {
+                    const float s = (float)kk * p.step;
+                    c = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey),
+                                      fmaf(s, r.dz, r.ez));
+                }
+                bool done = false;
+#pragma unroll
+                for (int j = 0; j < RL; ++j) {
+                    float4 cj = c;
+                    if (RL > 1) {
+                        cj.x = __shfl_sync(gmask, c.x, j, RL);
+                        cj.y = __shfl_sync(gmask, c.y, j, RL);
+                        cj.z = __shfl_sync(gmask, c.z, j, RL);
+                        cj.w = __shfl_sync(gmask, c.w, j, RL);
+                    }
+                    if (!done && k + j < r.nsteps) {
+                        const float a = clamp01(cj.w);
+                        const float t = (1.0f - A) * a;
+                        C0 = fmaf(t, cj.x, C0);
+                        C1 = fmaf(t, cj.y, C1);
+                        C2 = fmaf(t, cj.z, C2);
+                        A += t;
+                        ++ns;
+                        done = A >= p.term;
+                    }
+                }
+                if (done) break;
+            }
+            if (sub == 0) write_pixel(p, r.pix, C0, C1, C2, A, ns);
+        }
+    }
+}
+
+template <int NACT>
+__device__ __forceinline__ void load_luts(const KParams &p, float4 *s_lut)
+{
+    for (int i = threadIdx.x; i < NACT * 256; i += blockDim.x) s_lut[i] = __ldg(p.lut[i >> 8] + (i & 255));
+    __syncthreads();
+}
+
+// The zero-copy frame kernel (128 threads, at most 64 registers per thread).
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, bool TOUCH = false>
+__global__ void __launch_bounds__(128, 8) k_raycast(const __grid_constant__ KParams p)
+{
+    __shared__ float4 s_lut[NACT * 256];
+    load_luts<NACT>(p, s_lut);
+    march<NACT, ZeroCopyShader<NACT, SIG, INTERP, Idx, TOUCH>, RL>(p, s_lut);
 }
 
 }  // namespace isaac

@@ -1,0 +1,53 @@
+// raycast_kernels.cu -- instantiations of the zero-copy frame kernel and the
+// table the host dispatches from.
+#include "kernel_table.h"
+#include "raycast.cuh"
+
+namespace isaac {
+
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, bool TOUCH>
+static void launch_zc(const KParams &p, dim3 grid, cudaStream_t st)
+{
+    k_raycast<NACT, SIG, INTERP, Idx, RL, TOUCH><<<grid, 128, 0, st>>>(p);
+}
+
+// {nact, sig, interp, rl, wide, touch, launcher}
+#define ISAAC_Z(N, S, I, R, W, T) \
+    {N, S, I, R, W, T, launch_zc<N, S, I, std::conditional_t<W, long long, int>, R, T>}
+#define ISAAC_Z2(N, S, R, W, T) ISAAC_Z(N, S, 0, R, W, T), ISAAC_Z(N, S, 1, R, W, T)
+// Precompiled source signatures (Sec. 3.2 compiles the source loop for the
+// application's source list): one scalar; E, B, rho in AoS and in component
+// planes.  Anything else runs the generic kernel with run-time f_dim.
+static const ZcEntry k_entries[] = {
+    ISAAC_Z2(1, 0x9u, 1, false, false), ISAAC_Z2(1, 0x9u, 2, false, false),
+    ISAAC_Z2(1, 0x9u, 4, false, false),
+    ISAAC_Z2(3, 0x9BBu, 1, false, false), ISAAC_Z2(3, 0x9BBu, 2, false, false),
+    ISAAC_Z2(3, 0x9BBu, 4, false, false),
+    ISAAC_Z2(3, 0x933u, 2, false, false),
+    ISAAC_Z2(1, 0u, 2, false, false), ISAAC_Z2(2, 0u, 2, false, false),
+    ISAAC_Z2(3, 0u, 2, false, false), ISAAC_Z2(4, 0u, 2, false, false),
+    ISAAC_Z2(1, 0u, 2, true, false), ISAAC_Z2(2, 0u, 2, true, false),
+    ISAAC_Z2(3, 0u, 2, true, false), ISAAC_Z2(4, 0u, 2, true, false),
+    ISAAC_Z2(1, 0u, 1, false, true), ISAAC_Z2(2, 0u, 1, false, true),
+    ISAAC_Z2(3, 0u, 1, false, true), ISAAC_Z2(4, 0u, 1, false, true),
+};
+#undef ISAAC_Z2
+#undef ISAAC_Z
+
+extern const ZcEntry *const k_zc_entries = k_entries;
+extern const int k_n_zc_entries = (int)(sizeof(k_entries) / sizeof(k_entries[0]));
+
+// The setup and background kernels are launched from this translation unit.
+void launch_fill(const KParams &p, cudaStream_t st)
+{
+    const int blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
+    k_fill_background<<<blocks, 256, 0, st>>>(p);
+}
+
+void launch_setup(const KParams &p, cudaStream_t st)
+{
+    const int tiles = ((p.rx1 - p.rx0 + 15) / 16) * ((p.ry1 - p.ry0 + 7) / 8);
+    k_setup_rays<<<tiles, 128, 0, st>>>(p);
+}
+
+}  // namespace isaac

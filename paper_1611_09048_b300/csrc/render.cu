@@ -1,396 +1,140 @@
-// render.cu -- host side of isaac_render: argument validation, functor-chain
-// compilation, the FP64 camera inverse, the screen rectangle the box can
-// cover, and kernel dispatch by source signature.
+// render.cu -- isaac_render: source validation, kernel selection by source
+// signature and lanes per ray, the per-stream workspace and the three-kernel
+// frame launch.
 #include <algorithm>
 #include <cmath>
-#include <cstdarg>
-#include <cstdio>
+#include <cstdlib>
 #include <cstring>
-#include <string>
+#include <mutex>
+#include <vector>
 
-#include "raycast.cuh"
-#include "isaac_b300.h"
 #include "common.h"
+#include "raycast.cuh"
 
 namespace isaac {
 
-static thread_local std::string g_last_error;
+// ------------------------------------------------------------ workspace
 
-int fail(int code, const char *fmt, ...)
+// One workspace per (device, stream): counters + one ray record per pixel of
+// the largest screen rectangle seen on that stream.  Frames on one stream are
+// ordered, so they can share it; different streams never do.
+struct Workspace {
+    int device;
+    cudaStream_t stream;
+    void *ptr;
+    size_t bytes;
+};
+static std::mutex g_ws_mu;
+static std::vector<Workspace> g_ws;
+
+int bind_workspace(KParams &p, cudaStream_t st)
 {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return code;
-}
-
-void clear_error() { g_last_error.clear(); }
-
-int check_cuda(const char *what)
-{
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(ISAAC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+    const size_t need = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * sizeof(RayRec);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    Workspace *w = nullptr;
+    for (Workspace &e : g_ws)
+        if (e.device == dev && e.stream == st) w = &e;
+    if (!w) {
+        g_ws.push_back({dev, st, nullptr, 0});
+        w = &g_ws.back();
+    }
+    if (w->bytes < need) {
+        if (w->ptr) {
+            // frames still in flight on this stream may use the old buffer
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda("workspace sync");
+            cudaFree(w->ptr);
+            w->ptr = nullptr;
+            w->bytes = 0;
+        }
+        const size_t bytes = need + need / 4;
+        if (cudaMalloc(&w->ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ISAAC_ENOMEM, "cannot allocate a %zu-byte render workspace", bytes);
+        }
+        w->bytes = bytes;
+    }
+    p.ctr = static_cast<WsCounters *>(w->ptr);
+    p.rays = reinterpret_cast<RayRec *>(static_cast<char *>(w->ptr) + kWsHeader);
     return ISAAC_OK;
 }
 
-// ---------------------------------------------------------------- camera
-
-// Column-major 4x4 product C = A * B.
-static void mat_mul(const double *A, const double *B, double *C)
+static int sm_count()
 {
-    for (int c = 0; c < 4; ++c)
-        for (int r = 0; r < 4; ++r) {
-            double s = 0.0;
-            for (int k = 0; k < 4; ++k) s = fma(A[4 * k + r], B[4 * c + k], s);
-            C[4 * c + r] = s;
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 148;
         }
+        cached[dev] = n;
+    }
+    return cached[dev];
 }
 
-// Inverse by cofactor expansion (adjugate / determinant), in double.
-static bool mat_inverse(const double *m, double *inv)
+int choose_lanes(long long rect_pixels, int hint)
 {
-    double a[16];
-    a[0] = m[5] * m[10] * m[15] - m[5] * m[11] * m[14] - m[9] * m[6] * m[15] + m[9] * m[7] * m[14] +
-           m[13] * m[6] * m[11] - m[13] * m[7] * m[10];
-    a[4] = -m[4] * m[10] * m[15] + m[4] * m[11] * m[14] + m[8] * m[6] * m[15] - m[8] * m[7] * m[14] -
-           m[12] * m[6] * m[11] + m[12] * m[7] * m[10];
-    a[8] = m[4] * m[9] * m[15] - m[4] * m[11] * m[13] - m[8] * m[5] * m[15] + m[8] * m[7] * m[13] +
-           m[12] * m[5] * m[11] - m[12] * m[7] * m[9];
-    a[12] = -m[4] * m[9] * m[14] + m[4] * m[10] * m[13] + m[8] * m[5] * m[14] - m[8] * m[6] * m[13] -
-            m[12] * m[5] * m[10] + m[12] * m[6] * m[9];
-    a[1] = -m[1] * m[10] * m[15] + m[1] * m[11] * m[14] + m[9] * m[2] * m[15] - m[9] * m[3] * m[14] -
-           m[13] * m[2] * m[11] + m[13] * m[3] * m[10];
-    a[5] = m[0] * m[10] * m[15] - m[0] * m[11] * m[14] - m[8] * m[2] * m[15] + m[8] * m[3] * m[14] +
-           m[12] * m[2] * m[11] - m[12] * m[3] * m[10];
-    a[9] = -m[0] * m[9] * m[15] + m[0] * m[11] * m[13] + m[8] * m[1] * m[15] - m[8] * m[3] * m[13] -
-           m[12] * m[1] * m[11] + m[12] * m[3] * m[9];
-    a[13] = m[0] * m[9] * m[14] - m[0] * m[10] * m[13] - m[8] * m[1] * m[14] + m[8] * m[2] * m[13] +
-            m[12] * m[1] * m[10] - m[12] * m[2] * m[9];
-    a[2] = m[1] * m[6] * m[15] - m[1] * m[7] * m[14] - m[5] * m[2] * m[15] + m[5] * m[3] * m[14] +
-           m[13] * m[2] * m[7] - m[13] * m[3] * m[6];
-    a[6] = -m[0] * m[6] * m[15] + m[0] * m[7] * m[14] + m[4] * m[2] * m[15] - m[4] * m[3] * m[14] -
-           m[12] * m[2] * m[7] + m[12] * m[3] * m[6];
-    a[10] = m[0] * m[5] * m[15] - m[0] * m[7] * m[13] - m[4] * m[1] * m[15] + m[4] * m[3] * m[13] +
-            m[12] * m[1] * m[7] - m[12] * m[3] * m[5];
-    a[14] = -m[0] * m[5] * m[14] + m[0] * m[6] * m[13] + m[4] * m[1] * m[14] - m[4] * m[2] * m[13] -
-            m[12] * m[1] * m[6] + m[12] * m[2] * m[5];
-    a[3] = -m[1] * m[6] * m[11] + m[1] * m[7] * m[10] + m[5] * m[2] * m[11] - m[5] * m[3] * m[10] -
-           m[9] * m[2] * m[7] + m[9] * m[3] * m[6];
-    a[7] = m[0] * m[6] * m[11] - m[0] * m[7] * m[10] - m[4] * m[2] * m[11] + m[4] * m[3] * m[10] +
-           m[8] * m[2] * m[7] - m[8] * m[3] * m[6];
-    a[11] = -m[0] * m[5] * m[11] + m[0] * m[7] * m[9] + m[4] * m[1] * m[11] - m[4] * m[3] * m[9] -
-            m[8] * m[1] * m[7] + m[8] * m[3] * m[5];
-    a[15] = m[0] * m[5] * m[10] - m[0] * m[6] * m[9] - m[4] * m[1] * m[10] + m[4] * m[2] * m[9] +
-            m[8] * m[1] * m[6] - m[8] * m[2] * m[5];
-    const double det = m[0] * a[0] + m[1] * a[4] + m[2] * a[8] + m[3] * a[12];
-    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
-    const double id = 1.0 / det;
-    for (int i = 0; i < 16; ++i) inv[i] = a[i] * id;
-    return true;
+    if (hint) return hint;
+    // about 0.6 of the rectangle's pixels hit the box; use more lanes per ray
+    // until the hit rays fill the resident threads (8 blocks of 128 per SM)
+    const double slots = (double)sm_count() * 8.0 * 128.0;
+    int rl = 1;
+    while (rl < 4 && 0.6 * (double)rect_pixels * rl < slots) rl *= 2;
+    return rl;
 }
 
-// ------------------------------------------------------------ validation
-
-static bool finite_n(const float *v, int n)
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st)
 {
-    for (int i = 0; i < n; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
-
-// Compile one public chain into the kernel's op list.
-int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out)
-{
-    if (in.n_ops < 0 || in.n_ops > ISAAC_MAX_FUNCTORS)
-        return fail(ISAAC_EINVAL, "source %d: chain has %d functors (max %d)", s, in.n_ops,
-                    ISAAC_MAX_FUNCTORS);
-    int dim = fdim, n = 0;
-    for (int i = 0; i < in.n_ops; ++i) {
-        const isaac_functor &f = in.ops[i];
-        KOp o;
-        o.dim = dim;
-        o.a[0] = o.a[1] = o.a[2] = o.a[3] = 0.0f;
-        switch (f.op) {
-        case ISAAC_OP_ADD:
-        case ISAAC_OP_MUL:
-        case ISAAC_OP_POW: {
-            if (f.n_args != 1 && f.n_args != dim)
-                return fail(ISAAC_EINVAL,
-                            "source %d functor %d: %d arguments for a %d-component value "
-                            "(need 1 or %d)", s, i, f.n_args, dim, dim);
-            if (!finite_n(f.arg, f.n_args))
-                return fail(ISAAC_EINVAL, "source %d functor %d: non-finite argument", s, i);
-            for (int c = 0; c < 4; ++c)
-                o.a[c] = f.n_args == 1 ? f.arg[0] : (c < dim ? f.arg[c] : 0.0f);
-            o.code = f.op == ISAAC_OP_ADD ? K_ADD : f.op == ISAAC_OP_MUL ? K_MUL : K_POW;
-            if (o.code == K_POW) {
-                bool all_half = true;
-                for (int c = 0; c < dim; ++c) all_half &= (o.a[c] == 0.5f);
-                if (all_half) o.code = K_SQRT;
-            }
-        } break;
-        case ISAAC_OP_LENGTH:
-            o.code = K_LENGTH;
-            dim = 1;
-            break;
-        case ISAAC_OP_SUM:
-            o.code = K_SUM;
-            dim = 1;
-            break;
-        case ISAAC_OP_LOG:
-            o.code = K_LOG;
-            break;
-        default:
-            return fail(ISAAC_EINVAL, "source %d functor %d: unknown op %d", s, i, f.op);
-        }
-        out.op[n++] = o;
+    const bool any = fn && p.rx1 > p.rx0 && p.ry1 > p.ry0;
+    if (!any) {   // nothing to ray cast: the background covers every pixel
+        p.rx0 = p.rx1 = p.ry0 = p.ry1 = 0;
+        p.ctr = nullptr;
+        launch_fill(p, st);
+        return check_cuda("render launch");
     }
-    out.n = n;
-    for (int i = n; i < ISAAC_MAX_FUNCTORS; ++i) {
-        out.op[i].code = 0;
-        out.op[i].dim = 1;
-        out.op[i].a[0] = out.op[i].a[1] = out.op[i].a[2] = out.op[i].a[3] = 0.0f;
-    }
-    return ISAAC_OK;
-}
-
-// Validate one source's reachable cells against its extent and fill the
-// kernel descriptor.  elem = bytes per element.  Returns the signature
-// nibble via *nib and whether 64-bit offsets are needed via *wide.
-int prepare_source(const isaac_source &src, int s, const int64_t n[3], int interp, float weight,
-                   int elem, KSource &ks, unsigned *nib, bool *wide)
-{
-    if (!src.ptr) return fail(ISAAC_EINVAL, "source %d: NULL pointer for an active source", s);
-    if (src.f_dim < 1 || src.f_dim > 4)
-        return fail(ISAAC_EINVAL, "source %d: f_dim %d outside 1..4", s, src.f_dim);
-    if (src.guard < 0) return fail(ISAAC_EINVAL, "source %d: negative guard", s);
-    if (src.extent <= 0 || src.offset < 0)
-        return fail(ISAAC_EINVAL, "source %d: extent %lld / offset %lld", s, (long long)src.extent,
-                    (long long)src.offset);
-    if (((uintptr_t)src.ptr) % (uintptr_t)elem != 0)
-        return fail(ISAAC_EINVAL, "source %d: pointer not aligned to its element size", s);
-    const int g1 = (interp && src.guard >= 1) ? 1 : 0;
-    // smallest and largest element index any sample can read
-    long double lo = (long double)src.offset, hi = lo, span = 0.0L;
-    for (int a = 0; a < 3; ++a) {
-        const long double i0 = -g1, i1 = (long double)(n[a] - 1 + g1);
-        const long double st = (long double)src.stride[a];
-        lo += std::fmin(i0 * st, i1 * st);
-        hi += std::fmax(i0 * st, i1 * st);
-        span += std::fmax(std::fabs(i0 * st), std::fabs(i1 * st));
-    }
-    const long double cst = (long double)(src.f_dim - 1) * (long double)src.comp_stride;
-    lo += std::fmin(0.0L, cst);
-    hi += std::fmax(0.0L, cst);
-    span += std::fabs(cst);
-    if (lo < 0.0L || hi >= (long double)src.extent)
-        return fail(ISAAC_EGUARD,
-                    "source %d: cells reachable with guard %d span elements [%.0Lf, %.0Lf] but the "
-                    "extent is %lld", s, src.guard, lo, hi, (long long)src.extent);
-    *wide = span >= 2147483647.0L;
-    ks.base = reinterpret_cast<const float *>(static_cast<const char *>(src.ptr) +
-                                              (size_t)src.offset * (size_t)elem);
-    ks.sx = src.stride[0];
-    ks.sy = src.stride[1];
-    ks.sz = src.stride[2];
-    ks.sc = src.comp_stride;
-    ks.fdim = src.f_dim;
-    ks.lo = -g1;
-    ks.hi_pad = g1;
-    ks.w = weight;
-    *nib = (unsigned)src.f_dim | ((src.f_dim == 1 || src.comp_stride == 1) ? 8u : 0u);
-    return ISAAC_OK;
-}
-
-// Common validation of everything but the sources; fills the geometric part
-// of KParams.
-int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_clip,
-                  const isaac_render_opts *opt, KParams &p)
-{
-    if (!cam || !opt) return fail(ISAAC_EINVAL, "camera and opts are required");
-    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
-        return fail(ISAAC_EINVAL, "image size %dx%d outside 1..32768", cam->width, cam->height);
-    for (int a = 0; a < 3; ++a) {
-        if (opt->n[a] < 1 || opt->n[a] > (1 << 30))
-            return fail(ISAAC_EINVAL, "volume size n[%d] = %lld", a, (long long)opt->n[a]);
-        if (opt->offset[a] < 0) return fail(ISAAC_EINVAL, "negative offset[%d]", a);
-    }
-    const bool same = opt->global_n[0] == 0 && opt->global_n[1] == 0 && opt->global_n[2] == 0;
-    int64_t gn[3];
-    for (int a = 0; a < 3; ++a) {
-        gn[a] = same ? opt->n[a] : opt->global_n[a];
-        if (opt->offset[a] + opt->n[a] > gn[a])
-            return fail(ISAAC_EINVAL, "local box [%lld, %lld) exceeds the global size %lld on axis %d",
-                        (long long)opt->offset[a], (long long)(opt->offset[a] + opt->n[a]),
-                        (long long)gn[a], a);
-    }
-    if (!(opt->step > 0.0f) || !std::isfinite(opt->step))
-        return fail(ISAAC_EINVAL, "step must be positive and finite");
-    if (opt->interp != 0 && opt->interp != 1) return fail(ISAAC_EINVAL, "interp must be 0 or 1");
-    if (std::isnan(opt->term_alpha)) return fail(ISAAC_EINVAL, "term_alpha is NaN");
-    if (!finite_n(opt->bg, 4)) return fail(ISAAC_EINVAL, "background is not finite");
-    if (n_clip < 0 || n_clip > ISAAC_MAX_CLIP)
-        return fail(ISAAC_EINVAL, "%d clip planes (max %d)", n_clip, ISAAC_MAX_CLIP);
-    if (n_clip > 0 && !clip) return fail(ISAAC_EINVAL, "clip is NULL with n_clip > 0");
-    for (int i = 0; i < n_clip; ++i)
-        for (int j = 0; j < 4; ++j) {
-            const double v = j < 3 ? clip[i].n[j] : clip[i].d;
-            if (!std::isfinite(v)) return fail(ISAAC_EINVAL, "clip plane %d is not finite", i);
-            p.clip[i][j] = v;
-        }
-    p.n_clip = n_clip;
-
-    double M[16];
-    mat_mul(cam->projection, cam->modelview, M);
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(M[i])) return fail(ISAAC_EINVAL, "camera matrices are not finite");
-    if (!mat_inverse(M, p.minv)) return fail(ISAAC_EINVAL, "projection * modelview is singular");
-
-    p.W = cam->width;
-    p.H = cam->height;
-    p.ndc_sx = 2.0 / (double)cam->width;
-    p.ndc_sy = 2.0 / (double)cam->height;
-    p.nx = (int)opt->n[0];
-    p.ny = (int)opt->n[1];
-    p.nz = (int)opt->n[2];
-    for (int a = 0; a < 3; ++a) {
-        p.gn[a] = (double)gn[a];
-        p.half_g[a] = 0.5 * (double)gn[a];
-        p.llo[a] = (double)opt->offset[a];
-        p.lhi[a] = (double)(opt->offset[a] + opt->n[a]);
-    }
-    p.step = opt->step;
-    p.step_d = (double)opt->step;
-    // every ray's samples lie on one chord of the local box
-    const double diag = std::sqrt((double)opt->n[0] * opt->n[0] + (double)opt->n[1] * opt->n[1] +
-                                  (double)opt->n[2] * opt->n[2]);
-    const double max_steps = std::ceil(diag / (double)opt->step) + 2.0;
-    if (max_steps > (double)(1 << 24))
-        return fail(ISAAC_EINVAL, "step %g gives up to %.0f samples per ray (max %d)",
-                    (double)opt->step, max_steps, 1 << 24);
-    p.max_steps = (int)max_steps;
-    p.term = opt->term_alpha;
-    for (int c = 0; c < 4; ++c) p.bg[c] = opt->bg[c];
-
-    // Screen rectangle: project the 8 local-box corners; a pixel whose ray can
-    // reach the box lies in their bounding box (one-pixel margin for rounding).
-    bool full = false;
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    for (int c = 0; c < 8; ++c) {
-        const double w[3] = {((c & 1) ? p.lhi[0] : p.llo[0]) - p.half_g[0],
-                             ((c & 2) ? p.lhi[1] : p.llo[1]) - p.half_g[1],
-                             ((c & 4) ? p.lhi[2] : p.llo[2]) - p.half_g[2]};
-        double v[4];
-        for (int r = 0; r < 4; ++r) v[r] = M[r] * w[0] + M[4 + r] * w[1] + M[8 + r] * w[2] + M[12 + r];
-        if (!(v[3] > 1e-12)) {
-            full = true;
-            break;
-        }
-        const double sx = (v[0] / v[3] + 1.0) * 0.5 * cam->width - 0.5;
-        const double sy = (1.0 - v[1] / v[3]) * 0.5 * cam->height - 0.5;
-        xmin = std::fmin(xmin, sx);
-        xmax = std::fmax(xmax, sx);
-        ymin = std::fmin(ymin, sy);
-        ymax = std::fmax(ymax, sy);
-    }
-    if (full) {
-        p.rx0 = p.ry0 = 0;
-        p.rx1 = cam->width;
-        p.ry1 = cam->height;
-    } else {
-        p.rx0 = (int)std::fmax(0.0, std::fmin((double)cam->width, std::floor(xmin) - 1.0));
-        p.rx1 = (int)std::fmax(0.0, std::fmin((double)cam->width, std::ceil(xmax) + 2.0));
-        p.ry0 = (int)std::fmax(0.0, std::fmin((double)cam->height, std::floor(ymin) - 1.0));
-        p.ry1 = (int)std::fmax(0.0, std::fmin((double)cam->height, std::ceil(ymax) + 2.0));
-        if (p.rx1 <= p.rx0 || p.ry1 <= p.ry0) p.rx0 = p.rx1 = p.ry0 = p.ry1 = 0;
-    }
-    p.tiles_x = (p.rx1 - p.rx0 + 15) / 16;
-    return ISAAC_OK;
-}
-
-// ------------------------------------------------------------- dispatch
-
-using LaunchFn = void (*)(const KParams &, dim3, cudaStream_t);
-
-template <int NACT, unsigned SIG, int INTERP, typename Idx, bool TOUCH = false>
-static void launch_raycast(const KParams &p, dim3 grid, cudaStream_t st)
-{
-    k_raycast<NACT, SIG, INTERP, Idx, TOUCH><<<grid, 128, 0, st>>>(p);
-}
-
-struct SigEntry {
-    int nact;
-    unsigned sig;
-    LaunchFn fn[2];   // [interp]
-};
-
-#define ISAAC_SIG(N, S) {N, S, {launch_raycast<N, S, 0, int>, launch_raycast<N, S, 1, int>}}
-// Precompiled source signatures (Sec. 3.2 compiles the source loop for the
-// application's source list): one scalar; one vector; E, B, rho in AoS and in
-// component planes.  Anything else runs the generic kernel with run-time f_dim.
-static const SigEntry k_sigs[] = {
-    ISAAC_SIG(1, 0x9u), ISAAC_SIG(1, 0xBu), ISAAC_SIG(2, 0x99u), ISAAC_SIG(2, 0x9Bu),
-    ISAAC_SIG(2, 0xBBu), ISAAC_SIG(3, 0x9BBu), ISAAC_SIG(3, 0x933u),
-};
-#undef ISAAC_SIG
-
-static const LaunchFn k_generic[ISAAC_MAX_ACTIVE][2][2] = {  // [nact-1][wide][interp]
-    {{launch_raycast<1, 0u, 0, int>, launch_raycast<1, 0u, 1, int>},
-     {launch_raycast<1, 0u, 0, long long>, launch_raycast<1, 0u, 1, long long>}},
-    {{launch_raycast<2, 0u, 0, int>, launch_raycast<2, 0u, 1, int>},
-     {launch_raycast<2, 0u, 0, long long>, launch_raycast<2, 0u, 1, long long>}},
-    {{launch_raycast<3, 0u, 0, int>, launch_raycast<3, 0u, 1, int>},
-     {launch_raycast<3, 0u, 0, long long>, launch_raycast<3, 0u, 1, long long>}},
-    {{launch_raycast<4, 0u, 0, int>, launch_raycast<4, 0u, 1, int>},
-     {launch_raycast<4, 0u, 0, long long>, launch_raycast<4, 0u, 1, long long>}},
-};
-
-// Footprint-recording variants (generic signature only).
-#define ISAAC_T(N, I) launch_raycast<N, 0u, 0, I, true>, launch_raycast<N, 0u, 1, I, true>
-static const LaunchFn k_touch[ISAAC_MAX_ACTIVE][2][2] = {
-    {{ISAAC_T(1, int)}, {ISAAC_T(1, long long)}}, {{ISAAC_T(2, int)}, {ISAAC_T(2, long long)}},
-    {{ISAAC_T(3, int)}, {ISAAC_T(3, long long)}}, {{ISAAC_T(4, int)}, {ISAAC_T(4, long long)}},
-};
-#undef ISAAC_T
-
-int launch_with(const KParams &p, FrameLaunch fn, cudaStream_t st)
-{
-    const int fill_blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
-    if (fn) {
-        k_fill_background<<<fill_blocks, 256, 0, st>>>(p);
-    } else {   // nothing to ray cast: the background covers every pixel
-        KParams q = p;
-        q.rx0 = q.rx1 = q.ry0 = q.ry1 = 0;
-        k_fill_background<<<fill_blocks, 256, 0, st>>>(q);
-    }
-    if (fn && p.rx1 > p.rx0 && p.ry1 > p.ry0) {
-        const int tiles_y = (p.ry1 - p.ry0 + 7) / 8;
-        fn(p, dim3((unsigned)(p.tiles_x * tiles_y)), st);
-    }
+    int rc = bind_workspace(p, st);
+    if (rc) return rc;
+    launch_fill(p, st);
+    launch_setup(p, st);
+    const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+    const long long want = (rect * rl + 127) / 128;
+    const long long cap = (long long)sm_count() * 8;
+    fn(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
     return check_cuda("render launch");
 }
 
-static int launch_frame(const KParams &p, int nact, unsigned sig, bool wide, int interp,
-                        cudaStream_t st)
+// --------------------------------------------------------------- dispatch
+
+static FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
+                           int *rl_used)
 {
-    LaunchFn fn = nullptr;
-    if (nact > 0) {
-        fn = p.touched ? k_touch[nact - 1][wide ? 1 : 0][interp] : nullptr;
-        if (!fn && !wide)
-            for (const SigEntry &e : k_sigs)
-                if (e.nact == nact && e.sig == sig) fn = e.fn[interp];
-        if (!fn) fn = k_generic[nact - 1][wide ? 1 : 0][interp];
+    const ZcEntry *best = nullptr;
+    for (int pass = 0; pass < 2 && !best; ++pass) {
+        const unsigned want = pass == 0 ? sig : 0u;
+        for (int i = 0; i < k_n_zc_entries; ++i) {
+            const ZcEntry &e = k_zc_entries[i];
+            if (e.nact != nact || e.sig != want || e.interp != interp || e.wide != wide ||
+                e.touch != touch)
+                continue;
+            if (!best || (e.rl == rl) || (best->rl != rl && std::abs(e.rl - rl) < std::abs(best->rl - rl)))
+                best = &e;
+        }
     }
-    return launch_with(p, fn, st);
+    if (!best) return nullptr;
+    *rl_used = best->rl;
+    return best->fn;
 }
 
-// Validate the sources of one call and fill the source part of KParams.
-int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
-                    const float *luts, const float *weights, const isaac_render_opts *opts,
-                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out)
+static int prepare_sources(const isaac_source *sources, const isaac_chain *chains,
+                           int32_t n_sources, const float *luts, const float *weights,
+                           const isaac_render_opts *opts, KParams &p, int *nact_out,
+                           unsigned *sig_out, bool *wide_out)
 {
     if (!sources || !chains || !weights)
         return fail(ISAAC_EINVAL, "sources, chains and weights are required");
@@ -427,19 +171,6 @@ int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int3
     return ISAAC_OK;
 }
 
-int prepare_fb(const isaac_framebuffer *fb, KParams &p)
-{
-    if (!fb || !fb->rgba8) return fail(ISAAC_EINVAL, "fb->rgba8 is required");
-    if (((uintptr_t)fb->rgba8) % 4 || ((uintptr_t)fb->rgba32) % 16 || ((uintptr_t)fb->nsamples) % 4)
-        return fail(ISAAC_EINVAL, "framebuffer pointers are misaligned");
-    p.fb8 = reinterpret_cast<uchar4 *>(fb->rgba8);
-    p.fb32 = reinterpret_cast<float4 *>(fb->rgba32);
-    p.nsamp = fb->nsamples;
-    if (((uintptr_t)fb->touched) % 4) return fail(ISAAC_EINVAL, "fb->touched is misaligned");
-    p.touched = reinterpret_cast<unsigned *>(fb->touched);
-    return ISAAC_OK;
-}
-
 }  // namespace isaac
 
 using namespace isaac;
@@ -462,9 +193,38 @@ extern "C" int isaac_render(const isaac_source *sources, const isaac_chain *chai
     if (rc) return rc;
     rc = prepare_fb(fb, p);
     if (rc) return rc;
-    return launch_frame(p, nact, sig, wide, opts->interp, (cudaStream_t)stream);
+    FrameLaunch fn = nullptr;
+    int rl = 1;
+    if (nact > 0) {
+        const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+        const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray);
+        fn = find_zc(nact, sig, opts->interp, wide, p.touched != nullptr, want, &rl);
+        if (!fn)
+            return fail(ISAAC_ENOTSUP, "no kernel for %d sources (footprint with 64-bit offsets?)",
+                        nact);
+    }
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream);
 }
 
-extern "C" const char *isaac_last_error(void) { return g_last_error.c_str(); }
+extern "C" int isaac_release_workspaces(void)
+{
+    clear_error();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    if (cudaDeviceSynchronize() != cudaSuccess) return check_cuda("cudaDeviceSynchronize");
+    std::vector<Workspace> keep;
+    for (Workspace &w : g_ws) {
+        if (w.device == dev) {
+            if (w.ptr) cudaFree(w.ptr);
+        } else {
+            keep.push_back(w);
+        }
+    }
+    g_ws.swap(keep);
+    return check_cuda("isaac_release_workspaces");
+}
+
+extern "C" const char *isaac_last_error(void) { return last_error(); }
 
 extern "C" int isaac_abi_version(void) { return ISAAC_ABI_VERSION; }

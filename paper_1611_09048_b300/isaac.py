@@ -26,7 +26,11 @@ OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 
 # every C symbol declared in include/isaac_b300.h
 EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_layout",
-           "isaac_pack", "isaac_render_packed")
+           "isaac_pack", "isaac_render_packed", "isaac_release_workspaces",
+           "isaac_opacity_grid")
+
+# lanes per ray used when a call does not pass one (0 = the library chooses)
+LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
 
 
 class Source(C.Structure):
@@ -55,7 +59,7 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("n", C.c_int64 * 3), ("global_n", C.c_int64 * 3), ("offset", C.c_int64 * 3),
                 ("step", C.c_float), ("interp", C.c_int32), ("term_alpha", C.c_float),
-                ("bg", C.c_float * 4), ("active_mask", C.c_uint32)]
+                ("bg", C.c_float * 4), ("active_mask", C.c_uint32), ("lanes_per_ray", C.c_int32)]
 
 
 class Framebuffer(C.Structure):
@@ -107,6 +111,11 @@ def load(path: Optional[str] = None):
                                             C.c_void_p, C.POINTER(Camera), C.POINTER(Plane),
                                             C.c_int32, C.POINTER(RenderOpts),
                                             C.POINTER(Framebuffer), C.c_void_p]
+        lib.isaac_opacity_grid.restype = C.c_int
+        lib.isaac_opacity_grid.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32,
+                                           C.c_void_p, C.c_void_p, C.POINTER(RenderOpts),
+                                           C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
+        lib.isaac_release_workspaces.restype = C.c_int
         lib.isaac_last_error.restype = C.c_char_p
         lib.isaac_abi_version.restype = C.c_int
         _lib = lib
@@ -144,8 +153,9 @@ def make_camera(mv, proj, width, height) -> Camera:
     return cam
 
 
-def make_opts(scene, mask=None) -> RenderOpts:
+def make_opts(scene, mask=None, lanes=None) -> RenderOpts:
     o = RenderOpts()
+    o.lanes_per_ray = LANES_PER_RAY if lanes is None else int(lanes)
     for a in range(3):
         o.n[a] = int(scene.n[a])
         o.global_n[a] = int(scene.gn[a])
@@ -220,7 +230,7 @@ class DeviceScene:
         return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
-                touched=None):
+                touched=None, lanes=None):
         """Marshal one frame's arguments (camera, opts, framebuffer) once; the
         returned tuple can be launched repeatedly with ``launch``."""
         sc = self.scene
@@ -230,7 +240,7 @@ class DeviceScene:
         fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
                          nsamples.data_ptr() if nsamples is not None else None,
                          touched.data_ptr() if touched is not None else None)
-        opts = make_opts(sc, mask)
+        opts = make_opts(sc, mask, lanes)
         keep = (cam, planes, fb, opts)
         return (self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
@@ -242,7 +252,7 @@ class DeviceScene:
         check(load().isaac_render(*args, _stream_handle(stream)))
 
     def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
-               mask=None, want_f32=False, want_nsamp=False, touched=None):
+               mask=None, want_f32=False, want_nsamp=False, touched=None, lanes=None):
         """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
         as device tensors."""
         import torch
@@ -253,9 +263,23 @@ class DeviceScene:
             rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         if nsamples is None and want_nsamp:
             nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
-        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched), stream)
+        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes), stream)
         return out, rgba32, nsamples
 
+
+    def opacity_grid(self, cell=16, mask=None, stream=None, out=None):
+        """Max-opacity grid (Gz, Gy, Gx) float32 on the device."""
+        import torch
+        sc = self.scene
+        G = [(int(k) + cell - 1) // cell for k in sc.n]
+        if out is None:
+            out = torch.empty((G[2], G[1], G[0]), dtype=torch.float32, device=self.device)
+        opts = make_opts(sc, mask)
+        check(load().isaac_opacity_grid(self.sources, self.chains, len(sc.sources),
+                                        self.luts.data_ptr(), C.cast(self.weights, C.c_void_p),
+                                        C.byref(opts), int(cell), out.data_ptr(), out.numel(),
+                                        _stream_handle(stream)))
+        return out
 
     # ----------------------------------------------------- packed copies
 
@@ -295,14 +319,14 @@ class PackedVolume:
         self.luts = ds.luts[src_index].contiguous()
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
-                touched=None):
+                lanes=None):
         sc = self.ds.scene
         cam = make_camera(sc.modelview if mv is None else mv,
                           sc.projection if proj is None else proj, sc.width, sc.height)
         planes, n_clip = make_planes(sc.clip)
         fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
                          nsamples.data_ptr() if nsamples is not None else None, None)
-        opts = make_opts(sc, (1 << len(self.src_index)) - 1 if mask is None else mask)
+        opts = make_opts(sc, (1 << len(self.src_index)) - 1 if mask is None else mask, lanes)
         keep = (cam, planes, fb, opts)
         return (C.byref(self.desc), self.chains, self.luts.data_ptr(),
                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
@@ -314,7 +338,7 @@ class PackedVolume:
         check(load().isaac_render_packed(*args, _stream_handle(stream)))
 
     def render(self, mv=None, proj=None, out=None, stream=None, mask=None, want_f32=False,
-               want_nsamp=False):
+               want_nsamp=False, lanes=None):
         import torch
         W, H = self.ds.scene.width, self.ds.scene.height
         dev = self.ds.device
@@ -322,7 +346,7 @@ class PackedVolume:
             out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
         f32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if want_f32 else None
         ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
-        self.launch(self.prepare(mv, proj, out, f32, ns, mask), stream)
+        self.launch(self.prepare(mv, proj, out, f32, ns, mask, lanes), stream)
         return out, f32, ns
 
 

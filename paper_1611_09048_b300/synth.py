@@ -292,6 +292,71 @@ def source_from_zyx(arr: np.ndarray, guard: int, layout: str = "aos", name: str 
                   guard=guard, name=name)
 
 
+def value_noise(n: int, seed: int, octaves=((64, 0.5), (32, 0.3), (16, 0.2))) -> np.ndarray:
+    """Smooth seeded noise in [0, 1): random lattice values every L cells,
+    trilinearly upsampled, summed over octaves with the given weights."""
+    import torch
+    rng = np.random.default_rng(seed)
+    out = torch.zeros((n, n, n), dtype=torch.float32)
+    for L, w in octaves:
+        L = max(2, min(L, n))
+        m = n // L + 2
+        lat = torch.from_numpy(rng.uniform(0.0, 1.0, (1, 1, m, m, m)).astype(np.float32))
+        up = torch.nn.functional.interpolate(lat, size=(m - 1) * L, mode="trilinear",
+                                             align_corners=True)[0, 0, :n, :n, :n]
+        out += w * up
+    return out.numpy()
+
+
+def bubble_field(n: int = 512, frame: int = 0, seed: int = 0, noise=None,
+                 thickness: float = 6.0, speed: float = 2.0) -> np.ndarray:
+    """Laser-wakefield-like bubble: an ellipsoidal shell (semi-axes 60/60/90
+    cells at n = 512, scaled with n) of Gaussian profile and the given
+    thickness, centred on the x-y axis and moving +z by `speed` cells per frame
+    from z = 150 (scaled), plus 0.1 * seeded value noise.  Shape (z, y, x)."""
+    import torch
+    s = n / 512.0
+    ax, ay, az = 60.0 * s, 60.0 * s, 90.0 * s
+    cz = (150.0 + speed * frame) * s
+    c = torch.arange(n, dtype=torch.float32) + 0.5
+    z, y, x = c[:, None, None], c[None, :, None], c[None, None, :]
+    r = torch.sqrt(((x - n / 2) / ax) ** 2 + ((y - n / 2) / ay) ** 2 + ((z - cz) / az) ** 2)
+    d = (r - 1.0) * min(ax, ay, az)
+    sig = max(thickness * s, 1.0) / 2.0
+    shell = torch.exp(-(d * d) / (2.0 * sig * sig))
+    if noise is None:
+        noise = value_noise(n, seed + 77)
+    return (shell + 0.1 * torch.from_numpy(np.asarray(noise))).numpy().astype(np.float32)
+
+
+def bubble_lut(seed: int, alpha_max: float = 0.3) -> np.ndarray:
+    """TF for the bubble: fully transparent below a seeded threshold in
+    U(0.15, 0.35) (so the 0.1-amplitude background noise is empty space), then
+    piecewise linear through 3 seeded points with alpha U(0.02, alpha_max)."""
+    rng = np.random.default_rng(seed)
+    thr = rng.uniform(0.15, 0.35)
+    xs = np.concatenate([[0.0, thr], np.sort(rng.uniform(thr + 0.02, 1.0, 2)), [1.0]])
+    rgb = rng.uniform(0.0, 1.0, (5, 3))
+    a = np.concatenate([[0.0, 0.0], rng.uniform(0.02, alpha_max, 3)])
+    pts = np.concatenate([rgb, a[:, None]], axis=1)
+    grid = np.arange(256, dtype=np.float64) / 255.0
+    lut = np.stack([np.interp(grid, xs, pts[:, c]) for c in range(4)], axis=1)
+    lut[grid <= thr, 3] = 0.0
+    return lut.astype(np.float32)
+
+
+def scene_bubble(n: int = 512, frame: int = 0, seed: int = 0, width: int = 1920,
+                 height: int = 1080, field=None, lut_seed=None, dist_factor: float = 2.0) -> Scene:
+    """One frame of the bubble: scalar field, identity chain, seeded TF."""
+    f = bubble_field(n, frame, seed) if field is None else field
+    src = source_from_zyx(f, 0, name="bubble")
+    mv, proj = random_orbit_camera((n, n, n), width, height, seed + 1000 + frame, dist_factor)
+    lut = bubble_lut(seed + 4000 if lut_seed is None else lut_seed)
+    return Scene(n=(n, n, n), sources=[src], chains=[[]], luts=lut[None],
+                 weights=np.ones(1, np.float32), modelview=mv, projection=proj, width=width,
+                 height=height)
+
+
 # --------------------------------------------------------------------------
 # whole scenes
 # --------------------------------------------------------------------------

@@ -43,7 +43,8 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(isaac.Functor) == 4 + 4 + 16
     assert C.sizeof(isaac.Chain) == 4 + 24 * isaac.MAX_FUNCTORS
     assert C.sizeof(isaac.Camera) == 256 + 8
-    assert C.sizeof(isaac.RenderOpts) == 72 + 4 + 4 + 4 + 16 + 4
+    # 9 int64, step, interp, term_alpha, bg[4], active_mask, lanes_per_ray -> 108, 8-aligned
+    assert C.sizeof(isaac.RenderOpts) == 112
 
 
 FAKE = 0x7F0000000000  # never dereferenced: every call below fails validation first
