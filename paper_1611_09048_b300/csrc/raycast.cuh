@@ -58,13 +58,17 @@ struct KSource {
     float w;             // blend weight
 };
 
-// One entry of the compact ray list.
+// One entry of the compact ray list (same layout as the public isaac_ray).
 struct RayRec {
     float ex, ey, ez;    // local voxel position of the first sample
-    int nsteps;          // samples on the global grid inside [t_in, t_out)
+    int nsteps;          // samples on the global grid inside [t_in, t_out); march stops here
     float dx, dy, dz;    // unit direction
     int pix;             // y * W + x
+    int kbeg;            // first sample index to march (0, or a proposal's start)
+    int jf, jl;          // label mode: first / last composited sample with opacity > 0 (-1: none)
+    int reserved;
 };
+static_assert(sizeof(RayRec) == 48, "RayRec layout");
 
 // Workspace: counters, then the ray list (one record per rectangle pixel at most).
 constexpr int kWsHeader = 256;
@@ -337,6 +341,9 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
     r.ex = r.ey = r.ez = 0.0f;
     r.dx = r.dy = r.dz = 0.0f;
     r.pix = py * p.W + px;
+    r.kbeg = 0;
+    r.jf = r.jl = -1;
+    r.reserved = 0;
     const double *m = p.minv;
     const double xn = ((double)px + 0.5) * p.ndc_sx - 1.0;
     const double yn = 1.0 - ((double)py + 0.5) * p.ndc_sy;
@@ -487,7 +494,7 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
             float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
             int ns = 0;
             const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
-            for (int k = 0; k < r.nsteps; k += RL) {
+            for (int k = r.kbeg; k < r.nsteps; k += RL) {
                 const int kk = k + sub;
                 float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (kk < r.nsteps) {
