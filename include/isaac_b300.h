@@ -237,6 +237,38 @@ int isaac_opacity_grid(const isaac_source *sources, const isaac_chain *chains, i
                        const float *luts, const float *weights, const isaac_render_opts *opts,
                        int32_t cell, float *grid, int64_t grid_len, void *stream);
 
+/*
+ * isaac_render_noalloc -- the frame of isaac_render (same arguments, same
+ * kernels, same image) for callers that must not allocate device memory.
+ * The paper has no counterpart.  isaac_render allocates its per-stream ray
+ * list with cudaMalloc; in-situ hosts often cannot allow that: a simulation
+ * typically reserves nearly all device memory at start-up and serves later
+ * requests from its own pool (a library-side cudaMalloc then fails or
+ * fragments that memory), and a host rendering from inside its time-step
+ * loop may forbid allocation there because cudaMalloc can synchronise the
+ * device.  This call keeps the ray list in a fixed array compiled into the
+ * library instead (about 12 MiB of static device memory on every GPU that
+ * loads the library, held until the process exits), so it allocates and
+ * frees nothing.
+ *   Limit: the screen rectangle the local box can cover must hold at most
+ *   262,144 pixels (e.g. 512x512); beyond that the call fails with
+ *   ISAAC_ENOMEM before any launch.  The footprint output (fb->touched) is
+ *   not offered (ISAAC_ENOTSUP).
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress, which may load the library's device code);
+ *   make that first call before any stream capture.
+ *   Sharing: every call on a device uses that device's one copy of the array,
+ *   which keeps the previous call's contents; each call's first kernel resets
+ *   the counters it needs, so calls ordered one after another (one stream) are
+ *   independent, but calls on the same device that overlap on the GPU (for
+ *   example on two streams) race and corrupt each other's rays.
+ */
+int isaac_render_noalloc(const isaac_source *sources, const isaac_chain *chains,
+                         int32_t n_sources, const float *luts, const float *weights,
+                         const isaac_camera *camera, const isaac_plane *clip, int32_t n_clip,
+                         const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                         void *stream);
+
 /* Free the render workspaces of the current device (synchronises the device). */
 int isaac_release_workspaces(void);
 

@@ -26,6 +26,13 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
 int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
 int prepare_fb(const isaac_framebuffer *fb, KParams &p);
 
+// Validate the sources of isaac_render and fill their part of KParams.
+int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                    const float *luts, const float *weights, const isaac_render_opts *opts,
+                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out);
+// Zero-copy frame kernel for a source signature (nullptr if none).
+FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
+                    int *rl_used);
 // Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic).
 int choose_lanes(long long rect_pixels, int hint);
 // Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays.

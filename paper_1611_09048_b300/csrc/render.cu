@@ -109,8 +109,8 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st)
 
 // --------------------------------------------------------------- dispatch
 
-static FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
-                           int *rl_used)
+FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
+                    int *rl_used)
 {
     const ZcEntry *best = nullptr;
     for (int pass = 0; pass < 2 && !best; ++pass) {
@@ -129,10 +129,9 @@ static FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool t
     return best->fn;
 }
 
-static int prepare_sources(const isaac_source *sources, const isaac_chain *chains,
-                           int32_t n_sources, const float *luts, const float *weights,
-                           const isaac_render_opts *opts, KParams &p, int *nact_out,
-                           unsigned *sig_out, bool *wide_out)
+int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                    const float *luts, const float *weights, const isaac_render_opts *opts,
+                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out)
 {
     if (!sources || !chains || !weights)
         return fail(ISAAC_EINVAL, "sources, chains and weights are required");

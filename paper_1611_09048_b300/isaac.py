@@ -27,7 +27,7 @@ OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 # every C symbol declared in include/isaac_b300.h
 EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_layout",
            "isaac_pack", "isaac_render_packed", "isaac_release_workspaces",
-           "isaac_opacity_grid")
+           "isaac_opacity_grid", "isaac_render_noalloc")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -116,6 +116,8 @@ def load(path: Optional[str] = None):
                                            C.c_void_p, C.c_void_p, C.POINTER(RenderOpts),
                                            C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
         lib.isaac_release_workspaces.restype = C.c_int
+        lib.isaac_render_noalloc.restype = C.c_int
+        lib.isaac_render_noalloc.argtypes = lib.isaac_render.argtypes
         lib.isaac_last_error.restype = C.c_char_p
         lib.isaac_abi_version.restype = C.c_int
         _lib = lib
