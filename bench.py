@@ -323,6 +323,7 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
+        torch.cuda.nvtx.range_push(f"timed_{fmt}")
         with torch.cuda.stream(stream):
             for i in range(steps):
                 flush.zero_()
@@ -330,6 +331,7 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
                 pv.launch(prep[(args.warmup + i) % n_cam], stream)
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         ns = sum(samples[(args.warmup + i) % n_cam] for i in range(steps))
         out[fmt] = {"samples_per_s": ns / (ms * 1e-3), "ms_per_frame": ms / steps,

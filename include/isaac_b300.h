@@ -269,6 +269,117 @@ int isaac_render_noalloc(const isaac_source *sources, const isaac_chain *chains,
                          const isaac_render_opts *opts, const isaac_framebuffer *fb,
                          void *stream);
 
+/*
+ * Learned ray-interval proposal.  Not in the paper: a small MLP predicts, per
+ * ray, which part of its samples can have nonzero opacity, so the march can
+ * skip empty space; the plain march is its fallback (confidence below a
+ * threshold) and its teacher (labels).
+ *
+ * Ray record of the frame's compact ray list (what isaac_trace returns).
+ */
+typedef struct {
+    float e[3];          /* local voxel position of the ray's first sample */
+    int32_t nsteps;      /* samples on the global grid inside the box and clip planes */
+    float d[3];          /* unit direction */
+    int32_t pix;         /* pixel index y * width + x */
+    int32_t kbeg;        /* first sample marched (0 for the plain march) */
+    int32_t jf, jl;      /* first / last composited sample with opacity > 0, -1 if none */
+    int32_t reserved;
+} isaac_ray;
+
+/*
+ * Model: inputs (224) = for each of the 6 scalars e/n and d, sin and cos of
+ * pi * 2^(k/2) * s for k = 0..15 (192 values), then the max-opacity grid at
+ * 32 points e + ((i + 1/2)/32 * nsteps * step) * d, i = 0..31; network
+ * 224 -> 64 -> 64 -> 64 -> 3 with ReLU; outputs u: te = sigmoid(u0), tx =
+ * sigmoid(u1) = start / end of the visible samples as fractions of nsteps,
+ * conf = sigmoid(u2).  A confident ray (conf >= threshold) marches samples
+ * [floor(te*nsteps) - margin, ceil(tx*nsteps) + margin) clipped to the ray.
+ * Parameters (float32, ISAAC_MLP_PARAMS): W1[224][64] (input-major), b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[64][3], b4[3].
+ * Tensor-core kernels use an FP16 copy (ISAAC_MLP_HALF halves) refreshed by
+ * isaac_mlp_sync and every training step.  All buffers are device memory
+ * owned by the caller, 16-byte aligned; `step` counts Adam steps.
+ */
+#define ISAAC_MLP_PARAMS 22915
+#define ISAAC_MLP_HALF 32256
+#define ISAAC_MLP_INPUTS 224
+typedef struct {
+    float *params;
+    float *grads;        /* training only */
+    float *adam_m;       /* training only, zero-initialised by the caller */
+    float *adam_v;       /* training only, zero-initialised by the caller */
+    uint16_t *half_w;
+    int32_t step;
+} isaac_mlp;
+
+/* Refresh the FP16 kernel copy from the float32 parameters. */
+int isaac_mlp_sync(const isaac_mlp *model, void *stream);
+
+/* Inputs of n_rays records into X (device, n_rays * 224 FP16, row-major);
+ * grid as written by isaac_opacity_grid for the same volume size and cell. */
+int isaac_mlp_features(const isaac_ray *rays, int64_t n_rays, const int64_t vol_n[3], float step,
+                       const float *grid, int32_t cell, uint16_t *X, void *stream);
+
+/* Raw outputs u (device, n_rays * 3 floats) for inputs X. */
+int isaac_mlp_forward(const isaac_mlp *model, const uint16_t *X, int64_t n_rays, float *U,
+                      void *stream);
+
+/* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the batch mean of
+ * per-ray loss huber(te - ye) + huber(tx - yx) + 0.1 * BCE(conf, c), huber
+ * delta 0.02, targets ye = jf/nsteps, yx = (jl+1)/nsteps (1 and 0 for a ray
+ * with no visible sample), c = 1 when the proposed range with `margin`
+ * covers [jf, jl] (always for an empty ray).  rays supply jf, jl, nsteps.
+ * model->grads holds the batch gradient afterwards; loss_sum (device,
+ * optional) accumulates the batch's mean loss. */
+int isaac_mlp_train_step(isaac_mlp *model, const uint16_t *X, const isaac_ray *rays,
+                         int64_t n_rays, float lr, int32_t margin, float *loss_sum, void *stream);
+
+/* The interval proposal applied to one frame. */
+typedef struct {
+    const isaac_mlp *model;   /* params + half_w are read */
+    const float *grid;        /* device max-opacity grid of this frame (isaac_opacity_grid) */
+    int32_t cell;             /* its macro-cell size */
+    float threshold;          /* confidence needed to restrict a ray (e.g. 0.9) */
+    int32_t margin;           /* samples added on both sides of the proposed range */
+    int32_t *stats;           /* optional device int32[2]: += rays seen, rays restricted */
+} isaac_proposal;
+
+/*
+ * isaac_trace -- isaac_render that also returns the frame's ray list: every
+ * ray that enters the box (first sample, direction, sample count, pixel) with
+ * its visible span jf/jl (first and last composited sample with opacity > 0,
+ * counted from the ray's first sample; -1 if none).  With a proposal the
+ * records show the restricted range (kbeg, nsteps) and the span within it.
+ * rays: device array of `capacity` records (16-byte aligned); count: device
+ * int32 receiving the number of rays (records beyond capacity are dropped).
+ * The footprint output is not offered here.
+ */
+int isaac_trace(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                const float *luts, const float *weights, const isaac_camera *camera,
+                const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
+                const isaac_framebuffer *fb, const isaac_proposal *proposal, isaac_ray *rays,
+                int64_t capacity, int32_t *count, void *stream);
+
+/* isaac_render with the interval proposal: after ray setup the MLP runs on
+ * every ray of the frame (tensor cores); confident rays march only their
+ * proposed sample range (same global sample grid, so where the range covers
+ * every sample with opacity > 0 the pixel is bit-identical to isaac_render),
+ * the others the whole ray. */
+int isaac_render_learned(const isaac_source *sources, const isaac_chain *chains,
+                         int32_t n_sources, const float *luts, const float *weights,
+                         const isaac_camera *camera, const isaac_plane *clip, int32_t n_clip,
+                         const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                         const isaac_proposal *proposal, void *stream);
+
+/* isaac_render_packed with the interval proposal. */
+int isaac_render_packed_learned(const isaac_packed *vol, const isaac_chain *chains,
+                                const float *luts, const float *weights,
+                                const isaac_camera *camera, const isaac_plane *clip,
+                                int32_t n_clip, const isaac_render_opts *opts,
+                                const isaac_framebuffer *fb, const isaac_proposal *proposal,
+                                void *stream);
+
 /* Free the render workspaces of the current device (synchronises the device). */
 int isaac_release_workspaces(void);
 

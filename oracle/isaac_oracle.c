@@ -111,6 +111,8 @@ typedef struct {
     int32_t *nsamp_alt;
     double *margin;      /* 4 per pixel: entry, exit (in steps), termination (in A), nearest (in voxels) */
     int32_t *kfirst;     /* first sample index on the global grid, -1 on a miss */
+    int32_t *jspan;      /* 2 per pixel: first and last composited sample with opacity > 0,
+                            counted from the ray's first sample; -1 if none */
 } orc_outputs;
 
 /* ---------------------------------------------------------------- camera */
@@ -337,6 +339,7 @@ typedef struct {
 typedef struct {
     double C[3], A;
     int32_t n;
+    int64_t jf, jl;   /* first / last composited sample index with opacity > 0, -1 if none */
 } orc_state;
 
 /* Composite the samples k in [k_begin, k_end) starting from state *st.
@@ -373,6 +376,10 @@ static int64_t orc_march(const orc_frame *F, const double o[3], const double d[3
         if (!(a >= 0.0)) a = 0.0;
         if (a > 1.0) a = 1.0;
         if (before_stop) *before_stop = *st;
+        if (a > 0.0) {
+            if (st->jf < 0) st->jf = k;
+            st->jl = k;
+        }
         double tf = (1.0 - st->A) * a;
         for (int c = 0; c < 3; ++c) st->C[c] += tf * acc[c];
         st->A += tf;
@@ -448,7 +455,7 @@ static void orc_pixel(const orc_frame *F, int64_t pix, const orc_outputs *out, i
     }
     int raised = t_in > t0;
     double ol[3] = {o[0] - (double)p->off[0], o[1] - (double)p->off[1], o[2] - (double)p->off[2]};
-    orc_state st = {{0.0, 0.0, 0.0}, 0.0, 0};
+    orc_state st = {{0.0, 0.0, 0.0}, 0.0, 0, -1, -1};
     orc_state alt_st = st;
     if (!miss && t_in < t_out) {
         double ein = (t_in - t0) / p->step, eout = (t_out - t0) / p->step;
@@ -494,6 +501,10 @@ static void orc_pixel(const orc_frame *F, int64_t pix, const orc_outputs *out, i
     if (out->nsamp) out->nsamp[slot] = ns;
     if (out->nsamp_alt) out->nsamp_alt[slot] = ns_alt;
     if (out->kfirst) out->kfirst[slot] = (int32_t)kf_out;
+    if (out->jspan) {
+        out->jspan[slot * 2] = st.jf < 0 ? -1 : (int32_t)(st.jf - kf_out);
+        out->jspan[slot * 2 + 1] = st.jl < 0 ? -1 : (int32_t)(st.jl - kf_out);
+    }
     if (out->margin) {
         out->margin[slot * 4 + 0] = m_in;
         out->margin[slot * 4 + 1] = m_out;

@@ -52,7 +52,7 @@ class _Params(C.Structure):
 class _Outputs(C.Structure):
     _fields_ = [("rgba", C.c_void_p), ("rgba_alt", C.c_void_p), ("rgba8", C.c_void_p),
                 ("rgba8_alt", C.c_void_p), ("nsamp", C.c_void_p), ("nsamp_alt", C.c_void_p),
-                ("margin", C.c_void_p), ("kfirst", C.c_void_p)]
+                ("margin", C.c_void_p), ("kfirst", C.c_void_p), ("jspan", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -287,10 +287,11 @@ def render(scene, pixels=None, threads: int = 0, mask=None) -> dict:
         "nsamp_alt": np.zeros(shape, np.int32),
         "margin": np.zeros(shape + (4,), np.float64),
         "kfirst": np.zeros(shape, np.int32),
+        "jspan": np.zeros(shape + (2,), np.int32),
     }
     O = _Outputs(*(res[k].ctypes.data for k in
                    ("rgba", "rgba_alt", "rgba8", "rgba8_alt", "nsamp", "nsamp_alt", "margin",
-                    "kfirst")))
+                    "kfirst", "jspan")))
     if count == 0:
         return res
     rc = lib.orc_render(C.byref(P), srcs, chains, luts.ctypes.data, w.ctypes.data, n_src,

@@ -30,14 +30,22 @@ int prepare_fb(const isaac_framebuffer *fb, KParams &p);
 int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
                     const float *luts, const float *weights, const isaac_render_opts *opts,
                     KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out);
-// Zero-copy frame kernel for a source signature (nullptr if none).
-FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
+// Zero-copy frame kernel for a source signature and march mode (nullptr if none).
+FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, int mode, int rl,
                     int *rl_used);
+
+// Work inserted between ray setup and march (the interval proposal).
+struct FrameHook {
+    int (*fn)(const KParams &p, const void *arg, cudaStream_t st);
+    const void *arg;
+};
+// Validate a proposal and describe it as a hook (proposal may be null: no hook).
+int proposal_hook(const isaac_proposal *proposal, const isaac_render_opts *opts, FrameHook *hook);
 // Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic).
 int choose_lanes(long long rect_pixels, int hint);
 // Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays.
 int bind_workspace(KParams &p, cudaStream_t st);
-// Background + ray setup + march kernel `fn` (null: background only).
-int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st);
+// Background + ray setup + optional hook + march kernel `fn` (null: background only).
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook);
 
 }  // namespace isaac

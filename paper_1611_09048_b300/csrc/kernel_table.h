@@ -8,6 +8,7 @@
 namespace isaac {
 
 struct KParams;
+struct RayRec;
 using FrameLaunch = void (*)(const KParams &, dim3, cudaStream_t);
 
 struct ZcEntry {
@@ -16,7 +17,7 @@ struct ZcEntry {
     int interp;
     int rl;              // lanes per ray
     bool wide;           // 64-bit element offsets
-    bool touch;          // records the footprint bitmap
+    int mode;            // MODE_PLAIN, MODE_TOUCH (footprint) or MODE_LABEL (visible span)
     FrameLaunch fn;
 };
 
@@ -25,5 +26,6 @@ extern const int k_n_zc_entries;
 
 void launch_fill(const KParams &p, cudaStream_t st);
 void launch_setup(const KParams &p, cudaStream_t st);
+void launch_copy_rays(const KParams &p, RayRec *out, long long cap, int *count, cudaStream_t st);
 
 }  // namespace isaac

@@ -1,0 +1,565 @@
+// mlp.cu -- kernels and entry points of the learned ray-interval proposal:
+// FP16 weight copy, input features, forward pass, one fused forward+backward
+// training pass with gradient accumulation, Adam.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.h"
+#include "mlp.cuh"
+
+namespace isaac {
+
+constexpr float kHuberDelta = 0.02f, kConfWeight = 0.1f;
+
+// ----------------------------------------------------------- FP16 copy
+
+static __global__ void k_mlp_half(const float *__restrict__ p, __half *__restrict__ h)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_HALF; i += gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        if (i < H_T2) {                       // T1[n][k] = W1[k][n]
+            const int n = i / MLP_IN, k = i % MLP_IN;
+            v = p[P_W1 + k * MLP_W + n];
+        } else if (i < H_T3) {
+            const int j = i - H_T2, n = j / MLP_W, k = j % MLP_W;
+            v = p[P_W2 + k * MLP_W + n];
+        } else if (i < H_T4) {
+            const int j = i - H_T3, n = j / MLP_W, k = j % MLP_W;
+            v = p[P_W3 + k * MLP_W + n];
+        } else if (i < H_B2) {                // T4[n][k] = W4[k][n], n < 3
+            const int j = i - H_T4, n = j / MLP_W, k = j % MLP_W;
+            v = n < MLP_OUT ? p[P_W4 + k * MLP_OUT + n] : 0.0f;
+        } else if (i < H_B3) {
+            v = p[P_W2 + (i - H_B2)];
+        } else if (i < H_B4) {
+            v = p[P_W3 + (i - H_B3)];
+        } else {                              // B4[in][o] = W4[in][o], o < 3
+            const int j = i - H_B4, in = j / 16, o = j % 16;
+            v = o < MLP_OUT ? p[P_W4 + in * MLP_OUT + o] : 0.0f;
+        }
+        h[i] = __float2half_rn(v);
+    }
+}
+
+// ------------------------------------------------------------ features
+
+struct KFeat {
+    const RayRec *rays;
+    long long n;
+    float step;
+    const float *grid;
+    int cell, gx, gy, gz;
+    float nx, ny, nz;
+    __half *X;
+};
+
+static __global__ void k_mlp_features(const __grid_constant__ KFeat p)
+{
+    const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 1;
+    if (i >= p.n) return;
+    const RayRec r = p.rays[i];
+    ray_features_half(r, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, p.nx, p.ny, p.nz, threadIdx.x & 1,
+                      p.X + i * MLP_IN);
+}
+
+// ---------------------------------------------------------------- forward
+
+struct KFwd {
+    const __half *hw;
+    const float *params;
+    const __half *X;
+    long long n;
+    float *U;
+};
+
+constexpr int kFwdSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + 64 * LD_IN;
+
+static __global__ void __launch_bounds__(128) k_mlp_forward(const __grid_constant__ KFwd p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __half *sT1 = reinterpret_cast<__half *>(smem_raw);
+    __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
+    __half *xs = sT4 + 8 * LD_W;
+    load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    for (long long base = blockIdx.x * 64LL; base < p.n; base += gridDim.x * 64LL) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 64 * MLP_IN; i += blockDim.x) {
+            const long long r = base + i / MLP_IN;
+            xs[(i / MLP_IN) * LD_IN + i % MLP_IN] = r < p.n ? p.X[r * MLP_IN + i % MLP_IN] : __float2half_rn(0.0f);
+        }
+        __syncthreads();
+        float u[4];
+        mlp_forward_warp(xs, warp * 16, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr,
+                         nullptr, 0);
+        const long long r0 = base + warp * 16 + g, r1 = r0 + 8;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = 2 * t + j;
+            if (col < MLP_OUT) {
+                if (r0 < p.n) p.U[r0 * MLP_OUT + col] = u[j];
+                if (r1 < p.n) p.U[r1 * MLP_OUT + col] = u[2 + j];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- training
+
+struct KTrain {
+    const __half *hw;
+    const float *params;
+    float *grads;
+    const __half *X;
+    const RayRec *rays;       // jf, jl, nsteps of every training ray
+    long long n;
+    float inv_n;
+    int margin;
+    float *loss_sum;          // optional
+};
+
+constexpr int kTrainSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W   // forward weights
+                                 + 2 * MLP_W * LD_W + MLP_W * LD_B4             // backward weights
+                                 + 64 * LD_IN + MLP_IN * LD_R                   // X, X^T
+                                 + 6 * MLP_W * LD_R + 8 * LD_R;                 // h^T, dA^T tiles
+constexpr int kTrainSmemBytes = kTrainSmemHalves * 2 + 3 * 64 * 4;
+
+__device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + __expf(-x)); }
+
+__device__ __forceinline__ float dhuber(float r)
+{
+    return fabsf(r) < kHuberDelta ? r / kHuberDelta : (r > 0.0f ? 1.0f : (r < 0.0f ? -1.0f : 0.0f));
+}
+
+__device__ __forceinline__ float huberf(float r)
+{
+    const float a = fabsf(r);
+    return a < kHuberDelta ? 0.5f * r * r / kHuberDelta : a - 0.5f * kHuberDelta;
+}
+
+// Per-ray output gradient (without the 1/N of the batch mean) and loss.
+__device__ __forceinline__ void ray_grad(float u0, float u1, float u2, int jf, int jl, int ns,
+                                         int margin, bool valid, float &d0, float &d1, float &d2,
+                                         float &loss)
+{
+    d0 = d1 = d2 = loss = 0.0f;
+    if (!valid) return;
+    const float te = sigmoidf(u0), tx = sigmoidf(u1), conf = sigmoidf(u2);
+    const bool empty = jf < 0;
+    const float ye = empty ? 1.0f : (float)jf / (float)ns;
+    const float yx = empty ? 0.0f : (float)(jl + 1) / (float)ns;
+    float c = 1.0f;
+    if (!empty) {
+        const float kb = floorf(te * (float)ns) - (float)margin;
+        const float ke = ceilf(tx * (float)ns) + (float)margin;
+        c = (kb <= (float)jf && ke >= (float)(jl + 1)) ? 1.0f : 0.0f;
+    }
+    d0 = dhuber(te - ye) * te * (1.0f - te);
+    d1 = dhuber(tx - yx) * tx * (1.0f - tx);
+    d2 = kConfWeight * (conf - c);
+    const float bce = -(c * __logf(fmaxf(conf, 1e-30f)) + (1.0f - c) * __logf(fmaxf(1.0f - conf, 1e-30f)));
+    loss = huberf(te - ye) + huberf(tx - yx) + kConfWeight * bce;
+}
+
+// dA of one layer: (dA_next . W^T) masked by the layer's ReLU; returns the
+// accumulators and stores them transposed (output-major) for the weight grads.
+__device__ __forceinline__ void backward_layer(const unsigned (&A)[4][4], int ksteps, const __half *bt,
+                                               int ldb, unsigned mask, float (&c)[8][4],
+                                               __half *dt, int col0)
+{
+    const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            unsigned b[2];
+            frag_b(bt, ldb, nt * 8, ks * 16, b);
+            mma16816(c[nt], A[ks], b);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (!((mask >> (nt * 4 + j)) & 1u)) c[nt][j] = 0.0f;
+        const int f = nt * 8 + 2 * t;
+        dt[f * LD_R + col0 + g] = __float2half_rn(c[nt][0]);
+        dt[(f + 1) * LD_R + col0 + g] = __float2half_rn(c[nt][1]);
+        dt[f * LD_R + col0 + g + 8] = __float2half_rn(c[nt][2]);
+        dt[(f + 1) * LD_R + col0 + g + 8] = __float2half_rn(c[nt][3]);
+    }
+}
+
+static __global__ void __launch_bounds__(128) k_mlp_train(const __grid_constant__ KTrain p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __half *sT1 = reinterpret_cast<__half *>(smem_raw);
+    __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
+    __half *sB2 = sT4 + 8 * LD_W, *sB3 = sB2 + MLP_W * LD_W, *sB4 = sB3 + MLP_W * LD_W;
+    __half *xs = sB4 + MLP_W * LD_B4, *xt = xs + 64 * LD_IN;
+    __half *h1t = xt + MLP_IN * LD_R, *h2t = h1t + MLP_W * LD_R, *h3t = h2t + MLP_W * LD_R;
+    __half *d1t = h3t + MLP_W * LD_R, *d2t = d1t + MLP_W * LD_R, *d3t = d2t + MLP_W * LD_R;
+    __half *d4t = d3t + MLP_W * LD_R;
+    int *s_jf = reinterpret_cast<int *>(d4t + 8 * LD_R), *s_jl = s_jf + 64, *s_ns = s_jl + 64;
+
+    load_weights_smem(p.hw, sT1, sT2, sT3, sT4, sB2, sB3, sB4);
+    const long long base = blockIdx.x * 64LL;
+    for (int i = threadIdx.x; i < 64 * MLP_IN; i += blockDim.x) {
+        const int rr = i / MLP_IN, k = i % MLP_IN;
+        const long long r = base + rr;
+        const __half v = r < p.n ? p.X[r * MLP_IN + k] : __float2half_rn(0.0f);
+        xs[rr * LD_IN + k] = v;
+        xt[k * LD_R + rr] = v;
+    }
+    for (int i = threadIdx.x; i < 8 * LD_R; i += blockDim.x) d4t[i] = __float2half_rn(0.0f);
+    if (threadIdx.x < 64) {
+        const long long r = base + threadIdx.x;
+        const bool ok = r < p.n;
+        s_jf[threadIdx.x] = ok ? p.rays[r].jf : -1;
+        s_jl[threadIdx.x] = ok ? p.rays[r].jl : -1;
+        s_ns[threadIdx.x] = ok ? p.rays[r].nsteps : 0;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int col0 = warp * 16;
+    Hidden hid;
+    float u[4];
+    mlp_forward_warp(xs, col0, sT1, sT2, sT3, sT4, p.params, u, &hid, h1t, h2t, h3t, col0);
+
+    // output gradient of rays col0+g and col0+g+8 (computed on lanes t == 0)
+    const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1), u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
+    float da[3] = {0, 0, 0}, db[3] = {0, 0, 0}, la = 0.0f, lb = 0.0f;
+    if (t == 0) {
+        const int ra = col0 + g, rb = ra + 8;
+        ray_grad(u[0], u[1], u2a, s_jf[ra], s_jl[ra], s_ns[ra], p.margin, base + ra < p.n, da[0],
+                 da[1], da[2], la);
+        ray_grad(u[2], u[3], u2b, s_jf[rb], s_jl[rb], s_ns[rb], p.margin, base + rb < p.n, db[0],
+                 db[1], db[2], lb);
+        for (int o = 0; o < 3; ++o) {
+            d4t[o * LD_R + ra] = __float2half_rn(da[o]);
+            d4t[o * LD_R + rb] = __float2half_rn(db[o]);
+        }
+        if (p.loss_sum) atomicAdd(p.loss_sum, (la + lb) * p.inv_n);
+    }
+    const float da2 = __shfl_up_sync(0xffffffffu, da[2], 1), db2 = __shfl_up_sync(0xffffffffu, db[2], 1);
+    unsigned A4[4][4];
+    for (int j = 0; j < 4; ++j)
+        for (int q = 0; q < 4; ++q) A4[j][q] = 0u;
+    if (t == 0) {
+        A4[0][0] = pack_h2(da[0], da[1]);
+        A4[0][1] = pack_h2(db[0], db[1]);
+    } else if (t == 1) {
+        A4[0][0] = pack_h2(da2, 0.0f);
+        A4[0][1] = pack_h2(db2, 0.0f);
+    }
+    float c[8][4];
+    unsigned A[4][4];
+    backward_layer(A4, 1, sB4, LD_B4, hid.m3, c, d3t, col0);        // dA3
+    for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
+    backward_layer(A, 4, sB3, LD_W, hid.m2, c, d2t, col0);          // dA2
+    for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
+    backward_layer(A, 4, sB2, LD_W, hid.m1, c, d1t, col0);          // dA1
+    __syncthreads();
+
+    // weight gradients over the block's 64 rays: dW = H^T . dA (jobs = m-tiles)
+    // layer 4: 4 m-tiles x 1 n-tile, layers 3, 2: 4 x 8, layer 1: 14 x 8
+    for (int job = warp; job < 26; job += 4) {
+        const __half *at, *bt;
+        int mt, nts, wo, out_dim;
+        if (job < 4) {
+            at = h3t; bt = d4t; mt = job; nts = 1; wo = P_W4; out_dim = MLP_OUT;
+        } else if (job < 8) {
+            at = h2t; bt = d3t; mt = job - 4; nts = 8; wo = P_W3; out_dim = MLP_W;
+        } else if (job < 12) {
+            at = h1t; bt = d2t; mt = job - 8; nts = 8; wo = P_W2; out_dim = MLP_W;
+        } else {
+            at = xt; bt = d1t; mt = job - 12; nts = 8; wo = P_W1; out_dim = MLP_W;
+        }
+        float acc[8][4];
+        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+        for (int ks = 0; ks < 4; ++ks) {
+            unsigned a[4];
+            frag_a(at, LD_R, mt * 16, ks * 16, a);
+            for (int nt = 0; nt < nts; ++nt) {
+                unsigned b[2];
+                frag_b(bt, LD_R, nt * 8, ks * 16, b);
+                mma16816(acc[nt], a, b);
+            }
+        }
+        for (int nt = 0; nt < nts; ++nt)
+            for (int j = 0; j < 4; ++j) {
+                const int in = mt * 16 + g + (j >= 2 ? 8 : 0);
+                const int out = nt * 8 + 2 * t + (j & 1);
+                if (out < out_dim) atomicAdd(p.grads + wo + in * out_dim + out, acc[nt][j] * p.inv_n);
+            }
+    }
+    // bias gradients: sum of dA over the block's rays
+    for (int o = threadIdx.x; o < 3 * MLP_W + MLP_OUT; o += blockDim.x) {
+        const __half *row;
+        int bo;
+        if (o < MLP_W) { row = d1t + o * LD_R; bo = P_B1 + o; }
+        else if (o < 2 * MLP_W) { row = d2t + (o - MLP_W) * LD_R; bo = P_B2 + o - MLP_W; }
+        else if (o < 3 * MLP_W) { row = d3t + (o - 2 * MLP_W) * LD_R; bo = P_B3 + o - 2 * MLP_W; }
+        else { row = d4t + (o - 3 * MLP_W) * LD_R; bo = P_B4 + o - 3 * MLP_W; }
+        float s = 0.0f;
+        for (int r = 0; r < 64; ++r) s += __half2float(row[r]);
+        atomicAdd(p.grads + bo, s * p.inv_n);
+    }
+}
+
+// ------------------------------------------------------------------- Adam
+
+static __global__ void k_adam(float *p, const float *g, float *m, float *v, float lr, float b1,
+                              float b2, float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_PARAMS; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace isaac
+
+using namespace isaac;
+
+static int check_model(const isaac_mlp *m, bool train)
+{
+    if (!m || !m->params || !m->half_w) return fail(ISAAC_EINVAL, "model params and half_w are required");
+    if (train && (!m->grads || !m->adam_m || !m->adam_v))
+        return fail(ISAAC_EINVAL, "training needs grads, adam_m and adam_v");
+    if (((uintptr_t)m->half_w) % 16 || ((uintptr_t)m->params) % 16)
+        return fail(ISAAC_EINVAL, "model buffers must be 16-byte aligned");
+    return ISAAC_OK;
+}
+
+extern "C" int isaac_mlp_sync(const isaac_mlp *m, void *stream)
+{
+    clear_error();
+    int rc = check_model(m, false);
+    if (rc) return rc;
+    k_mlp_half<<<64, 256, 0, (cudaStream_t)stream>>>(m->params, reinterpret_cast<__half *>(m->half_w));
+    return check_cuda("isaac_mlp_sync");
+}
+
+extern "C" int isaac_mlp_features(const isaac_ray *rays, int64_t n_rays, const int64_t vol_n[3],
+                                  float step, const float *grid, int32_t cell, uint16_t *X,
+                                  void *stream)
+{
+    clear_error();
+    if (n_rays < 0 || (n_rays > 0 && (!rays || !grid || !X || !vol_n)))
+        return fail(ISAAC_EINVAL, "rays, grid, X and vol_n are required");
+    if (cell < 1 || !(step > 0.0f)) return fail(ISAAC_EINVAL, "cell and step must be positive");
+    if (n_rays == 0) return ISAAC_OK;
+    if (((uintptr_t)X) % 4) return fail(ISAAC_EINVAL, "X must be 4-byte aligned");
+    KFeat p;
+    p.rays = reinterpret_cast<const RayRec *>(rays);
+    p.n = n_rays;
+    p.step = step;
+    p.grid = grid;
+    p.cell = cell;
+    p.gx = (int)((vol_n[0] + cell - 1) / cell);
+    p.gy = (int)((vol_n[1] + cell - 1) / cell);
+    p.gz = (int)((vol_n[2] + cell - 1) / cell);
+    p.nx = (float)vol_n[0];
+    p.ny = (float)vol_n[1];
+    p.nz = (float)vol_n[2];
+    p.X = reinterpret_cast<__half *>(X);
+    const long long threads = 2 * n_rays;
+    k_mlp_features<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(p);
+    return check_cuda("isaac_mlp_features");
+}
+
+extern "C" int isaac_mlp_forward(const isaac_mlp *m, const uint16_t *X, int64_t n_rays, float *U,
+                                 void *stream)
+{
+    clear_error();
+    int rc = check_model(m, false);
+    if (rc) return rc;
+    if (n_rays <= 0) return n_rays == 0 ? ISAAC_OK : fail(ISAAC_EINVAL, "negative ray count");
+    if (!X || !U || ((uintptr_t)X) % 4) return fail(ISAAC_EINVAL, "X (4-byte aligned) and U are required");
+    KFwd p;
+    p.hw = reinterpret_cast<const __half *>(m->half_w);
+    p.params = m->params;
+    p.X = reinterpret_cast<const __half *>(X);
+    p.n = n_rays;
+    p.U = U;
+    const int smem = kFwdSmemHalves * 2;
+    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const long long blocks = std::min<long long>((n_rays + 63) / 64, 148LL * 2);
+    k_mlp_forward<<<(unsigned)blocks, 128, smem, (cudaStream_t)stream>>>(p);
+    return check_cuda("isaac_mlp_forward");
+}
+
+extern "C" int isaac_mlp_train_step(isaac_mlp *m, const uint16_t *X, const isaac_ray *rays,
+                                    int64_t n_rays, float lr, int32_t margin, float *loss_sum,
+                                    void *stream)
+{
+    clear_error();
+    int rc = check_model(m, true);
+    if (rc) return rc;
+    if (n_rays <= 0 || !X || !rays) return fail(ISAAC_EINVAL, "X, rays and a positive count are required");
+    if (((uintptr_t)X) % 4) return fail(ISAAC_EINVAL, "X must be 4-byte aligned");
+    if (!std::isfinite(lr) || lr < 0.0f) return fail(ISAAC_EINVAL, "lr must be finite and >= 0");
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(m->grads, 0, N_PARAMS * sizeof(float), st) != cudaSuccess)
+        return check_cuda("grad reset");
+    KTrain p;
+    p.hw = reinterpret_cast<const __half *>(m->half_w);
+    p.params = m->params;
+    p.grads = m->grads;
+    p.X = reinterpret_cast<const __half *>(X);
+    p.rays = reinterpret_cast<const RayRec *>(rays);
+    p.n = n_rays;
+    p.inv_n = 1.0f / (float)n_rays;
+    p.margin = margin;
+    p.loss_sum = loss_sum;
+    cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmemBytes);
+    k_mlp_train<<<(unsigned)((n_rays + 63) / 64), 128, kTrainSmemBytes, st>>>(p);
+    rc = check_cuda("isaac_mlp_train_step (gradients)");
+    if (rc) return rc;
+    m->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    k_adam<<<64, 256, 0, st>>>(m->params, m->grads, m->adam_m, m->adam_v, lr, (float)b1, (float)b2,
+                               1e-8f, (float)(1.0 - std::pow(b1, m->step)),
+                               (float)(1.0 - std::pow(b2, m->step)));
+    k_mlp_half<<<64, 256, 0, st>>>(m->params, reinterpret_cast<__half *>(m->half_w));
+    return check_cuda("isaac_mlp_train_step (update)");
+}
+
+// ------------------------------------------------- proposal inside a frame
+
+namespace isaac {
+
+struct KPropose {
+    WsCounters *ctr;
+    RayRec *rays;
+    const __half *hw;
+    const float *params;
+    const float *grid;
+    int cell, gx, gy, gz;
+    float step, nx, ny, nz;
+    float threshold;
+    int margin;
+    int *stats;
+};
+
+constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + 4 * 16 * LD_IN;
+
+// Persistent warps take 16 rays of the frame's ray list at a time: inputs
+// (2 lanes per ray) into the warp's shared tile, the MLP forward pass, then
+// the decision on lanes holding (u0, u1) of rays g and g+8.
+static __global__ void __launch_bounds__(128) k_mlp_propose(const __grid_constant__ KPropose p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __half *sT1 = reinterpret_cast<__half *>(smem_raw);
+    __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
+    __half *xs_all = sT4 + 8 * LD_W;
+    load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    __half *xs = xs_all + warp * 16 * LD_IN;
+    const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
+    int seen = 0, restricted = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctr->next_prop, 16u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        {
+            const unsigned r = base + (lane >> 1);
+            __half *row = xs + (lane >> 1) * LD_IN;
+            if (r < n) {
+                const RayRec rec = p.rays[r];
+                ray_features_half(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, p.nx, p.ny, p.nz,
+                                  lane & 1, row);
+            } else {
+                for (int i = (lane & 1); i < MLP_IN; i += 2) row[i] = __float2half_rn(0.0f);
+            }
+        }
+        __syncwarp();
+        float u[4];
+        mlp_forward_warp(xs, 0, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr, nullptr, 0);
+        const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1);
+        const float u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
+        if (t == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned r = base + g + 8 * h;
+                if (r >= n) continue;
+                ++seen;
+                const float conf = sigmoidf(h ? u2b : u2a);
+                if (conf < p.threshold) continue;
+                const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
+                const int ns = p.rays[r].nsteps;
+                int kb = (int)floorf(te * (float)ns) - p.margin;
+                int ke = (int)ceilf(tx * (float)ns) + p.margin;
+                kb = min(max(kb, 0), ns);
+                ke = min(max(ke, kb), ns);
+                p.rays[r].kbeg = kb;
+                p.rays[r].nsteps = ke;
+                ++restricted;
+            }
+        }
+        __syncwarp();
+    }
+    if (p.stats && t == 0 && (seen | restricted)) {
+        atomicAdd(p.stats, seen);
+        atomicAdd(p.stats + 1, restricted);
+    }
+}
+
+static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
+{
+    const isaac_proposal *pr = static_cast<const isaac_proposal *>(arg);
+    KPropose p;
+    p.ctr = fp.ctr;
+    p.rays = fp.rays;
+    p.hw = reinterpret_cast<const __half *>(pr->model->half_w);
+    p.params = pr->model->params;
+    p.grid = pr->grid;
+    p.cell = pr->cell;
+    p.gx = (fp.nx + pr->cell - 1) / pr->cell;
+    p.gy = (fp.ny + pr->cell - 1) / pr->cell;
+    p.gz = (fp.nz + pr->cell - 1) / pr->cell;
+    p.step = fp.step;
+    p.nx = (float)fp.nx;
+    p.ny = (float)fp.ny;
+    p.nz = (float)fp.nz;
+    p.threshold = pr->threshold;
+    p.margin = pr->margin;
+    p.stats = pr->stats;
+    const int smem = kPropSmemHalves * 2;
+    cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+    const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
+    const long long blocks = std::max(1LL, std::min<long long>((rect + 63) / 64, (long long)sms * 2));
+    k_mlp_propose<<<(unsigned)blocks, 128, smem, st>>>(p);
+    return check_cuda("interval proposal launch");
+}
+
+int proposal_hook(const isaac_proposal *pr, const isaac_render_opts *opts, FrameHook *hook)
+{
+    hook->fn = nullptr;
+    hook->arg = nullptr;
+    if (!pr) return ISAAC_OK;
+    int rc = check_model(pr->model, false);
+    if (rc) return rc;
+    if (!pr->grid || pr->cell < 1) return fail(ISAAC_EINVAL, "proposal needs a grid and a cell size >= 1");
+    if (!(pr->threshold >= 0.0f) || pr->margin < 0)
+        return fail(ISAAC_EINVAL, "proposal threshold must be >= 0 and margin >= 0");
+    if (((uintptr_t)pr->stats) % 4) return fail(ISAAC_EINVAL, "proposal stats misaligned");
+    (void)opts;
+    hook->fn = launch_propose;
+    hook->arg = pr;
+    return ISAAC_OK;
+}
+
+}  // namespace isaac

@@ -152,13 +152,12 @@ extern "C" int isaac_pack(const isaac_source *sources, int32_t n_sources, uint32
     return ISAAC_OK;
 }
 
-extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains,
-                                   const float *luts, const float *weights,
-                                   const isaac_camera *camera, const isaac_plane *clip,
-                                   int32_t n_clip, const isaac_render_opts *opts,
-                                   const isaac_framebuffer *fb, void *stream)
+static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains,
+                              const float *luts, const float *weights, const isaac_camera *camera,
+                              const isaac_plane *clip, int32_t n_clip,
+                              const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                              void *stream, const isaac_proposal *proposal)
 {
-    clear_error();
     if (!vol || !chains || !weights || !opts)
         return fail(ISAAC_EINVAL, "vol, chains, weights and opts are required");
     const PackedTable *T = table_for(vol->dtype);
@@ -236,5 +235,33 @@ extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *c
         fn = best->fn;
         rl = best->rl;
     }
-    return launch_frame_with(p, fn, rl, (cudaStream_t)stream);
+    if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered for packed copies");
+    FrameHook hook;
+    rc = proposal_hook(proposal, opts, &hook);
+    if (rc) return rc;
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream, proposal ? &hook : nullptr);
+}
+
+extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains,
+                                   const float *luts, const float *weights,
+                                   const isaac_camera *camera, const isaac_plane *clip,
+                                   int32_t n_clip, const isaac_render_opts *opts,
+                                   const isaac_framebuffer *fb, void *stream)
+{
+    clear_error();
+    return render_packed_impl(vol, chains, luts, weights, camera, clip, n_clip, opts, fb, stream,
+                              nullptr);
+}
+
+extern "C" int isaac_render_packed_learned(const isaac_packed *vol, const isaac_chain *chains,
+                                           const float *luts, const float *weights,
+                                           const isaac_camera *camera, const isaac_plane *clip,
+                                           int32_t n_clip, const isaac_render_opts *opts,
+                                           const isaac_framebuffer *fb,
+                                           const isaac_proposal *proposal, void *stream)
+{
+    clear_error();
+    if (!proposal) return fail(ISAAC_EINVAL, "proposal is required");
+    return render_packed_impl(vol, chains, luts, weights, camera, clip, n_clip, opts, fb, stream,
+                              proposal);
 }

@@ -75,7 +75,11 @@ constexpr int kWsHeader = 256;
 struct WsCounters {
     unsigned n_rays;     // appended by k_setup_rays
     unsigned next;       // next list entry to march (k_raycast)
+    unsigned next_prop;  // next list entry for the interval proposal
 };
+
+// March modes: plain, footprint bitmap, visible-span labels.
+enum : int { MODE_PLAIN = 0, MODE_TOUCH = 1, MODE_LABEL = 2 };
 
 struct KParams {
     double minv[16];                 // inverse of projection * modelview, column-major
@@ -435,6 +439,7 @@ static __global__ void k_fill_background(const __grid_constant__ KParams p)
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.ctr) {
         p.ctr->n_rays = 0u;
         p.ctr->next = 0u;
+        p.ctr->next_prop = 0u;
     }
     const size_t total = (size_t)p.W * (size_t)p.H;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
@@ -476,7 +481,7 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
 // group evaluate samples k+0 .. k+RL-1 of their ray together; every lane then
 // composites the group's RL samples in order, stopping at the termination
 // sample, so all lanes hold the same C and A.
-template <int NACT, class Shader, int RL>
+template <int NACT, class Shader, int RL, bool LABEL = false>
 __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
 {
     constexpr int RAYS = 32 / RL;
@@ -492,7 +497,7 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
         if (idx < n_rays) {
             const RayRec r = p.rays[idx];
             float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-            int ns = 0;
+            int ns = 0, jf = -1, jl = -1;
             const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
             for (int k = r.kbeg; k < r.nsteps; k += RL) {
                 const int kk = k + sub;
@@ -514,6 +519,10 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
                     }
                     if (!done && k + j < r.nsteps) {
                         const float a = clamp01(cj.w);
+                        if (LABEL && a > 0.0f) {
+                            if (jf < 0) jf = k + j;
+                            jl = k + j;
+                        }
                         const float t = (1.0f - A) * a;
                         C0 = fmaf(t, cj.x, C0);
                         C1 = fmaf(t, cj.y, C1);
@@ -525,7 +534,13 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
                 }
                 if (done) break;
             }
-            if (sub == 0) write_pixel(p, r.pix, C0, C1, C2, A, ns);
+            if (sub == 0) {
+                write_pixel(p, r.pix, C0, C1, C2, A, ns);
+                if (LABEL) {
+                    p.rays[idx].jf = jf;
+                    p.rays[idx].jl = jl;
+                }
+            }
         }
     }
 }
@@ -538,12 +553,25 @@ __device__ __forceinline__ void load_luts(const KParams &p, float4 *s_lut)
 }
 
 // The zero-copy frame kernel (128 threads, at most 64 registers per thread).
-template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, bool TOUCH = false>
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, int MODE = MODE_PLAIN>
 __global__ void __launch_bounds__(128, 8) k_raycast(const __grid_constant__ KParams p)
 {
     __shared__ float4 s_lut[NACT * 256];
     load_luts<NACT>(p, s_lut);
-    march<NACT, ZeroCopyShader<NACT, SIG, INTERP, Idx, TOUCH>, RL>(p, s_lut);
+    march<NACT, ZeroCopyShader<NACT, SIG, INTERP, Idx, MODE == MODE_TOUCH>, RL, MODE == MODE_LABEL>(
+        p, s_lut);
+}
+
+// Copy the ray list (at most `cap` records) and its length out of the workspace.
+static __global__ void k_copy_rays(const __grid_constant__ KParams p, RayRec *out, long long cap,
+                                   int *count)
+{
+    const unsigned n = p.ctr->n_rays;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = (int)n;
+    const long long m = min((long long)n, cap);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = p.rays[i];
 }
 
 }  // namespace isaac

@@ -5,31 +5,33 @@
 
 namespace isaac {
 
-template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, bool TOUCH>
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, int MODE>
 static void launch_zc(const KParams &p, dim3 grid, cudaStream_t st)
 {
-    k_raycast<NACT, SIG, INTERP, Idx, RL, TOUCH><<<grid, 128, 0, st>>>(p);
+    k_raycast<NACT, SIG, INTERP, Idx, RL, MODE><<<grid, 128, 0, st>>>(p);
 }
 
-// {nact, sig, interp, rl, wide, touch, launcher}
-#define ISAAC_Z(N, S, I, R, W, T) \
-    {N, S, I, R, W, T, launch_zc<N, S, I, std::conditional_t<W, long long, int>, R, T>}
-#define ISAAC_Z2(N, S, R, W, T) ISAAC_Z(N, S, 0, R, W, T), ISAAC_Z(N, S, 1, R, W, T)
+// {nact, sig, interp, rl, wide, mode, launcher}
+#define ISAAC_Z(N, S, I, R, W, M) \
+    {N, S, I, R, W, M, launch_zc<N, S, I, std::conditional_t<W, long long, int>, R, M>}
+#define ISAAC_Z2(N, S, R, W, M) ISAAC_Z(N, S, 0, R, W, M), ISAAC_Z(N, S, 1, R, W, M)
 // Precompiled source signatures (Sec. 3.2 compiles the source loop for the
 // application's source list): one scalar; E, B, rho in AoS and in component
 // planes.  Anything else runs the generic kernel with run-time f_dim.
 static const ZcEntry k_entries[] = {
-    ISAAC_Z2(1, 0x9u, 1, false, false), ISAAC_Z2(1, 0x9u, 2, false, false),
-    ISAAC_Z2(1, 0x9u, 4, false, false),
-    ISAAC_Z2(3, 0x9BBu, 1, false, false), ISAAC_Z2(3, 0x9BBu, 2, false, false),
-    ISAAC_Z2(3, 0x9BBu, 4, false, false),
-    ISAAC_Z2(3, 0x933u, 2, false, false),
-    ISAAC_Z2(1, 0u, 2, false, false), ISAAC_Z2(2, 0u, 2, false, false),
-    ISAAC_Z2(3, 0u, 2, false, false), ISAAC_Z2(4, 0u, 2, false, false),
-    ISAAC_Z2(1, 0u, 2, true, false), ISAAC_Z2(2, 0u, 2, true, false),
-    ISAAC_Z2(3, 0u, 2, true, false), ISAAC_Z2(4, 0u, 2, true, false),
-    ISAAC_Z2(1, 0u, 1, false, true), ISAAC_Z2(2, 0u, 1, false, true),
-    ISAAC_Z2(3, 0u, 1, false, true), ISAAC_Z2(4, 0u, 1, false, true),
+    ISAAC_Z2(1, 0x9u, 1, false, MODE_PLAIN), ISAAC_Z2(1, 0x9u, 2, false, MODE_PLAIN),
+    ISAAC_Z2(1, 0x9u, 4, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0x9BBu, 1, false, MODE_PLAIN), ISAAC_Z2(3, 0x9BBu, 2, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0x9BBu, 4, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0x933u, 4, false, MODE_PLAIN),
+    ISAAC_Z2(1, 0u, 4, false, MODE_PLAIN), ISAAC_Z2(2, 0u, 4, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0u, 4, false, MODE_PLAIN), ISAAC_Z2(4, 0u, 4, false, MODE_PLAIN),
+    ISAAC_Z2(1, 0u, 4, true, MODE_PLAIN), ISAAC_Z2(2, 0u, 4, true, MODE_PLAIN),
+    ISAAC_Z2(3, 0u, 4, true, MODE_PLAIN), ISAAC_Z2(4, 0u, 4, true, MODE_PLAIN),
+    ISAAC_Z2(1, 0u, 1, false, MODE_TOUCH), ISAAC_Z2(2, 0u, 1, false, MODE_TOUCH),
+    ISAAC_Z2(3, 0u, 1, false, MODE_TOUCH), ISAAC_Z2(4, 0u, 1, false, MODE_TOUCH),
+    ISAAC_Z2(1, 0u, 4, false, MODE_LABEL), ISAAC_Z2(2, 0u, 4, false, MODE_LABEL),
+    ISAAC_Z2(3, 0u, 4, false, MODE_LABEL), ISAAC_Z2(4, 0u, 4, false, MODE_LABEL),
 };
 #undef ISAAC_Z2
 #undef ISAAC_Z
@@ -37,7 +39,7 @@ static const ZcEntry k_entries[] = {
 extern const ZcEntry *const k_zc_entries = k_entries;
 extern const int k_n_zc_entries = (int)(sizeof(k_entries) / sizeof(k_entries[0]));
 
-// The setup and background kernels are launched from this translation unit.
+// The setup, background and copy kernels are launched from this translation unit.
 void launch_fill(const KParams &p, cudaStream_t st)
 {
     const int blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
@@ -48,6 +50,12 @@ void launch_setup(const KParams &p, cudaStream_t st)
 {
     const int tiles = ((p.rx1 - p.rx0 + 15) / 16) * ((p.ry1 - p.ry0 + 7) / 8);
     k_setup_rays<<<tiles, 128, 0, st>>>(p);
+}
+
+void launch_copy_rays(const KParams &p, RayRec *out, long long cap, int *count, cudaStream_t st)
+{
+    const long long blocks = std::max(1LL, std::min<long long>((cap + 255) / 256, 148LL * 4));
+    k_copy_rays<<<(unsigned)blocks, 256, 0, st>>>(p, out, cap, count);
 }
 
 }  // namespace isaac

@@ -87,7 +87,7 @@ int choose_lanes(long long rect_pixels, int hint)
     return hint ? hint : 4;
 }
 
-int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st)
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook)
 {
     const bool any = fn && p.rx1 > p.rx0 && p.ry1 > p.ry0;
     if (!any) {   // nothing to ray cast: the background covers every pixel
@@ -100,6 +100,10 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st)
     if (rc) return rc;
     launch_fill(p, st);
     launch_setup(p, st);
+    if (hook) {
+        rc = hook->fn(p, hook->arg, st);
+        if (rc) return rc;
+    }
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
     const long long want = (rect * rl + 127) / 128;
     const long long cap = (long long)sm_count() * 8;
@@ -109,7 +113,7 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st)
 
 // --------------------------------------------------------------- dispatch
 
-FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, int rl,
+FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, int mode, int rl,
                     int *rl_used)
 {
     const ZcEntry *best = nullptr;
@@ -118,7 +122,7 @@ FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, bool touch, i
         for (int i = 0; i < k_n_zc_entries; ++i) {
             const ZcEntry &e = k_zc_entries[i];
             if (e.nact != nact || e.sig != want || e.interp != interp || e.wide != wide ||
-                e.touch != touch)
+                e.mode != mode)
                 continue;
             if (!best || (e.rl == rl) || (best->rl != rl && std::abs(e.rl - rl) < std::abs(best->rl - rl)))
                 best = &e;
@@ -195,12 +199,85 @@ extern "C" int isaac_render(const isaac_source *sources, const isaac_chain *chai
     if (nact > 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
         const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray);
-        fn = find_zc(nact, sig, opts->interp, wide, p.touched != nullptr, want, &rl);
+        fn = find_zc(nact, sig, opts->interp, wide, p.touched ? MODE_TOUCH : MODE_PLAIN, want, &rl);
         if (!fn)
             return fail(ISAAC_ENOTSUP, "no kernel for %d sources (footprint with 64-bit offsets?)",
                         nact);
     }
-    return launch_frame_with(p, fn, rl, (cudaStream_t)stream);
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream, nullptr);
+}
+
+// The frame of isaac_render in one of the march modes, with an optional hook
+// between ray setup and march (the interval proposal).
+static int render_mode(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                       const float *luts, const float *weights, const isaac_camera *camera,
+                       const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
+                       const isaac_framebuffer *fb, cudaStream_t st, int mode,
+                       const FrameHook *hook, KParams &p)
+{
+    memset(&p, 0, sizeof p);
+    int rc = prepare_frame(camera, clip, n_clip, opts, p);
+    if (rc) return rc;
+    int nact = 0;
+    unsigned sig = 0;
+    bool wide = false;
+    rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, p, &nact, &sig, &wide);
+    if (rc) return rc;
+    rc = prepare_fb(fb, p);
+    if (rc) return rc;
+    if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered here");
+    FrameLaunch fn = nullptr;
+    int rl = 1;
+    if (nact > 0) {
+        const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+        fn = find_zc(nact, sig, opts->interp, wide, mode, choose_lanes(rect, opts->lanes_per_ray), &rl);
+        if (!fn) return fail(ISAAC_ENOTSUP, "no kernel for %d sources in this mode", nact);
+    }
+    return launch_frame_with(p, fn, rl, st, hook);
+}
+
+extern "C" int isaac_trace(const isaac_source *sources, const isaac_chain *chains,
+                           int32_t n_sources, const float *luts, const float *weights,
+                           const isaac_camera *camera, const isaac_plane *clip, int32_t n_clip,
+                           const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                           const isaac_proposal *proposal, isaac_ray *rays, int64_t capacity,
+                           int32_t *count, void *stream)
+{
+    clear_error();
+    if (!rays || capacity < 0 || !count) return fail(ISAAC_EINVAL, "rays, capacity and count are required");
+    if (((uintptr_t)rays) % 16 || ((uintptr_t)count) % 4)
+        return fail(ISAAC_EINVAL, "rays must be 16-byte aligned, count 4-byte aligned");
+    FrameHook hook;
+    int rc = proposal_hook(proposal, opts, &hook);
+    if (rc) return rc;
+    KParams p;
+    const cudaStream_t st = (cudaStream_t)stream;
+    rc = render_mode(sources, chains, n_sources, luts, weights, camera, clip, n_clip, opts, fb, st,
+                     MODE_LABEL, proposal ? &hook : nullptr, p);
+    if (rc) return rc;
+    if (!p.ctr) {   // nothing was cast: no rays
+        if (cudaMemsetAsync(count, 0, sizeof(int32_t), st) != cudaSuccess) return check_cuda("isaac_trace");
+        return ISAAC_OK;
+    }
+    launch_copy_rays(p, reinterpret_cast<RayRec *>(rays), capacity, count, st);
+    return check_cuda("isaac_trace copy");
+}
+
+extern "C" int isaac_render_learned(const isaac_source *sources, const isaac_chain *chains,
+                                    int32_t n_sources, const float *luts, const float *weights,
+                                    const isaac_camera *camera, const isaac_plane *clip,
+                                    int32_t n_clip, const isaac_render_opts *opts,
+                                    const isaac_framebuffer *fb, const isaac_proposal *proposal,
+                                    void *stream)
+{
+    clear_error();
+    if (!proposal) return fail(ISAAC_EINVAL, "proposal is required");
+    FrameHook hook;
+    int rc = proposal_hook(proposal, opts, &hook);
+    if (rc) return rc;
+    KParams p;
+    return render_mode(sources, chains, n_sources, luts, weights, camera, clip, n_clip, opts, fb,
+                       (cudaStream_t)stream, MODE_PLAIN, &hook, p);
 }
 
 extern "C" int isaac_release_workspaces(void)

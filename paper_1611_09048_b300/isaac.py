@@ -27,7 +27,9 @@ OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 # every C symbol declared in include/isaac_b300.h
 EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_layout",
            "isaac_pack", "isaac_render_packed", "isaac_release_workspaces",
-           "isaac_opacity_grid", "isaac_render_noalloc")
+           "isaac_opacity_grid", "isaac_render_noalloc", "isaac_trace", "isaac_render_learned",
+           "isaac_render_packed_learned", "isaac_mlp_sync", "isaac_mlp_features",
+           "isaac_mlp_forward", "isaac_mlp_train_step")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -75,6 +77,37 @@ class Packed(C.Structure):
 
 DTYPES = {"f32": F32, "bf16": BF16, "f16": F16, "e4m3": E4M3}
 
+MLP_PARAMS, MLP_HALF, MLP_INPUTS = 22915, 32256, 224
+# public parameter layout: name, shape (input-major weights)
+MLP_LAYOUT = [("W1", (224, 64)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+              ("W3", (64, 64)), ("b3", (64,)), ("W4", (64, 3)), ("b4", (3,))]
+RAY_INTS = 12   # isaac_ray = 48 bytes
+
+
+class Mlp(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("grads", C.c_void_p), ("adam_m", C.c_void_p),
+                ("adam_v", C.c_void_p), ("half_w", C.c_void_p), ("step", C.c_int32)]
+
+
+class Proposal(C.Structure):
+    _fields_ = [("model", C.POINTER(Mlp)), ("grid", C.c_void_p), ("cell", C.c_int32),
+                ("threshold", C.c_float), ("margin", C.c_int32), ("stats", C.c_void_p)]
+
+
+def pack_mlp_params(named) -> np.ndarray:
+    """Named arrays -> the flat float32 layout of the C ABI."""
+    return np.concatenate([np.asarray(named[k], np.float32).reshape(-1) for k, _ in MLP_LAYOUT])
+
+
+def unpack_mlp_params(flat) -> dict:
+    flat = np.asarray(flat)
+    out, o = {}, 0
+    for k, shape in MLP_LAYOUT:
+        size = int(np.prod(shape))
+        out[k] = flat[o:o + size].reshape(shape)
+        o += size
+    return out
+
 
 class IsaacError(RuntimeError):
     def __init__(self, code: int, msg: str):
@@ -118,6 +151,26 @@ def load(path: Optional[str] = None):
         lib.isaac_release_workspaces.restype = C.c_int
         lib.isaac_render_noalloc.restype = C.c_int
         lib.isaac_render_noalloc.argtypes = lib.isaac_render.argtypes
+        render_args = list(lib.isaac_render.argtypes[:-1])
+        lib.isaac_trace.restype = C.c_int
+        lib.isaac_trace.argtypes = render_args + [C.POINTER(Proposal), C.c_void_p, C.c_int64,
+                                                  C.c_void_p, C.c_void_p]
+        lib.isaac_render_learned.restype = C.c_int
+        lib.isaac_render_learned.argtypes = render_args + [C.POINTER(Proposal), C.c_void_p]
+        lib.isaac_render_packed_learned.restype = C.c_int
+        lib.isaac_render_packed_learned.argtypes = list(lib.isaac_render_packed.argtypes[:-1]) + \
+            [C.POINTER(Proposal), C.c_void_p]
+        lib.isaac_mlp_sync.restype = C.c_int
+        lib.isaac_mlp_sync.argtypes = [C.POINTER(Mlp), C.c_void_p]
+        lib.isaac_mlp_features.restype = C.c_int
+        lib.isaac_mlp_features.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_float, C.c_void_p,
+                                           C.c_int32, C.c_void_p, C.c_void_p]
+        lib.isaac_mlp_forward.restype = C.c_int
+        lib.isaac_mlp_forward.argtypes = [C.POINTER(Mlp), C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_void_p]
+        lib.isaac_mlp_train_step.restype = C.c_int
+        lib.isaac_mlp_train_step.argtypes = [C.POINTER(Mlp), C.c_void_p, C.c_void_p, C.c_int64,
+                                             C.c_float, C.c_int32, C.c_void_p, C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
         lib.isaac_abi_version.restype = C.c_int
         _lib = lib
@@ -283,6 +336,40 @@ class DeviceScene:
                                         _stream_handle(stream)))
         return out
 
+    def trace(self, mv=None, proj=None, out=None, proposal=None, capacity=None, stream=None,
+              lanes=None, want_f32=False, want_nsamp=False):
+        """Render and return the frame's ray list: (rays (cap, 12) int32
+        records, count (1,) int32 on the device, rgba8, rgba32, nsamples)."""
+        import torch
+        W, H = self.scene.width, self.scene.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=self.device) if want_nsamp else None
+        rays, count, _ = _trace(self, mv, proj, out, proposal, capacity, stream, lanes, f32, ns)
+        return rays, count, out, f32, ns
+
+    def prepare_learned(self, proposal, mv=None, proj=None, out=None, rgba32=None, nsamples=None,
+                        lanes=None):
+        args, keep = self.prepare(mv, proj, out, rgba32, nsamples, lanes=lanes)
+        return args + (C.byref(proposal),), keep + (proposal,)
+
+    @staticmethod
+    def launch_learned(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render_learned(*args, _stream_handle(stream)))
+
+    def render_learned(self, proposal, mv=None, proj=None, out=None, stream=None, lanes=None,
+                       want_f32=False, want_nsamp=False):
+        import torch
+        W, H = self.scene.width, self.scene.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=self.device) if want_nsamp else None
+        self.launch_learned(self.prepare_learned(proposal, mv, proj, out, f32, ns, lanes), stream)
+        return out, f32, ns
+
     # ----------------------------------------------------- packed copies
 
     def pack(self, dtype="bf16", mask=None, stream=None):
@@ -339,6 +426,28 @@ class PackedVolume:
         args, _keep = prepared
         check(load().isaac_render_packed(*args, _stream_handle(stream)))
 
+    def prepare_learned(self, proposal, mv=None, proj=None, out=None, rgba32=None, nsamples=None,
+                        mask=None, lanes=None):
+        args, keep = self.prepare(mv, proj, out, rgba32, nsamples, mask, lanes)
+        return args + (C.byref(proposal),), keep + (proposal,)
+
+    @staticmethod
+    def launch_learned(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render_packed_learned(*args, _stream_handle(stream)))
+
+    def render_learned(self, proposal, mv=None, proj=None, out=None, stream=None, want_f32=False,
+                       want_nsamp=False, lanes=None):
+        import torch
+        W, H = self.ds.scene.width, self.ds.scene.height
+        dev = self.ds.device
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
+        self.launch_learned(self.prepare_learned(proposal, mv, proj, out, f32, ns, None, lanes), stream)
+        return out, f32, ns
+
     def render(self, mv=None, proj=None, out=None, stream=None, mask=None, want_f32=False,
                want_nsamp=False, lanes=None):
         import torch
@@ -350,6 +459,76 @@ class PackedVolume:
         ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
         self.launch(self.prepare(mv, proj, out, f32, ns, mask, lanes), stream)
         return out, f32, ns
+
+
+# ------------------------------------------------------- learned proposal
+
+class MLPModel:
+    """Device buffers of the interval-proposal MLP (float32 master weights,
+    gradients, Adam moments, FP16 kernel copy)."""
+
+    def __init__(self, params_flat, device="cuda", train=True):
+        import torch
+        self.device = torch.device(device)
+        flat = np.asarray(params_flat, np.float32).reshape(-1)
+        assert flat.size == MLP_PARAMS
+        self.params = torch.from_numpy(flat.copy()).to(self.device)
+        z = lambda: torch.zeros(MLP_PARAMS, dtype=torch.float32, device=self.device)  # noqa: E731
+        self.grads, self.m, self.v = (z(), z(), z()) if train else (None, None, None)
+        self.half = torch.empty(MLP_HALF, dtype=torch.float16, device=self.device)
+        self.desc = Mlp(self.params.data_ptr(), self.grads.data_ptr() if train else None,
+                        self.m.data_ptr() if train else None, self.v.data_ptr() if train else None,
+                        self.half.data_ptr(), 0)
+        check(load().isaac_mlp_sync(C.byref(self.desc), None))
+
+    @property
+    def step(self):
+        return self.desc.step
+
+    def named(self):
+        return unpack_mlp_params(self.params.cpu().numpy())
+
+    def forward(self, X, stream=None):
+        import torch
+        U = torch.empty((X.shape[0], 3), dtype=torch.float32, device=self.device)
+        check(load().isaac_mlp_forward(C.byref(self.desc), X.data_ptr(), X.shape[0], U.data_ptr(),
+                                       _stream_handle(stream)))
+        return U
+
+    def train_step(self, X, rays, lr=1e-3, margin=2, loss_sum=None, stream=None):
+        check(load().isaac_mlp_train_step(C.byref(self.desc), X.data_ptr(), rays.data_ptr(),
+                                          X.shape[0], float(lr), int(margin),
+                                          loss_sum.data_ptr() if loss_sum is not None else None,
+                                          _stream_handle(stream)))
+
+    def proposal(self, grid, cell, threshold=0.9, margin=2, stats=None):
+        p = Proposal(C.pointer(self.desc), grid.data_ptr(), int(cell), float(threshold), int(margin),
+                     stats.data_ptr() if stats is not None else None)
+        p._keep = (grid, stats)
+        return p
+
+
+def mlp_features(rays, n_rays, vol_n, step, grid, cell, stream=None):
+    """Inputs (n_rays, 224) FP16 of ray records (tensor (N, 12) int32)."""
+    import torch
+    X = torch.empty((max(1, n_rays), MLP_INPUTS), dtype=torch.float16, device=rays.device)
+    nn_ = (C.c_int64 * 3)(*[int(v) for v in vol_n])
+    check(load().isaac_mlp_features(rays.data_ptr(), int(n_rays), C.cast(nn_, C.c_void_p), float(step),
+                                    grid.data_ptr(), int(cell), X.data_ptr(), _stream_handle(stream)))
+    return X[:n_rays]
+
+
+def _trace(ds, mv, proj, out, proposal, capacity, stream, lanes, rgba32=None, nsamples=None):
+    import torch
+    sc = ds.scene
+    if capacity is None:
+        capacity = sc.width * sc.height
+    rays = torch.zeros((max(1, capacity), RAY_INTS), dtype=torch.int32, device=ds.device)
+    count = torch.zeros(1, dtype=torch.int32, device=ds.device)
+    args, keep = ds.prepare(mv, proj, out, rgba32, nsamples, lanes=lanes)
+    check(load().isaac_trace(*args, C.byref(proposal) if proposal is not None else None,
+                             rays.data_ptr(), capacity, count.data_ptr(), _stream_handle(stream)))
+    return rays, count, keep
 
 
 def render(scene, **kw):

@@ -357,6 +357,40 @@ def scene_bubble(n: int = 512, frame: int = 0, seed: int = 0, width: int = 1920,
                  height=height)
 
 
+def mlp_params(seed: int = 0, bias_scale: float = 0.0) -> dict:
+    """Seeded initial weights of the 224-64-64-64-3 proposal MLP: He-uniform
+    weights (input-major), biases U(-bias_scale, bias_scale)."""
+    rng = np.random.default_rng(seed)
+    shapes = [("W1", (224, 64)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+              ("W3", (64, 64)), ("b3", (64,)), ("W4", (64, 3)), ("b4", (3,))]
+    out = {}
+    for name, shape in shapes:
+        if name.startswith("W"):
+            lim = math.sqrt(6.0 / shape[0])
+            out[name] = rng.uniform(-lim, lim, shape).astype(np.float32)
+        else:
+            out[name] = rng.uniform(-bias_scale, bias_scale, shape).astype(np.float32)
+    return out
+
+
+def random_rays(n_rays: int, n, seed: int = 0, ns_range=(20, 400)):
+    """Seeded synthetic ray records: first sample inside the box, unit
+    direction, sample count, and a visible span [jf, jl] (-1 for ~20% empty
+    rays).  Returns a dict of arrays."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(0.0, 1.0, (n_rays, 3)) * np.asarray(n, np.float64)
+    d = rng.standard_normal((n_rays, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    ns = rng.integers(ns_range[0], ns_range[1], n_rays)
+    jf = rng.integers(0, ns // 2 + 1)
+    jl = np.minimum(ns - 1, jf + rng.integers(0, ns // 2 + 1))
+    empty = rng.uniform(size=n_rays) < 0.2
+    jf = np.where(empty, -1, jf)
+    jl = np.where(empty, -1, jl)
+    return {"e": e.astype(np.float32), "d": d.astype(np.float32), "nsteps": ns.astype(np.int32),
+            "jf": jf.astype(np.int32), "jl": jl.astype(np.int32)}
+
+
 # --------------------------------------------------------------------------
 # whole scenes
 # --------------------------------------------------------------------------

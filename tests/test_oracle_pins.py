@@ -119,6 +119,25 @@ def test_clip_plane_raises_entry_on_global_grid(step, top):
     np.testing.assert_allclose(r["rgba"][..., 3], 1 - (1 - a) ** (ke - kf), rtol=0, atol=1e-13)
 
 
+def test_visible_span_closed_form():
+    """A slab of opacity a between z = 2 and z = 5 inside an empty volume:
+    rays along -z enter at z = 8, so with step 0.5 and nearest-cell sampling
+    the first sample with opacity is the one at z = 4.5 (index 7) and the last
+    the one at z = 2.0 (index 12)."""
+    n = (8, 8, 8)
+    field = np.zeros(n[::-1], np.float32)
+    field[2:5] = 1.0
+    lut = np.zeros((256, 4), np.float32)
+    lut[128:, :] = (1.0, 1.0, 1.0, 0.1)
+    sc = make_scene([field], [[]], [lut], [1.0], n, ortho_down_z(n, 8, 8), 8, 8, interp=0,
+                    step=0.5, term=2.0)
+    r = oracle.render(sc)
+    # samples at z = 8 - 0.5k; cells 2..4 hold the slab: 4.5 (k=7) ... 2.0 (k=12)
+    assert np.all(r["jspan"][..., 0] == 7) and np.all(r["jspan"][..., 1] == 12)
+    sc.luts = np.zeros_like(sc.luts)
+    assert np.all(oracle.render(sc)["jspan"] == -1)
+
+
 def test_empty_transfer_function_gives_background():
     sc = small_pic_scene()
     sc.luts = sc.luts.copy()
