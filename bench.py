@@ -176,6 +176,12 @@ def run_ours(args, rank, world, local_rank):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    # events the library records around the march kernel of each timed frame
+    mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for a, b in mev:
+        a.record(stream)
+        b.record(stream)
     # The clock sampler (200 ms period) runs over a window that starts with
     # >= 1 s of further untimed frames (GPU under the same load) and ends
     # after the timed steps, so short timed regions still get clock samples.
@@ -196,15 +202,18 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.zero_()                      # evict L2 between timed frames
+                isaac.time_march(*mev[i])
                 ev[i][0].record(stream)
                 frame(args.warmup + i)
                 ev[i][1].record(stream)
         torch.cuda.synchronize()
+        isaac.time_march()
         torch.cuda.nvtx.range_pop()
         t_wall = time.perf_counter() - t_wall0
         if world > 1:
             torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    march_ms = [a.elapsed_time(b) for a, b in mev]
     dev_ms = sum(step_ms)
     timed_idx = [(args.warmup + i) % len(cams) for i in range(args.steps)]
     n_samp = sum(samples[j] for j in timed_idx)
@@ -227,6 +236,8 @@ def run_ours(args, rank, world, local_rank):
 
     variants = {} if args.no_variants else \
         run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
+    learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
+    serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
     # max over ranks
     vals = torch.tensor([dev_ms, e2e_ms, t_wall], dtype=torch.float64, device=dev)
@@ -242,9 +253,12 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak, peak_kind = _peaks()
     bpc = bytes_per_cell(sc)
     alg_bytes = [c * bpc + W * H * 4 for c in cells]
-    mean_launch_ms = dev_ms / args.steps
+    mean_launch_ms = statistics.mean(march_ms)
     achieved = (sum(alg_bytes) / args.steps) / (mean_launch_ms * 1e-3) / 1e9
-    traffic = _ncu_traffic(cfg["workload"])
+    prof = _ncu_traffic(cfg["workload"]) or {}
+    traffic = prof.get("dram_bytes_per_launch")
+    l2_peak = _l2_peak(dev)
+    lts = prof.get("lts_bytes_per_launch")
     res = {
         "metric": METRIC,
         "value": all_samp / (dev_ms * 1e-3),
@@ -266,17 +280,28 @@ def run_ours(args, rank, world, local_rank):
                        samples_per_ray_max=max(ray_stats[j][1] for j in timed_idx),
                        cells_read_per_frame_mean=sum(cells) / len(cells)),
         "wall_s_timed_region": t_wall,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": traffic,
-                     "kernel": "k_raycast (+ k_fill_background, same render call)",
-                     "algorithmic_bytes": "distinct cells read x 28 B (E,B,rho) + W*H*4 B image"},
+                     "kernel": "k_raycast (march), CUDA events recorded by the library around "
+                               "its launch on the render stream",
+                     "launch_ms_mean": mean_launch_ms,
+                     "frame_share": sum(march_ms) / dev_ms,
+                     "algorithmic_bytes": "distinct cells read x 28 B (E,B,rho) + W*H*4 B image",
+                     "binding_unit": prof.get("binding_unit")},
+        "roofline_l2": {"achieved": (lts / (mean_launch_ms * 1e-3) / 1e9) if lts else None,
+                        "peak": l2_peak, "unit": "GB/s",
+                        "frac": (lts / (mean_launch_ms * 1e-3) / 1e9 / l2_peak) if lts else None,
+                        "bytes": "ncu lts__t_bytes per k_raycast launch (profiles/traffic.json)",
+                        "peak_kind": "measured here: copy within half the L2 (read + write bytes), best of 10"},
         "e2e": {"value": all_samp / (e2e_ms * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(luts_host.numel() * 4),
                 "d2h_bytes_per_step": int(W * H * 4)},
         "clocks": clocks.summary(),
         "variants": variants,
+        "learned": learned,
+        "serving": serving,
     }
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(sc, cams, args.cpu_seconds)
@@ -344,8 +369,275 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
     return out
 
 
+def run_learned(args, dev, stream, flush):
+    """Bubble workload (512^3 scalar: an ellipsoidal shell moving through
+    mostly empty space, 1920x1080): train the interval proposal on traced
+    frames (random cameras and transfer functions), then time plain and
+    learned marching in float32 zero-copy and BF16 packed form on unseen
+    frames; the learned forms include the per-frame max-opacity grid."""
+    import torch
+    from paper_1611_09048_b300 import isaac, synth
+    n, W, H, cell = args.learned_n, 1920, 1080, 16
+    t_begin = time.perf_counter()
+    noise = synth.value_noise(n, 77, device=dev)
+    Xs, Rs = [], []
+    for fi, f in enumerate(range(0, 100, 10)):
+        field = synth.bubble_field(n, f, 0, noise=noise, device=dev)
+        for c in range(args.learned_views):
+            sc = synth.scene_bubble(n, frame=f, seed=1000 * fi + c, width=480, height=270,
+                                    field=field, lut_seed=500 + (7 * fi + c) % 16)
+            ds = isaac.DeviceScene(sc, device=dev)
+            rays, count, *_ = ds.trace()
+            k = int(count.item())
+            if k == 0:
+                continue
+            grid = ds.opacity_grid(cell)
+            Xs.append(isaac.mlp_features(rays[:k], k, sc.n, sc.step, grid, cell))
+            Rs.append(rays[:k].clone())
+    X, R = torch.cat(Xs), torch.cat(Rs)
+    t_data = time.perf_counter() - t_begin
+    model = isaac.MLPModel(isaac.pack_mlp_params(synth.mlp_params(3)), device=dev)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    t1 = time.perf_counter()
+    for it in range(args.learned_steps):
+        idx = torch.randint(0, X.shape[0], (8192,), generator=gen).to(dev)
+        if it == args.learned_steps - 1:
+            loss.zero_()
+        model.train_step(X[idx].contiguous(), R[idx].contiguous(), lr=1e-3, margin=2,
+                         loss_sum=loss if it == args.learned_steps - 1 else None)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+
+    kinds = ("plain_f32", "learned_f32", "plain_bf16", "learned_bf16")
+    acc = {k: {"ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0} for k in kinds}
+    stats = torch.zeros(2, dtype=torch.int32, device=dev)
+    for f in (5, 35, 65, 95):
+        field = synth.bubble_field(n, f, 0, noise=noise, device=dev)
+        for c in range(args.learned_test_views):
+            sc = synth.scene_bubble(n, frame=f, seed=77000 + 100 * f + c, width=W, height=H,
+                                    field=field, lut_seed=500 + (3 * f + c) % 16)
+            ds = isaac.DeviceScene(sc, device=dev)
+            pv = ds.pack("bf16")
+            grid = torch.empty(tuple((k + cell - 1) // cell for k in sc.n[::-1]),
+                               dtype=torch.float32, device=dev)
+            prop = model.proposal(grid, cell, threshold=args.learned_threshold,
+                                  margin=args.learned_margin, stats=stats)
+            outs = {k: torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for k in kinds}
+            nss = {k: torch.empty((H, W), dtype=torch.int32, device=dev) for k in kinds}
+
+            def run(kind, count=None):
+                if kind.startswith("learned"):
+                    ds.opacity_grid(cell, out=grid, stream=stream)
+                tgt = ds if kind.endswith("f32") else pv
+                kw = dict(out=outs[kind], stream=stream)
+                if kind.startswith("learned"):
+                    tgt.render_learned(prop, want_nsamp=count is not None, **kw)
+                else:
+                    tgt.render(want_nsamp=count is not None, **kw)
+
+            with torch.cuda.stream(stream):
+                for kind in kinds:           # counting pass (untimed)
+                    if kind.startswith("learned"):
+                        ds.opacity_grid(cell, out=grid, stream=stream)
+                    tgt = ds if kind.endswith("f32") else pv
+                    if kind.startswith("learned"):
+                        o = tgt.render_learned(prop, out=outs[kind], stream=stream, want_nsamp=True)
+                    else:
+                        o = tgt.render(out=outs[kind], stream=stream, want_nsamp=True)
+                    nss[kind] = o[2]
+            torch.cuda.synchronize()
+            ref = outs["plain_f32"]
+            hit = ref[..., 3] > 0
+            for kind in kinds:
+                d = (outs[kind].to(torch.int16) - ref.to(torch.int16)).abs()
+                acc[kind]["lsb_sum"] += float(d.float().sum().item())
+                acc[kind]["px"] += d.numel()
+                acc[kind]["lsb_max"] = max(acc[kind]["lsb_max"], int(d.max().item()))
+                acc[kind]["samples"] += int(nss[kind].sum(dtype=torch.int64).item())
+            for kind in kinds:
+                with torch.cuda.stream(stream):
+                    for _ in range(2):
+                        run(kind)
+                    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                          for _ in range(3)]
+                    torch.cuda.nvtx.range_push(f"timed_{kind}")
+                    for a, b in ev:
+                        flush.zero_()
+                        a.record(stream)
+                        run(kind)
+                        b.record(stream)
+                    torch.cuda.nvtx.range_pop()
+                torch.cuda.synchronize()
+                acc[kind]["ms"] += [a.elapsed_time(b) for a, b in ev]
+            del ds, pv
+    frames = len(acc["plain_f32"]["ms"]) // 3
+    seen, restricted = stats.tolist()
+    res = {"workload": f"bubble{n}_{W}x{H}", "train_rays": int(X.shape[0]),
+           "train_steps": args.learned_steps, "train_s": t_train, "data_s": t_data,
+           "final_loss": float(loss.item()), "threshold": args.learned_threshold,
+           "margin": args.learned_margin, "restricted_frac": restricted / max(1, seen),
+           "test_frames": frames}
+    for kind in kinds:
+        a = acc[kind]
+        ms = statistics.mean(a["ms"])
+        res[kind] = {"ms_per_frame": ms, "fps": 1e3 / ms,
+                     "samples_per_frame": a["samples"] / frames,
+                     "lsb_vs_plain_f32_mean": a["lsb_sum"] / max(1, a["px"]),
+                     "lsb_vs_plain_f32_max": a["lsb_max"]}
+    res["speedup_learned_bf16_vs_plain_f32"] = res["plain_f32"]["ms_per_frame"] / \
+        res["learned_bf16"]["ms_per_frame"]
+    return res
+
+
+def run_serving(args, ds, dev):
+    """Serving loop over the resident 512^3 E/B/rho volume in BF16: clients
+    with Poisson arrivals (open loop), image sizes drawn from {256^2, 512^2,
+    1280x720, 1920x1080}, cameras on seeded random walks, a share of requests
+    steering (new LUTs or functor parameters that the client then keeps).
+    Reports latency percentiles (submit -> image in pinned host memory),
+    frames/s and the batch sizes the server formed; then a closed-loop burst
+    for the saturated throughput."""
+    import torch
+    from paper_1611_09048_b300 import isaac, synth
+    sc = ds.scene
+    pv = ds.pack("bf16")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(2024)
+    sizes = [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
+    n_cl, rate, dur = args.serve_clients, args.serve_rate, args.serve_seconds
+    n_req = int(rate * dur)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    t_arr = np.cumsum(gaps)
+    who = rng.integers(0, n_cl, n_req)
+    size_of = rng.integers(0, len(sizes), n_req)
+    steer = rng.uniform(0, 1, n_req) < args.serve_steer
+    state = [{"theta": rng.uniform(0, 2 * math.pi), "phi": rng.uniform(-0.5, 0.5),
+              "luts": None, "chains": None} for _ in range(n_cl)]
+    base_chains = [list(c) for c in sc.chains]
+    # pinned output buffers, recycled (a request holds one until its result)
+    n_buf = args.serve_buffers
+    bufs = [torch.empty(1920 * 1080 * 4, dtype=torch.uint8).pin_memory() for _ in range(n_buf)]
+    free = list(range(n_buf))
+
+    def make(i):
+        c = state[who[i]]
+        c["theta"] += math.radians(rng.normal(0, 2.0))
+        c["phi"] = float(np.clip(c["phi"] + math.radians(rng.normal(0, 2.0)), -1.2, 1.2))
+        if steer[i]:
+            if rng.uniform() < 0.5:
+                c["luts"] = np.stack([synth.lut_from_points(int(rng.integers(1 << 30)))
+                                      for _ in range(pv.luts.shape[0])])
+            else:
+                ch = [list(x) for x in base_chains]
+                f = float(rng.uniform(0.7, 1.3))
+                ch[0] = [(op[0], tuple(a * f for a in op[1])) if op[0] == "mul" else op
+                         for op in ch[0]]
+                c["chains"] = ch
+        W, H = sizes[size_of[i]]
+        mv, proj = synth.orbit_camera(sc.n, W, H, c["theta"], c["phi"], dist_factor=2.0)
+        return mv, proj, W, H, c["luts"], c["chains"]
+
+    def run_open(srv):
+        res, stalls, t0 = [], 0, time.perf_counter()
+        held = {}
+        i = 0
+        while i < n_req or held:
+            now = time.perf_counter() - t0
+            if i < n_req and now >= t_arr[i]:
+                if not free:
+                    stalls += 1
+                    for r in srv.poll(wait=0.001):
+                        free.append(held.pop(r["tag"]))
+                        res.append(r)
+                    continue
+                mv, proj, W, H, luts, chains = make(i)
+                b = free.pop()
+                out = bufs[b][: W * H * 4]
+                held[srv.submit(mv, proj, W, H, out, luts=luts, chains=chains)] = b
+                i += 1
+                continue
+            wait = max(0.0, (t_arr[i] - now) if i < n_req else 0.002)
+            for r in srv.poll(wait=min(wait, 0.002)):
+                free.append(held.pop(r["tag"]))
+                res.append(r)
+        return res, stalls
+
+    with isaac.Server(pv, budget=args.serve_budget << 20, n_streams=args.serve_streams,
+                      max_batch=args.serve_max_batch) as srv:
+        # warm-up: a few requests of every size
+        for k in range(8):
+            mv, proj = synth.orbit_camera(sc.n, *sizes[k % 4], 0.1 * k, 0.1)
+            srv.submit(mv, proj, *sizes[k % 4], bufs[k][: sizes[k % 4][0] * sizes[k % 4][1] * 4])
+        srv.drain()
+        res, stalls = run_open(srv)
+        # closed loop: keep every buffer in flight, 1080p only
+        burst = []
+        held = {}
+        t0 = time.perf_counter()
+        n_burst = args.serve_burst
+        sent = 0
+        while sent < n_burst or held:
+            while free and sent < n_burst:
+                mv, proj = synth.orbit_camera(sc.n, 1920, 1080, 0.37 * sent, 0.2 * math.sin(sent))
+                b = free.pop()
+                held[srv.submit(mv, proj, 1920, 1080, bufs[b])] = b
+                sent += 1
+            for r in srv.poll(wait=0.01):
+                free.append(held.pop(r["tag"]))
+                burst.append(r)
+        t_burst = time.perf_counter() - t0
+    assert all(r["status"] == 0 for r in res + burst)
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+    qwait = np.array([r["t_launch"] - r["t_submit"] for r in res]) * 1e3
+    t_first = min(r["t_submit"] for r in res)
+    t_last = max(r["t_done"] for r in res)
+    px = sum(sizes[size_of[i]][0] * sizes[size_of[i]][1] for i in range(n_req))
+    bs = np.array([r["batch_size"] for r in res])
+    return {
+        "workload": "serve_pic512_bf16",
+        "clients": n_cl, "offered_rate_per_s": rate, "requests": n_req,
+        "sizes": [f"{w}x{h}" for w, h in sizes], "steering_share": args.serve_steer,
+        "budget_mib": args.serve_budget, "streams": args.serve_streams,
+        "max_batch": args.serve_max_batch,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                       "mean": float(lat.mean())},
+        "queue_ms": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
+        "fps": n_req / (t_last - t_first),
+        "mpix_per_s": px / (t_last - t_first) / 1e6,
+        "batch_size": {"mean": float(bs.mean()), "max": int(bs.max())},
+        "generator_stalls": stalls,
+        "saturated_1080p_fps": len(burst) / t_burst,
+        "latency_note": "submit -> RGBA8 image in pinned host memory, measured by the server's own "
+                        "clock; includes queueing, the batch's kernels and its device-to-host copy",
+    }
+
+
+def _l2_peak(dev):
+    """L2 bandwidth probe: copies between two buffers that together fill half
+    the L2 (resident after the first pass), read + write bytes, best of 10
+    runs of 20 copies, CUDA events."""
+    import torch
+    n = torch.cuda.get_device_properties(dev).L2_cache_size // 4 // 4
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(3):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 20)
+    return 2 * n * 4 / (best * 1e-3) / 1e9
+
+
 def _ncu_traffic(workload):
-    """DRAM bytes per k_raycast launch from the committed ncu summary, if any."""
+    """Per-launch ncu counters of the march kernel from the committed summary, if any."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -422,6 +714,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the packed-copy variants (FP32/BF16/FP16/E4M3)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-proposal comparison on the bubble workload")
+    ap.add_argument("--learned-n", type=int, default=512)
+    ap.add_argument("--learned-views", type=int, default=10)
+    ap.add_argument("--learned-test-views", type=int, default=2)
+    ap.add_argument("--learned-steps", type=int, default=1500)
+    ap.add_argument("--learned-threshold", type=float, default=0.9)
+    ap.add_argument("--learned-margin", type=int, default=4)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop measurement")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=600.0)
+    ap.add_argument("--serve-clients", type=int, default=48)
+    ap.add_argument("--serve-steer", type=float, default=0.1)
+    ap.add_argument("--serve-budget", type=int, default=256, help="MiB")
+    ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-max-batch", type=int, default=16)
+    ap.add_argument("--serve-buffers", type=int, default=64)
+    ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--preroll", type=float, default=1.0,
                     help="seconds of untimed frames inside the clock-sampling window")
     args = ap.parse_args()

@@ -116,7 +116,7 @@ typedef struct {
     float term_alpha;        /* a ray stops once its opacity A >= term_alpha; > 1 disables */
     float bg[4];             /* background RGBA (premultiplied) blended behind the volume */
     uint32_t active_mask;    /* bit s set: source s is rendered (Sec. 3.2) */
-    int32_t lanes_per_ray;   /* 0 = automatic, else 1, 2 or 4 threads cooperating on one
+    int32_t lanes_per_ray;   /* 0 = automatic, else 1, 2, 4, 8 or 16 threads cooperating on one
                                 ray; a hint (the nearest compiled variant is used) that
                                 never changes the image, only the speed */
 } isaac_render_opts;
@@ -229,7 +229,8 @@ int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains, cons
  * samples inside it read); its value is the largest blended opacity
  * clamp(sum_s weights[s] * LUT_s(chain_s(v_s)).alpha, 0, 1) over those cells,
  * each active source read at the cell itself (clamped without guards).
- * grid: device, ceil(n/cell) values per axis, x fastest; grid_len its length.
+ * cell: 2..1024.  grid: device, ceil(n/cell) values per axis, x fastest;
+ * grid_len its length (the first ceil(n/cell)^3 values are overwritten).
  * Sources, chains, luts, weights and opts (n, active_mask) as in
  * isaac_render.
  */
@@ -379,6 +380,101 @@ int isaac_render_packed_learned(const isaac_packed *vol, const isaac_chain *chai
                                 int32_t n_clip, const isaac_render_opts *opts,
                                 const isaac_framebuffer *fb, const isaac_proposal *proposal,
                                 void *stream);
+
+/*
+ * Serving loop.  The paper has no counterpart kernel: its central server
+ * (Sec. 3.5 "Steering arbitrary HPC applications using open standards")
+ * forwards one application's frames to many clients, each of which may steer
+ * the camera, transfer functions and functor chains.  Here one process renders
+ * many such viewers' requests against one device-resident volume with
+ * continuous batching:
+ *
+ *   isaac_server_submit queues a request (its camera and image size, and
+ *   optionally its own transfer functions and functor chains).  A worker
+ *   thread admits queued requests in arrival order while the device memory
+ *   they need (RGBA8 image, ray list, table entry, LUT copy) fits the
+ *   server's budget, at most max_batch per batch, and launches each batch as
+ *   one frame: one background, one ray-setup and one march launch over all
+ *   its requests, each ray carrying its request's constants.  Up to
+ *   n_streams batches are in flight on their own streams, so requests that
+ *   arrive while others render start as soon as memory and a stream free up.
+ *   The image reaches request->out when the request's result is returned by
+ *   isaac_server_poll.  A request's image does not depend on which other
+ *   requests share its batch: it equals the same request rendered alone.
+ *
+ * The server never allocates during serving: the budget is one device
+ * allocation made by isaac_server_create (ISAAC_ENOMEM if it fails).
+ */
+#define ISAAC_SERVER_MAX_BATCH 64
+
+typedef struct isaac_server isaac_server;
+
+typedef struct {
+    int64_t budget_bytes;   /* device memory for requests in flight, >= 1 MiB */
+    int32_t n_streams;      /* batches in flight at once, 1..8 */
+    int32_t max_batch;      /* requests per batch, 1..ISAAC_SERVER_MAX_BATCH */
+} isaac_server_config;
+
+typedef struct {
+    isaac_camera camera;        /* view and image size of this request */
+    const float *luts;          /* host, n_sources * 256 RGBA floats (layout of isaac_render's
+                                   luts), or NULL for the server's; copied at submit */
+    const isaac_chain *chains;  /* host, n_sources chains, or NULL for the server's; compiled
+                                   at submit */
+    void *out;                  /* RGBA8 image, width * height * 4 bytes, row 0 at the top:
+                                   pinned host memory (cudaHostAlloc / registered) or device
+                                   memory; written when the result is reported */
+    int64_t tag;                /* returned with the result */
+} isaac_request;
+
+typedef struct {
+    int64_t tag;
+    int32_t status;             /* ISAAC_OK, or the error that failed the request's batch */
+    int32_t batch_size;         /* requests in the batch that rendered it */
+    double t_submit;            /* seconds since isaac_server_create: queued, */
+    double t_launch;            /* its batch enqueued on the GPU, */
+    double t_done;              /* its image in `out` (completion seen by the worker) */
+} isaac_result;
+
+/*
+ * Create a server for one volume: either zero-copy sources (vol == NULL;
+ * sources, chains, n_sources, luts, weights as for isaac_render; at most 4
+ * active; 32-bit element offsets) or a BF16 packed copy (vol != NULL; sources
+ * ignored; all packed sources active; component sets {1} or {3,3,1}).  luts
+ * is a device array that must stay valid for the server's lifetime, as must
+ * the source data or the packed copy; opts and clip are copied.  The server
+ * renders on the current device.  ISAAC_ENOTSUP for source sets without a
+ * batched kernel.
+ */
+int isaac_server_create(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                        const float *luts, const float *weights, const isaac_packed *vol,
+                        const isaac_render_opts *opts, const isaac_plane *clip, int32_t n_clip,
+                        const isaac_server_config *cfg, isaac_server **out);
+
+/* Queue a request (thread-safe).  Rejected on the host (nothing queued) for a
+ * malformed camera, a non-finite LUT entry, an invalid chain, an `out` that is
+ * neither pinned host nor device memory, or a request larger than the budget
+ * (ISAAC_ENOMEM). */
+int isaac_server_submit(isaac_server *server, const isaac_request *request);
+
+/* Move up to `max` finished requests' results into `out`, waiting up to
+ * wait_s seconds for the first one.  Returns how many (>= 0) or an error. */
+int isaac_server_poll(isaac_server *server, isaac_result *out, int32_t max, double wait_s);
+
+/* Requests queued or in flight whose results are not yet available. */
+int isaac_server_outstanding(isaac_server *server);
+
+/* Finish every queued request, then free the server (results not yet polled
+ * are dropped).  NULL is a no-op. */
+int isaac_server_destroy(isaac_server *server);
+
+/* Measurement aid (no counterpart in the paper): while set, every frame the
+ * calling thread renders with isaac_render, isaac_render_packed or their
+ * learned variants records start_event and stop_event (cudaEvent_t handles,
+ * created by the caller) on the frame's stream immediately before and after
+ * its march kernel, so cudaEventElapsedTime gives that kernel's duration.
+ * NULL, NULL stops it; one NULL and one event is ISAAC_EINVAL. */
+int isaac_time_march(void *start_event, void *stop_event);
 
 /* Free the render workspaces of the current device (synchronises the device). */
 int isaac_release_workspaces(void);

@@ -41,11 +41,19 @@ struct FrameHook {
 };
 // Validate a proposal and describe it as a hook (proposal may be null: no hook).
 int proposal_hook(const isaac_proposal *proposal, const isaac_render_opts *opts, FrameHook *hook);
-// Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic).
-int choose_lanes(long long rect_pixels, int hint);
+// Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic) when a
+// sample gathers `corner_bytes` per trilinear corner (0: unknown).
+int choose_lanes(long long rect_pixels, int hint, int corner_bytes = 0);
+// Most march chunks a warp takes per atomic (KParams::grab, guided
+// self-scheduling): 16; the environment variable ISAAC_MARCH_GRAB (1..64)
+// overrides it, 1 = one chunk per atomic.  Scheduling only: the image does not
+// depend on it.
+int march_grab();
 // Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays.
 int bind_workspace(KParams &p, cudaStream_t st);
-// Background + ray setup + optional hook + march kernel `fn` (null: background only).
-int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook);
+// Background + ray setup + optional hook + march kernel `fn` (null: background
+// only).  long_list: a hook may fill the long-ray list (not in label mode).
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook,
+                      bool long_list = true);
 
 }  // namespace isaac

@@ -5,7 +5,6 @@
 // macro cell read), clipped to [-1, n]; its value is the largest blended
 // opacity clamp(sum_s w_s * LUT_s(chain_s(v_s)).alpha, 0, 1) over those cells,
 // each source read at the cell itself (clamped to the border without guards).
-// One 256-thread block per macro cell.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -26,55 +25,101 @@ struct KGrid {
     float *grid;
 };
 
-__device__ __forceinline__ float alpha_at(const KGrid &p, const float *s_alpha, int x, int y, int z)
-{
-    float a = 0.0f;
-#pragma unroll
-    for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
-        if (s >= p.nact) break;
-        const KSource &q = p.src[s];
-        const int xi = min(max(x, q.lo), p.nx - 1 + q.hi_pad);
-        const int yi = min(max(y, q.lo), p.ny - 1 + q.hi_pad);
-        const int zi = min(max(z, q.lo), p.nz - 1 + q.hi_pad);
-        const float *b = q.base + ((long long)xi * q.sx + (long long)yi * q.sy + (long long)zi * q.sz);
-        float v[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = c < q.fdim ? __ldg(b + (long long)c * q.sc) : 0.0f;
-        const float xv = run_chain(p.ch[s], v);
-        const float pos = clamp01(xv) * 255.0f;
-        const int j = min((int)pos, 254);
-        const float f = pos - (float)j;
-        a = fmaf(q.w, lerp1(s_alpha[s * 256 + j], s_alpha[s * 256 + j + 1], f), a);
-    }
-    return clamp01(a);
-}
+constexpr int kGridThreads = 352;   // 11 warps: one pass over the 18 x 18 columns of a 16^3 cell
+constexpr int kGridZ = 8;           // z-cells whose loads are in flight together
 
-static __global__ void __launch_bounds__(256) k_opacity_grid(const __grid_constant__ KGrid p)
+// One block per column (i, j) of macro cells.  Each thread owns (x, y)
+// columns of the column's apron-extended footprint -- consecutive threads
+// take consecutive x, so a warp's loads are coalesced -- and walks its column
+// once in z, kGridZ cells at a time with their loads issued together.  Cell z
+// belongs to macro cells k with k*cell - 1 <= z <= (k+1)*cell (at most two
+// for cell >= 2), so a thread keeps two running maxima, for the lowest open
+// macro cell and the next; when z leaves the lower one, the warp's maximum
+// is folded into the grid with one atomic max (opacities are >= 0, so their
+// bit patterns order like the values; the grid is zeroed first).
+static __global__ void __launch_bounds__(kGridThreads, 2) k_opacity_grid(const __grid_constant__ KGrid p)
 {
     __shared__ float s_alpha[ISAAC_MAX_ACTIVE * 256];
-    __shared__ float s_red[8];
     for (int i = threadIdx.x; i < p.nact * 256; i += blockDim.x) s_alpha[i] = __ldg(&p.lut[i >> 8][i & 255].w);
     __syncthreads();
-    const int g = blockIdx.x;
-    const int gi = g % p.gx, gj = (g / p.gx) % p.gy, gk = g / (p.gx * p.gy);
+    const int gi = blockIdx.x % p.gx, gj = blockIdx.x / p.gx;
     const int x0 = max(gi * p.cell - 1, -1), x1 = min((gi + 1) * p.cell, p.nx);
     const int y0 = max(gj * p.cell - 1, -1), y1 = min((gj + 1) * p.cell, p.ny);
-    const int z0 = max(gk * p.cell - 1, -1), z1 = min((gk + 1) * p.cell, p.nz);
-    const int wx = x1 - x0 + 1, wy = y1 - y0 + 1, wz = z1 - z0 + 1;
-    const int total = wx * wy * wz;
-    float best = 0.0f;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int x = x0 + i % wx, y = y0 + (i / wx) % wy, z = z0 + i / (wx * wy);
-        best = fmaxf(best, alpha_at(p, s_alpha, x, y, z));
-    }
+    const int wx = x1 - x0 + 1, wy = y1 - y0 + 1;
+    const int lane = threadIdx.x & 31;
+    unsigned *grid_bits = reinterpret_cast<unsigned *>(p.grid);
+    auto flush = [&](int k, float m) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_red[w]);
-        p.grid[g] = m;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m > 0.0f)
+            atomicMax(grid_bits + ((long long)k * p.gy + gj) * p.gx + gi, __float_as_uint(m));
+    };
+    // every thread of the block runs the same number of column passes, so the
+    // warp-wide reductions in flush() see all 32 lanes
+    const int passes = (wx * wy + (int)blockDim.x - 1) / (int)blockDim.x;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int col = pass * blockDim.x + threadIdx.x;
+        const bool live = col < wx * wy;
+        const int x = x0 + (live ? col % wx : 0), y = y0 + (live ? col / wx : 0);
+        const float *cp[ISAAC_MAX_ACTIVE];
+#pragma unroll
+        for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
+            cp[s] = p.src[0].base;
+            if (s < p.nact) {
+                const KSource &q = p.src[s];
+                const int xi = min(max(x, q.lo), p.nx - 1 + q.hi_pad);
+                const int yi = min(max(y, q.lo), p.ny - 1 + q.hi_pad);
+                cp[s] = q.base + ((long long)xi * q.sx + (long long)yi * q.sy);
+            }
+        }
+        int ka = 0;                               // lowest open macro cell
+        int end_a = min(p.cell, p.nz);            // its last z
+        float ma = 0.0f, mb = 0.0f;               // running maxima of cells ka, ka + 1
+        for (int zb = -1; zb <= p.nz; zb += kGridZ) {
+            float a[kGridZ];
+#pragma unroll
+            for (int j = 0; j < kGridZ; ++j) a[j] = 0.0f;
+#pragma unroll
+            for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
+                if (s >= p.nact) break;
+                const KSource &q = p.src[s];
+                float v[kGridZ][4];
+#pragma unroll
+                for (int j = 0; j < kGridZ; ++j) {
+                    const int zi = min(max(min(zb + j, p.nz), q.lo), p.nz - 1 + q.hi_pad);
+                    const float *b = cp[s] + (long long)zi * q.sz;
+                    v[j][0] = __ldg(b);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) v[j][c] = c < q.fdim ? __ldg(b + (long long)c * q.sc) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < kGridZ; ++j) {
+                    float w[4] = {v[j][0], v[j][1], v[j][2], v[j][3]};
+                    const float xv = run_chain(p.ch[s], w);
+                    const float pos = clamp01(xv) * 255.0f;
+                    const int k = min((int)pos, 254);
+                    const float f = pos - (float)k;
+                    a[j] = fmaf(q.w, lerp1(s_alpha[s * 256 + k], s_alpha[s * 256 + k + 1], f), a[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kGridZ; ++j) {
+                const int z = zb + j;
+                if (z > p.nz) break;
+                if (z > end_a) {                  // z left cell ka: fold it, open the next
+                    flush(ka, ma);
+                    ++ka;
+                    ma = mb;
+                    mb = 0.0f;
+                    end_a = min((ka + 1) * p.cell, p.nz);
+                }
+                const float al = live ? clamp01(a[j]) : 0.0f;
+                ma = fmaxf(ma, al);
+                if (z >= (ka + 1) * p.cell - 1 && ka + 1 < p.gz) mb = fmaxf(mb, al);
+            }
+        }
+        flush(ka, ma);
+        if (ka + 1 < p.gz) flush(ka + 1, mb);
     }
 }
 
@@ -92,7 +137,7 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
         return fail(ISAAC_EINVAL, "sources, chains, luts, weights, opts and grid are required");
     if (n_sources < 1 || n_sources > ISAAC_MAX_SOURCES)
         return fail(ISAAC_EINVAL, "n_sources %d outside 1..%d", n_sources, ISAAC_MAX_SOURCES);
-    if (cell < 1 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 1..1024", cell);
+    if (cell < 2 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 2..1024", cell);
     if (opts->active_mask >> n_sources) return fail(ISAAC_EINVAL, "active_mask beyond n_sources");
     if (((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
     KGrid p;
@@ -131,6 +176,8 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
             return check_cuda("isaac_opacity_grid memset");
         return ISAAC_OK;
     }
-    k_opacity_grid<<<(unsigned)cells, 256, 0, (cudaStream_t)stream>>>(p);
+    if (cudaMemsetAsync(grid, 0, (size_t)cells * sizeof(float), (cudaStream_t)stream) != cudaSuccess)
+        return check_cuda("isaac_opacity_grid memset");
+    k_opacity_grid<<<(unsigned)(p.gx * p.gy), kGridThreads, 0, (cudaStream_t)stream>>>(p);
     return check_cuda("isaac_opacity_grid launch");
 }

@@ -262,9 +262,9 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
     if (opt->interp != 0 && opt->interp != 1) return fail(ISAAC_EINVAL, "interp must be 0 or 1");
     if (std::isnan(opt->term_alpha)) return fail(ISAAC_EINVAL, "term_alpha is NaN");
     if (!finite_n(opt->bg, 4)) return fail(ISAAC_EINVAL, "background is not finite");
-    if (opt->lanes_per_ray != 0 && opt->lanes_per_ray != 1 && opt->lanes_per_ray != 2 &&
-        opt->lanes_per_ray != 4)
-        return fail(ISAAC_EINVAL, "lanes_per_ray must be 0, 1, 2 or 4");
+    const int lpr = opt->lanes_per_ray;
+    if (lpr != 0 && lpr != 1 && lpr != 2 && lpr != 4 && lpr != 8 && lpr != 16)
+        return fail(ISAAC_EINVAL, "lanes_per_ray must be 0, 1, 2, 4, 8 or 16");
     if (n_clip < 0 || n_clip > ISAAC_MAX_CLIP)
         return fail(ISAAC_EINVAL, "%d clip planes (max %d)", n_clip, ISAAC_MAX_CLIP);
     if (n_clip > 0 && !clip) return fail(ISAAC_EINVAL, "clip is NULL with n_clip > 0");

@@ -438,6 +438,7 @@ namespace isaac {
 struct KPropose {
     WsCounters *ctr;
     RayRec *rays;
+    unsigned *longs;          // long-ray list to fill (nullptr: none)
     const __half *hw;
     const float *params;
     const float *grid;
@@ -466,11 +467,9 @@ static __global__ void __launch_bounds__(128) k_mlp_propose(const __grid_constan
     __half *xs = xs_all + warp * 16 * LD_IN;
     const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
     int seen = 0, restricted = 0;
-    for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctr->next_prop, 16u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
+    // every ray costs the same here, so warps take fixed strides of the list
+    const unsigned stride = 16u * gridDim.x * (blockDim.x >> 5);
+    for (unsigned base = 16u * (blockIdx.x * (blockDim.x >> 5) + warp); base < n; base += stride) {
         {
             const unsigned r = base + (lane >> 1);
             __half *row = xs + (lane >> 1) * LD_IN;
@@ -494,16 +493,22 @@ static __global__ void __launch_bounds__(128) k_mlp_propose(const __grid_constan
                 if (r >= n) continue;
                 ++seen;
                 const float conf = sigmoidf(h ? u2b : u2a);
-                if (conf < p.threshold) continue;
-                const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
                 const int ns = p.rays[r].nsteps;
-                int kb = (int)floorf(te * (float)ns) - p.margin;
-                int ke = (int)ceilf(tx * (float)ns) + p.margin;
-                kb = min(max(kb, 0), ns);
-                ke = min(max(ke, kb), ns);
-                p.rays[r].kbeg = kb;
-                p.rays[r].nsteps = ke;
-                ++restricted;
+                int kb = 0, ke = ns;
+                if (conf >= p.threshold) {
+                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
+                    kb = (int)floorf(te * (float)ns) - p.margin;
+                    ke = (int)ceilf(tx * (float)ns) + p.margin;
+                    kb = min(max(kb, 0), ns);
+                    ke = min(max(ke, kb), ns);
+                    p.rays[r].kbeg = kb;
+                    p.rays[r].nsteps = ke;
+                    ++restricted;
+                }
+                if (p.longs && ke - kb > kLongRaySamples) {
+                    p.rays[r].jf = kLongRay;
+                    p.longs[atomicAdd(&p.ctr->n_long, 1u)] = r;
+                }
             }
         }
         __syncwarp();
@@ -520,6 +525,7 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     KPropose p;
     p.ctr = fp.ctr;
     p.rays = fp.rays;
+    p.longs = fp.longs;
     p.hw = reinterpret_cast<const __half *>(pr->model->half_w);
     p.params = pr->model->params;
     p.grid = pr->grid;

@@ -327,7 +327,7 @@ __device__ __forceinline__ void shade_packed(const KParams &p, const float (&v)[
         for (int c = 0; c < 4; ++c) in[c] = c < fd ? pick<PAD>(v, off + c) : 0.0f;
     }
     const float x = run_chain(p.ch[I], in);
-    const float4 c = classify(s_lut + I * 256, x);
+    const float4 c = classify(lut_of<I>(p, s_lut), x);
     const float w = p.src[I].w;
     acc.x = fmaf(w, c.x, acc.x);
     acc.y = fmaf(w, c.y, acc.y);

@@ -219,7 +219,7 @@ static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains
     int rl = 1;
     if (opts->active_mask != 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-        const int want = choose_lanes(rect, opts->lanes_per_ray);
+        const int want = choose_lanes(rect, opts->lanes_per_ray, vol->pad * elem_bytes(vol->dtype));
         const unsigned sig = packed_sig(vol->f_dim, vol->n_src);
         const bool spec = sig_index(sig) >= 0 && vol->pad == next_pow2(nc);
         const PackedEntry *best = nullptr;

@@ -29,9 +29,11 @@ static void launch_pack(const KPack &p, cudaStream_t st)
 #define ISAAC_E2(N, S, P, R) ISAAC_E(N, S, P, 0, R), ISAAC_E(N, S, P, 1, R)
 static const PackedEntry k_entries[] = {
     ISAAC_E2(1, 0x1u, 1, 1), ISAAC_E2(1, 0x1u, 1, 2), ISAAC_E2(1, 0x1u, 1, 4),
+    ISAAC_E2(1, 0x1u, 1, 8), ISAAC_E2(1, 0x1u, 1, 16),
     ISAAC_E2(1, 0x3u, 4, 2), ISAAC_E2(2, 0x11u, 2, 2), ISAAC_E2(2, 0x31u, 4, 2),
     ISAAC_E2(2, 0x33u, 8, 2),
     ISAAC_E2(3, 0x133u, 8, 1), ISAAC_E2(3, 0x133u, 8, 2), ISAAC_E2(3, 0x133u, 8, 4),
+    ISAAC_E2(3, 0x133u, 8, 8), ISAAC_E2(3, 0x133u, 8, 16),
     ISAAC_E2(1, 0u, 8, 2), ISAAC_E2(2, 0u, 8, 2), ISAAC_E2(3, 0u, 8, 2), ISAAC_E2(4, 0u, 8, 2),
 };
 #undef ISAAC_E2

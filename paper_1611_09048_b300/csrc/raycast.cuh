@@ -70,13 +70,21 @@ struct RayRec {
 };
 static_assert(sizeof(RayRec) == 48, "RayRec layout");
 
-// Workspace: counters, then the ray list (one record per rectangle pixel at most).
+// Workspace: counters, then the ray list (one record per rectangle pixel at
+// most), then (render workspaces only) the long-ray list: indices of the rays
+// an interval proposal left long, which the march takes first with a whole
+// warp per ray.
 constexpr int kWsHeader = 256;
 struct WsCounters {
     unsigned n_rays;     // appended by k_setup_rays
     unsigned next;       // next list entry to march (k_raycast)
-    unsigned next_prop;  // next list entry for the interval proposal
+    unsigned n_long;     // entries of the long-ray list (appended by the proposal)
+    unsigned next_long;  // next long-ray list entry to march
 };
+// RayRec::jf of a ray that is in the long-ray list (the short-ray pass skips it).
+constexpr int kLongRay = -2;
+// A proposal puts a ray in the long-ray list when it keeps more samples than this.
+constexpr int kLongRaySamples = 96;
 
 // March modes: plain, footprint bitmap, visible-span labels.
 enum : int { MODE_PLAIN = 0, MODE_TOUCH = 1, MODE_LABEL = 2 };
@@ -97,6 +105,7 @@ struct KParams {
     int W, H;
     int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
     int max_steps;                   // samples on the longest chord of the local box
+    int grab;                        // march: most chunks of 32/RL rays a warp takes per atomic
     KSource src[ISAAC_MAX_ACTIVE];
     KChain ch[ISAAC_MAX_ACTIVE];
     const float4 *lut[ISAAC_MAX_ACTIVE];
@@ -106,6 +115,7 @@ struct KParams {
     unsigned *touched;               // optional footprint bitmap over [-1, n]^3
     WsCounters *ctr;                 // workspace counters
     RayRec *rays;                    // workspace ray list
+    unsigned *longs;                 // workspace long-ray list (nullptr: none)
     // packed (reduced-precision) volume: records over cells [-1, n]^3
     const unsigned char *rec;        // record of cell (x,y,z) at ((z+1)*PY + y+1)*PX + x+1
     const float *scales;             // E4M3: per 8^3 brick (from cell -1), `pad` floats
@@ -286,6 +296,14 @@ __device__ __forceinline__ void fetch_source(const KParams &p, const Geo &g, flo
     }
 }
 
+// LUT of active source I: the block's shared copy, or (s_lut == nullptr, the
+// batched kernels whose blocks mix requests) the request's global array.
+template <int I>
+__device__ __forceinline__ const float4 *lut_of(const KParams &p, const float4 *s_lut)
+{
+    return s_lut ? s_lut + I * 256 : p.lut[I];
+}
+
 template <int I, unsigned SIG, int INTERP, typename Idx>
 __device__ __forceinline__ void shade_source(const KParams &p, const Geo &g, const float4 *s_lut,
                                              float4 &acc)
@@ -293,7 +311,7 @@ __device__ __forceinline__ void shade_source(const KParams &p, const Geo &g, con
     float v[4];
     fetch_source<I, SIG, INTERP, Idx>(p, g, v);
     const float x = run_chain(p.ch[I], v);
-    blend(acc, p.src[I].w, classify(s_lut + I * 256, x));
+    blend(acc, p.src[I].w, classify(lut_of<I>(p, s_lut), x));
 }
 
 template <unsigned SIG, int INTERP, typename Idx, int... Is>
@@ -439,7 +457,8 @@ static __global__ void k_fill_background(const __grid_constant__ KParams p)
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.ctr) {
         p.ctr->n_rays = 0u;
         p.ctr->next = 0u;
-        p.ctr->next_prop = 0u;
+        p.ctr->n_long = 0u;
+        p.ctr->next_long = 0u;
     }
     const size_t total = (size_t)p.W * (size_t)p.H;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
@@ -477,70 +496,115 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
 
 // ------------------------------------------------------------------ march
 
-// Persistent warps; each takes chunks of 32/RL rays from the list.  Lanes of a
-// group evaluate samples k+0 .. k+RL-1 of their ray together; every lane then
-// composites the group's RL samples in order, stopping at the termination
-// sample, so all lanes hold the same C and A.
+// One ray of the list, marched by the RL lanes of its group.  Lanes of a
+// group evaluate samples k+0 .. k+RL-1 together; every lane then composites
+// the group's RL samples in order, stopping at the termination sample, so all
+// lanes hold the same C and A.
+template <class Shader, int RL, bool LABEL>
+__device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut, unsigned idx,
+                                          int lane)
+{
+    const int sub = lane & (RL - 1);
+    const RayRec r = p.rays[idx];
+    if (RL < 32 && p.longs && r.jf == kLongRay) return;   // marched by a whole warp
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    int ns = 0, jf = -1, jl = -1;
+    const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
+    for (int k = r.kbeg; k < r.nsteps; k += RL) {
+        const int kk = k + sub;
+        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (kk < r.nsteps) {
+            const float s = (float)kk * p.step;
+            c = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey), fmaf(s, r.dz, r.ez));
+        }
+        bool done = false;
+        auto composite = [&](int j) {
+            float4 cj = c;
+            if (RL > 1) {
+                cj.x = __shfl_sync(gmask, c.x, j, RL);
+                cj.y = __shfl_sync(gmask, c.y, j, RL);
+                cj.z = __shfl_sync(gmask, c.z, j, RL);
+                cj.w = __shfl_sync(gmask, c.w, j, RL);
+            }
+            if (!done && k + j < r.nsteps) {
+                const float a = clamp01(cj.w);
+                if (LABEL && a > 0.0f) {
+                    if (jf < 0) jf = k + j;
+                    jl = k + j;
+                }
+                const float t = (1.0f - A) * a;
+                C0 = fmaf(t, cj.x, C0);
+                C1 = fmaf(t, cj.y, C1);
+                C2 = fmaf(t, cj.z, C2);
+                A += t;
+                ++ns;
+                done = A >= p.term;
+            }
+        };
+        if constexpr (RL <= 8) {
+#pragma unroll
+            for (int j = 0; j < RL; ++j) composite(j);
+        } else {   // whole-warp rays: a partly rolled loop keeps the register count down
+#pragma unroll 4
+            for (int j = 0; j < RL; ++j) composite(j);
+        }
+        if (done) break;
+    }
+    if (sub == 0) {
+        write_pixel(p, r.pix, C0, C1, C2, A, ns);
+        if (LABEL) {
+            p.rays[idx].jf = jf;
+            p.rays[idx].jl = jl;
+        }
+    }
+}
+
+// Persistent warps with guided self-scheduling: a warp takes chunks of 32/RL
+// rays from the list, as many per atomic as 1/(2W) of what was left at its
+// previous take (W warps in the grid; at most p.grab, at least one), so that
+// long lists need few atomics on the one shared counter while the last
+// chunks stay small enough to balance the warps.
+//
+// With a long-ray list (rays an interval proposal left long among mostly
+// short ones), warps first take its rays one at a time with all 32 lanes, so
+// that the few long rays do not leave a tail of sequential gathers; the
+// short-ray pass then skips them.  The lane count never changes a pixel.
+template <class Shader>
+__device__ __noinline__ void march_long_rays(const KParams &p, const float4 *s_lut)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned n_long = *(volatile unsigned *)&p.ctr->n_long;
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(&p.ctr->next_long, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_long) break;
+        march_ray<Shader, 32, false>(p, s_lut, p.longs[i], lane);
+    }
+}
+
 template <int NACT, class Shader, int RL, bool LABEL = false>
 __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
 {
-    constexpr int RAYS = 32 / RL;
+    constexpr unsigned RAYS = 32 / RL;
     const int lane = threadIdx.x & 31;
-    const int sub = lane & (RL - 1);
+    // (a separate function, so that its registers do not add to the short pass's)
+    if (!LABEL && RL < 32 && p.longs) march_long_rays<Shader>(p, s_lut);
     const unsigned n_rays = *(volatile unsigned *)&p.ctr->n_rays;
+    const unsigned cap = (unsigned)max(p.grab, 1);
+    const unsigned per_take = RAYS * 2u * gridDim.x * (blockDim.x >> 5);
+    unsigned last = 0;
     for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctr->next, (unsigned)RAYS);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_rays) break;
-        const unsigned idx = base + (unsigned)(lane / RL);
-        if (idx < n_rays) {
-            const RayRec r = p.rays[idx];
-            float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-            int ns = 0, jf = -1, jl = -1;
-            const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
-            for (int k = r.kbeg; k < r.nsteps; k += RL) {
-                const int kk = k + sub;
-                float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (kk < r.nsteps) {
-                    const float s = (float)kk * p.step;
-                    c = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey),
-                                      fmaf(s, r.dz, r.ez));
-                }
-                bool done = false;
-#pragma unroll
-                for (int j = 0; j < RL; ++j) {
-                    float4 cj = c;
-                    if (RL > 1) {
-                        cj.x = __shfl_sync(gmask, c.x, j, RL);
-                        cj.y = __shfl_sync(gmask, c.y, j, RL);
-                        cj.z = __shfl_sync(gmask, c.z, j, RL);
-                        cj.w = __shfl_sync(gmask, c.w, j, RL);
-                    }
-                    if (!done && k + j < r.nsteps) {
-                        const float a = clamp01(cj.w);
-                        if (LABEL && a > 0.0f) {
-                            if (jf < 0) jf = k + j;
-                            jl = k + j;
-                        }
-                        const float t = (1.0f - A) * a;
-                        C0 = fmaf(t, cj.x, C0);
-                        C1 = fmaf(t, cj.y, C1);
-                        C2 = fmaf(t, cj.z, C2);
-                        A += t;
-                        ++ns;
-                        done = A >= p.term;
-                    }
-                }
-                if (done) break;
-            }
-            if (sub == 0) {
-                write_pixel(p, r.pix, C0, C1, C2, A, ns);
-                if (LABEL) {
-                    p.rays[idx].jf = jf;
-                    p.rays[idx].jl = jl;
-                }
-            }
+        const unsigned grab = min(max((n_rays - min(last, n_rays)) / per_take, 1u), cap);
+        unsigned first = 0;
+        if (lane == 0) first = atomicAdd(&p.ctr->next, RAYS * grab);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (first >= n_rays) break;
+        last = first;
+        for (unsigned c = 0; c < grab; ++c) {
+            const unsigned idx = first + c * RAYS + (unsigned)(lane / RL);
+            if (first + c * RAYS >= n_rays) break;
+            if (idx < n_rays) march_ray<Shader, RL, LABEL>(p, s_lut, idx, lane);
         }
     }
 }

@@ -20,9 +20,11 @@ static void launch_zc(const KParams &p, dim3 grid, cudaStream_t st)
 // planes.  Anything else runs the generic kernel with run-time f_dim.
 static const ZcEntry k_entries[] = {
     ISAAC_Z2(1, 0x9u, 1, false, MODE_PLAIN), ISAAC_Z2(1, 0x9u, 2, false, MODE_PLAIN),
-    ISAAC_Z2(1, 0x9u, 4, false, MODE_PLAIN),
+    ISAAC_Z2(1, 0x9u, 4, false, MODE_PLAIN), ISAAC_Z2(1, 0x9u, 8, false, MODE_PLAIN),
+    ISAAC_Z2(1, 0x9u, 16, false, MODE_PLAIN),
     ISAAC_Z2(3, 0x9BBu, 1, false, MODE_PLAIN), ISAAC_Z2(3, 0x9BBu, 2, false, MODE_PLAIN),
-    ISAAC_Z2(3, 0x9BBu, 4, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0x9BBu, 4, false, MODE_PLAIN), ISAAC_Z2(3, 0x9BBu, 8, false, MODE_PLAIN),
+    ISAAC_Z2(3, 0x9BBu, 16, false, MODE_PLAIN),
     ISAAC_Z2(3, 0x933u, 4, false, MODE_PLAIN),
     ISAAC_Z2(1, 0u, 4, false, MODE_PLAIN), ISAAC_Z2(2, 0u, 4, false, MODE_PLAIN),
     ISAAC_Z2(3, 0u, 4, false, MODE_PLAIN), ISAAC_Z2(4, 0u, 4, false, MODE_PLAIN),

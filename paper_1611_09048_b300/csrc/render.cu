@@ -30,7 +30,7 @@ static std::vector<Workspace> g_ws;
 int bind_workspace(KParams &p, cudaStream_t st)
 {
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-    const size_t need = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * sizeof(RayRec);
+    const size_t need = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * (sizeof(RayRec) + sizeof(unsigned));
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
     std::lock_guard<std::mutex> lock(g_ws_mu);
@@ -58,6 +58,7 @@ int bind_workspace(KParams &p, cudaStream_t st)
     }
     p.ctr = static_cast<WsCounters *>(w->ptr);
     p.rays = reinterpret_cast<RayRec *>(static_cast<char *>(w->ptr) + kWsHeader);
+    p.longs = reinterpret_cast<unsigned *>(p.rays + std::max(1LL, rect));
     return ISAAC_OK;
 }
 
@@ -78,16 +79,39 @@ static int sm_count()
     return cached[dev];
 }
 
-int choose_lanes(long long rect_pixels, int hint)
+int choose_lanes(long long rect_pixels, int hint, int corner_bytes)
 {
     (void)rect_pixels;
-    // Measured on B300 at 1080p over 512^3 (three sources): 1, 2 and 4 lanes
-    // per ray give 5.4, 10.0 and 13.0 G samples/s; more lanes per ray keep more
-    // independent gathers in flight per warp, so 4 is the default.
-    return hint ? hint : 4;
+    if (hint) return hint;
+    // Measured on B300 at 1080p over 512^3: with E, B, rho in FP32 (28 bytes
+    // per corner) 1, 2, 4, 8 and 16 lanes per ray give 5.4, 10.0, 13.4, 15.0
+    // and 13.7 G samples/s; with 16-bit records (16 bytes) and with one FP32
+    // scalar 4 lanes are fastest.  More lanes per ray put more of a warp's
+    // gathers on one ray's neighbouring cells, fewer leave more rays in flight.
+    return corner_bytes >= 24 ? 8 : 4;
 }
 
-int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook)
+static int zc_corner_bytes(const KParams &p, int nact)
+{
+    int b = 0;
+    for (int a = 0; a < nact; ++a) b += 4 * p.src[a].fdim;
+    return b;
+}
+
+int march_grab()
+{
+    static const int env = [] {
+        const char *e = getenv("ISAAC_MARCH_GRAB");
+        return e ? atoi(e) : 0;
+    }();
+    return env >= 1 && env <= 64 ? env : 16;
+}
+
+// Events recorded around the march kernel of this thread's frames (isaac_time_march).
+static thread_local cudaEvent_t t_march_start = nullptr, t_march_stop = nullptr;
+
+int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook,
+                      bool long_list)
 {
     const bool any = fn && p.rx1 > p.rx0 && p.ry1 > p.ry0;
     if (!any) {   // nothing to ray cast: the background covers every pixel
@@ -98,6 +122,8 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const
     }
     int rc = bind_workspace(p, st);
     if (rc) return rc;
+    if (!hook || !long_list) p.longs = nullptr;   // only a proposal fills the long-ray list
+    p.grab = march_grab();
     launch_fill(p, st);
     launch_setup(p, st);
     if (hook) {
@@ -107,7 +133,9 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
     const long long want = (rect * rl + 127) / 128;
     const long long cap = (long long)sm_count() * 8;
+    if (t_march_start) cudaEventRecord(t_march_start, st);
     fn(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
+    if (t_march_stop) cudaEventRecord(t_march_stop, st);
     return check_cuda("render launch");
 }
 
@@ -198,7 +226,7 @@ extern "C" int isaac_render(const isaac_source *sources, const isaac_chain *chai
     int rl = 1;
     if (nact > 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-        const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray);
+        const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact));
         fn = find_zc(nact, sig, opts->interp, wide, p.touched ? MODE_TOUCH : MODE_PLAIN, want, &rl);
         if (!fn)
             return fail(ISAAC_ENOTSUP, "no kernel for %d sources (footprint with 64-bit offsets?)",
@@ -230,10 +258,11 @@ static int render_mode(const isaac_source *sources, const isaac_chain *chains, i
     int rl = 1;
     if (nact > 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-        fn = find_zc(nact, sig, opts->interp, wide, mode, choose_lanes(rect, opts->lanes_per_ray), &rl);
+        fn = find_zc(nact, sig, opts->interp, wide, mode,
+                     choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact)), &rl);
         if (!fn) return fail(ISAAC_ENOTSUP, "no kernel for %d sources in this mode", nact);
     }
-    return launch_frame_with(p, fn, rl, st, hook);
+    return launch_frame_with(p, fn, rl, st, hook, mode != MODE_LABEL);
 }
 
 extern "C" int isaac_trace(const isaac_source *sources, const isaac_chain *chains,
@@ -302,3 +331,13 @@ extern "C" int isaac_release_workspaces(void)
 extern "C" const char *isaac_last_error(void) { return last_error(); }
 
 extern "C" int isaac_abi_version(void) { return ISAAC_ABI_VERSION; }
+
+extern "C" int isaac_time_march(void *start_event, void *stop_event)
+{
+    clear_error();
+    if ((start_event == nullptr) != (stop_event == nullptr))
+        return fail(ISAAC_EINVAL, "give both events or neither");
+    t_march_start = static_cast<cudaEvent_t>(start_event);
+    t_march_stop = static_cast<cudaEvent_t>(stop_event);
+    return ISAAC_OK;
+}

@@ -29,7 +29,9 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_pack", "isaac_render_packed", "isaac_release_workspaces",
            "isaac_opacity_grid", "isaac_render_noalloc", "isaac_trace", "isaac_render_learned",
            "isaac_render_packed_learned", "isaac_mlp_sync", "isaac_mlp_features",
-           "isaac_mlp_forward", "isaac_mlp_train_step")
+           "isaac_mlp_forward", "isaac_mlp_train_step", "isaac_server_create",
+           "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
+           "isaac_server_destroy", "isaac_time_march")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -92,6 +94,20 @@ class Mlp(C.Structure):
 class Proposal(C.Structure):
     _fields_ = [("model", C.POINTER(Mlp)), ("grid", C.c_void_p), ("cell", C.c_int32),
                 ("threshold", C.c_float), ("margin", C.c_int32), ("stats", C.c_void_p)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("n_streams", C.c_int32), ("max_batch", C.c_int32)]
+
+
+class ServerRequest(C.Structure):
+    _fields_ = [("camera", Camera), ("luts", C.c_void_p), ("chains", C.POINTER(Chain)),
+                ("out", C.c_void_p), ("tag", C.c_int64)]
+
+
+class ServerResult(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("status", C.c_int32), ("batch_size", C.c_int32),
+                ("t_submit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double)]
 
 
 def pack_mlp_params(named) -> np.ndarray:
@@ -171,6 +187,21 @@ def load(path: Optional[str] = None):
         lib.isaac_mlp_train_step.restype = C.c_int
         lib.isaac_mlp_train_step.argtypes = [C.POINTER(Mlp), C.c_void_p, C.c_void_p, C.c_int64,
                                              C.c_float, C.c_int32, C.c_void_p, C.c_void_p]
+        lib.isaac_server_create.restype = C.c_int
+        lib.isaac_server_create.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32,
+                                            C.c_void_p, C.c_void_p, C.POINTER(Packed),
+                                            C.POINTER(RenderOpts), C.POINTER(Plane), C.c_int32,
+                                            C.POINTER(ServerConfig), C.POINTER(C.c_void_p)]
+        lib.isaac_server_submit.restype = C.c_int
+        lib.isaac_server_submit.argtypes = [C.c_void_p, C.POINTER(ServerRequest)]
+        lib.isaac_server_poll.restype = C.c_int
+        lib.isaac_server_poll.argtypes = [C.c_void_p, C.POINTER(ServerResult), C.c_int32, C.c_double]
+        lib.isaac_server_outstanding.restype = C.c_int
+        lib.isaac_server_outstanding.argtypes = [C.c_void_p]
+        lib.isaac_server_destroy.restype = C.c_int
+        lib.isaac_server_destroy.argtypes = [C.c_void_p]
+        lib.isaac_time_march.restype = C.c_int
+        lib.isaac_time_march.argtypes = [C.c_void_p, C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
         lib.isaac_abi_version.restype = C.c_int
         _lib = lib
@@ -234,6 +265,14 @@ def make_planes(clip):
     return arr, len(clip)
 
 
+def time_march(start=None, stop=None):
+    """Record torch.cuda.Event ``start``/``stop`` around the march kernel of
+    this thread's next frames (None, None: stop).  The events must have been
+    recorded once before, so that their CUDA handles exist."""
+    check(load().isaac_time_march(C.c_void_p(start.cuda_event) if start is not None else None,
+                                  C.c_void_p(stop.cuda_event) if stop is not None else None))
+
+
 def _stream_handle(stream):
     import torch
     if stream is None:
@@ -256,7 +295,10 @@ class DeviceScene:
         self.sources = (Source * n_src)()
         self.chains = (Chain * n_src)()
         for s, src in enumerate(scene.sources):
-            t = torch.from_numpy(np.ascontiguousarray(src.data, np.float32)).to(self.device)
+            if isinstance(src.data, torch.Tensor):       # already resident: used in place
+                t = src.data.to(self.device, torch.float32).contiguous().reshape(-1)
+            else:
+                t = torch.from_numpy(np.ascontiguousarray(src.data, np.float32)).to(self.device)
             self.data.append(t)
             self._describe(s, src, t)
             self.chains[s] = make_chain(scene.chains[s])
@@ -459,6 +501,118 @@ class PackedVolume:
         ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
         self.launch(self.prepare(mv, proj, out, f32, ns, mask, lanes), stream)
         return out, f32, ns
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """Continuous-batching render server over one DeviceScene (zero-copy
+    sources) or PackedVolume (BF16 packed copy); see isaac_server_create.
+
+    ``submit`` queues one request and returns its tag; the request's ``out``
+    (a pinned host or device uint8 tensor of shape (H, W, 4)) is kept alive
+    here until ``poll`` reports the request finished."""
+
+    def __init__(self, target, budget=256 << 20, n_streams=4, max_batch=16, lanes=None):
+        self.target = target
+        lib = load()
+        handle = C.c_void_p()
+        cfg = ServerConfig(int(budget), int(n_streams), int(max_batch))
+        if isinstance(target, PackedVolume):
+            sc = target.ds.scene
+            self.n_src = len(target.src_index)
+            opts = make_opts(sc, (1 << self.n_src) - 1, lanes)
+            planes, n_clip = make_planes(sc.clip)
+            check(lib.isaac_server_create(None, target.chains, self.n_src, target.luts.data_ptr(),
+                                          C.cast(target.weights, C.c_void_p), C.byref(target.desc),
+                                          C.byref(opts), planes, n_clip, C.byref(cfg),
+                                          C.byref(handle)))
+        else:
+            sc = target.scene
+            self.n_src = len(sc.sources)
+            opts = make_opts(sc, None, lanes)
+            planes, n_clip = make_planes(sc.clip)
+            check(lib.isaac_server_create(target.sources, target.chains, self.n_src,
+                                          target.luts.data_ptr(), C.cast(target.weights, C.c_void_p),
+                                          None, C.byref(opts), planes, n_clip, C.byref(cfg),
+                                          C.byref(handle)))
+        self.handle = handle
+        self._live = {}
+        self._next_tag = 0
+
+    def submit(self, mv, proj, width, height, out, luts=None, chains=None):
+        """Queue a request; ``luts`` (n_src, 256, 4) float32 host array and
+        ``chains`` (list of n_src chain specs) override the server's."""
+        rq = ServerRequest()
+        rq.camera = make_camera(mv, proj, width, height)
+        keep = [out]
+        if luts is not None:
+            la = np.ascontiguousarray(luts, np.float32).reshape(-1)
+            if la.size != self.n_src * 256 * 4:
+                raise ValueError(f"luts must hold {self.n_src} x 256 x 4 floats")
+            keep.append(la)
+            rq.luts = la.ctypes.data
+        if chains is not None:
+            if len(chains) != self.n_src:
+                raise ValueError(f"chains must list {self.n_src} chains")
+            ca = (Chain * self.n_src)(*[make_chain(c) for c in chains])
+            keep.append(ca)
+            rq.chains = ca
+        rq.out = out.data_ptr()
+        rq.tag = self._next_tag
+        check(load().isaac_server_submit(self.handle, C.byref(rq)))
+        self._live[rq.tag] = keep
+        self._next_tag += 1
+        return rq.tag
+
+    def poll(self, max_results=256, wait=0.0):
+        """Finished requests as dicts (tag, status, batch_size, t_submit,
+        t_launch, t_done; times in seconds since the server started)."""
+        buf = (ServerResult * max_results)()
+        n = load().isaac_server_poll(self.handle, buf, max_results, float(wait))
+        if n < 0:
+            check(n)
+        out = []
+        for i in range(n):
+            r = buf[i]
+            self._live.pop(r.tag, None)
+            out.append({"tag": r.tag, "status": r.status, "batch_size": r.batch_size,
+                        "t_submit": r.t_submit, "t_launch": r.t_launch, "t_done": r.t_done})
+        return out
+
+    def outstanding(self):
+        n = load().isaac_server_outstanding(self.handle)
+        if n < 0:
+            check(n)
+        return n
+
+    def drain(self, timeout=60.0):
+        """Poll until every submitted request has finished; returns the results."""
+        import time
+        res, t_end = [], time.time() + timeout
+        while self._live and time.time() < t_end:
+            res += self.poll(wait=0.05)
+        if self._live:
+            raise TimeoutError(f"{len(self._live)} requests still outstanding")
+        return res
+
+    def close(self):
+        if self.handle:
+            check(load().isaac_server_destroy(self.handle))
+            self.handle = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------- learned proposal

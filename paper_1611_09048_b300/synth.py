@@ -278,7 +278,14 @@ def source_from_zyx(arr: np.ndarray, guard: int, layout: str = "aos", name: str 
     """Describe a (S,S,S[,C]) z-major array as a strided source without copying
     (``aos``: components innermost) or as component planes (``soa``)."""
     fdim = 1 if arr.ndim == 3 else arr.shape[3]
-    S = arr.shape[:3]
+    S = tuple(int(s) for s in arr.shape[:3])
+    if not isinstance(arr, np.ndarray) and hasattr(arr, "contiguous"):   # a torch tensor
+        if layout != "aos" and fdim > 1:
+            raise ValueError("tensor sources are described in place (AoS) only")
+        data = arr.contiguous().reshape(-1)
+        sx, sy, sz, cs = fdim, fdim * S[2], fdim * S[2] * S[1], 1
+        return Source(data=data, fdim=fdim, offset=guard * (sx + sy + sz), strides=(sx, sy, sz),
+                      cstride=cs, guard=guard, name=name)
     if layout == "aos" or fdim == 1:
         data = np.ascontiguousarray(arr, dtype=np.float32).reshape(-1)
         sx, sy, sz, cs = fdim, fdim * S[2], fdim * S[2] * S[1], 1
@@ -292,41 +299,48 @@ def source_from_zyx(arr: np.ndarray, guard: int, layout: str = "aos", name: str 
                   guard=guard, name=name)
 
 
-def value_noise(n: int, seed: int, octaves=((64, 0.5), (32, 0.3), (16, 0.2))) -> np.ndarray:
+def value_noise(n: int, seed: int, octaves=((64, 0.5), (32, 0.3), (16, 0.2)), device=None):
     """Smooth seeded noise in [0, 1): random lattice values every L cells,
-    trilinearly upsampled, summed over octaves with the given weights."""
+    trilinearly upsampled, summed over octaves with the given weights.  A numpy
+    array, or a torch tensor on `device` when one is given (same values up to
+    float rounding of the upsampling)."""
     import torch
     rng = np.random.default_rng(seed)
-    out = torch.zeros((n, n, n), dtype=torch.float32)
+    dev = torch.device(device) if device is not None else torch.device("cpu")
+    out = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
     for L, w in octaves:
         L = max(2, min(L, n))
         m = n // L + 2
-        lat = torch.from_numpy(rng.uniform(0.0, 1.0, (1, 1, m, m, m)).astype(np.float32))
+        lat = torch.from_numpy(rng.uniform(0.0, 1.0, (1, 1, m, m, m)).astype(np.float32)).to(dev)
         up = torch.nn.functional.interpolate(lat, size=(m - 1) * L, mode="trilinear",
                                              align_corners=True)[0, 0, :n, :n, :n]
         out += w * up
-    return out.numpy()
+    return out if device is not None else out.numpy()
 
 
 def bubble_field(n: int = 512, frame: int = 0, seed: int = 0, noise=None,
-                 thickness: float = 6.0, speed: float = 2.0) -> np.ndarray:
+                 thickness: float = 6.0, speed: float = 2.0, device=None):
     """Laser-wakefield-like bubble: an ellipsoidal shell (semi-axes 60/60/90
     cells at n = 512, scaled with n) of Gaussian profile and the given
     thickness, centred on the x-y axis and moving +z by `speed` cells per frame
-    from z = 150 (scaled), plus 0.1 * seeded value noise.  Shape (z, y, x)."""
+    from z = 150 (scaled), plus 0.1 * seeded value noise.  Shape (z, y, x);
+    numpy float32, or a torch tensor on `device` when one is given."""
     import torch
+    dev = torch.device(device) if device is not None else torch.device("cpu")
     s = n / 512.0
     ax, ay, az = 60.0 * s, 60.0 * s, 90.0 * s
     cz = (150.0 + speed * frame) * s
-    c = torch.arange(n, dtype=torch.float32) + 0.5
+    c = torch.arange(n, dtype=torch.float32, device=dev) + 0.5
     z, y, x = c[:, None, None], c[None, :, None], c[None, None, :]
     r = torch.sqrt(((x - n / 2) / ax) ** 2 + ((y - n / 2) / ay) ** 2 + ((z - cz) / az) ** 2)
     d = (r - 1.0) * min(ax, ay, az)
     sig = max(thickness * s, 1.0) / 2.0
     shell = torch.exp(-(d * d) / (2.0 * sig * sig))
     if noise is None:
-        noise = value_noise(n, seed + 77)
-    return (shell + 0.1 * torch.from_numpy(np.asarray(noise))).numpy().astype(np.float32)
+        noise = value_noise(n, seed + 77, device=device)
+    noise_t = noise if isinstance(noise, torch.Tensor) else torch.from_numpy(np.asarray(noise))
+    f = shell + 0.1 * noise_t.to(dev)
+    return f if device is not None else f.numpy().astype(np.float32)
 
 
 def bubble_lut(seed: int, alpha_max: float = 0.3) -> np.ndarray:

@@ -186,3 +186,59 @@ def test_rejects_misaligned_lut():
     a = _valid_call_args()
     a["luts"] = FAKE + 4
     _expect(a, isaac.EINVAL, "16-byte")
+
+
+# ------------------------------------------------------------ serving loop
+
+def test_server_struct_sizes():
+    assert C.sizeof(isaac.ServerConfig) == 8 + 4 + 4
+    assert C.sizeof(isaac.ServerRequest) == (256 + 8) + 8 + 8 + 8 + 8
+    assert C.sizeof(isaac.ServerResult) == 8 + 4 + 4 + 3 * 8
+
+
+def _server_create(a, cfg, vol=None):
+    lib = isaac.load()
+    h = C.c_void_p()
+    rc = lib.isaac_server_create(a["src"], a["chains"], a["n_src"], a["luts"],
+                                 C.cast(a["weights"], C.c_void_p), vol, C.byref(a["opts"]),
+                                 a["clip"], a["n_clip"], C.byref(cfg), C.byref(h))
+    return rc, h, lib.isaac_last_error().decode()
+
+
+@pytest.mark.parametrize("cfg,fragment", [
+    ((1 << 20, 0, 4), "n_streams"),
+    ((1 << 20, 9, 4), "n_streams"),
+    ((1 << 20, 2, 0), "max_batch"),
+    ((1 << 20, 2, 65), "max_batch"),
+    ((1 << 19, 2, 4), "budget"),
+])
+def test_server_create_rejects_bad_config(cfg, fragment):
+    rc, h, msg = _server_create(_valid_call_args(), isaac.ServerConfig(*cfg))
+    assert rc == isaac.EINVAL and fragment in msg and not h.value, (rc, msg)
+
+
+def test_server_create_rejects_bad_sources_before_any_allocation():
+    a = _valid_call_args(fdim=5)
+    rc, h, msg = _server_create(a, isaac.ServerConfig(1 << 20, 1, 4))
+    assert rc == isaac.EINVAL and "f_dim" in msg and not h.value
+    a = _valid_call_args()
+    a["luts"] = FAKE + 4
+    rc, h, msg = _server_create(a, isaac.ServerConfig(1 << 20, 1, 4))
+    assert rc == isaac.EINVAL and "16-byte" in msg and not h.value
+
+
+def test_server_calls_reject_null_handles():
+    lib = isaac.load()
+    rq = isaac.ServerRequest()
+    assert lib.isaac_server_submit(None, C.byref(rq)) == isaac.EINVAL
+    res = (isaac.ServerResult * 4)()
+    assert lib.isaac_server_poll(None, res, 4, 0.0) == isaac.EINVAL
+    assert lib.isaac_server_outstanding(None) == isaac.EINVAL
+    assert lib.isaac_server_destroy(None) == isaac.OK
+
+
+def test_time_march_wants_both_events_or_neither():
+    lib = isaac.load()
+    assert lib.isaac_time_march(C.c_void_p(FAKE), None) == isaac.EINVAL
+    assert "both" in lib.isaac_last_error().decode()
+    assert lib.isaac_time_march(None, None) == isaac.OK

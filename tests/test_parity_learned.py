@@ -33,7 +33,7 @@ def _fp16(a):
 
 def test_trace_labels_match_oracle(cuda_ok):
     import torch
-    sc = synth.scene_bubble(64, frame=2, seed=1, width=96, height=72, dist_factor=1.5)
+    sc = synth.scene_bubble(64, frame=10, seed=1, width=128, height=96, dist_factor=1.0)
     ds = isaac.DeviceScene(sc)
     rays, count, out, f32, ns = ds.trace(want_f32=True, want_nsamp=True)
     torch.cuda.synchronize()
@@ -47,7 +47,7 @@ def test_trace_labels_match_oracle(cuda_ok):
     got = rec[:, 9:11]
     m_term = ref["margin"].reshape(-1, 4)[pix, 2]
     same = np.all(got == want, axis=1)
-    assert n > 500 and (want[:, 0] >= 0).sum() > 50
+    assert n > 3000 and (want[:, 0] >= 0).sum() > 150
     # a different span is only allowed where the termination decision was a tie
     assert np.all(same | (m_term < 1e-3)), np.flatnonzero(~same)[:10]
 

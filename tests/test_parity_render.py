@@ -162,14 +162,14 @@ def test_constant_slab_closed_form_on_gpu(cuda_ok):
 @pytest.mark.parametrize("fmt", [None, "bf16", "e4m3"])
 @pytest.mark.parametrize("layout", ["aos", "soa"])
 def test_lanes_per_ray_do_not_change_the_image(cuda_ok, fmt, layout):
-    """1, 2 or 4 threads per ray composite the same samples in the same order:
-    the images (and sample counts) are bit-identical."""
+    """1, 2, 4, 8 or 16 threads per ray composite the same samples in the same
+    order: the images (and sample counts) are bit-identical."""
     import torch
     sc = small_pic_scene(n=24, guard=2, width=70, height=52, seed=8, layout=layout,
                          dist_factor=1.0)
     ds = isaac.DeviceScene(sc)
     target = ds if fmt is None else ds.pack(fmt)
-    outs = [target.render(want_f32=True, want_nsamp=True, lanes=rl) for rl in (1, 2, 4)]
+    outs = [target.render(want_f32=True, want_nsamp=True, lanes=rl) for rl in (1, 2, 4, 8, 16)]
     torch.cuda.synchronize()
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
