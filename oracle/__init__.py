@@ -5,4 +5,4 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 the C source, its structures and the op-code table here are its own.
 """
 from .oracle import (build, render, invert4, max_threads, chain_eval, classify,  # noqa: F401
-                     quantize, lowp_copy, opacity_grid, OP_CODES)
+                     quantize, lowp_copy, opacity_grid, range_grid, OP_CODES)

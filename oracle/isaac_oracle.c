@@ -613,6 +613,72 @@ int orc_opacity_grid(const orc_source *src, const orc_chain *ch, const float *lu
     return 0;
 }
 
+/* Value-range grid (the data of classical empty-space skipping).  For macro
+ * cell g -- the same box as in orc_opacity_grid, [i*cell - 1, (i+1)*cell]
+ * per axis clipped to [-1, n] -- and each component of each active source,
+ * the smallest and largest value read from the box's cells, each cell read
+ * as the renderer reads it (guard cells when present, else the clamped
+ * border).  Any NaN among them makes that component's range [-inf, +inf].
+ * out[(g * slots + slot) * 2 + {0: min, 1: max}], slot running over the
+ * active sources' components in source order; slots <= 16. */
+int orc_range_grid(const orc_source *src, int32_t n_src, const int64_t n[3], uint32_t mask,
+                   int32_t cell, float *out, int32_t n_threads)
+{
+    if (!src || !out || cell < 1 || n_src < 1 || n_src > ORC_MAX_SRC) return -1;
+    int slots = 0;
+    for (int s = 0; s < n_src; ++s)
+        if ((mask >> s) & 1u) {
+            if (src[s].fdim < 1 || src[s].fdim > 4) return -1;
+            slots += src[s].fdim;
+        }
+    if (slots < 1 || slots > 16) return -1;
+    int64_t G[3] = {(n[0] + cell - 1) / cell, (n[1] + cell - 1) / cell, (n[2] + cell - 1) / cell};
+    int64_t total = G[0] * G[1] * G[2];
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 4) num_threads(n_threads)
+#endif
+    for (int64_t g = 0; g < total; ++g) {
+        int64_t gi = g % G[0], gj = (g / G[0]) % G[1], gk = g / (G[0] * G[1]);
+        int64_t lo[3] = {gi * cell - 1, gj * cell - 1, gk * cell - 1};
+        int64_t hi[3] = {(gi + 1) * cell, (gj + 1) * cell, (gk + 1) * cell};
+        for (int a = 0; a < 3; ++a) {
+            if (lo[a] < -1) lo[a] = -1;
+            if (hi[a] > n[a]) hi[a] = n[a];
+        }
+        double mn[16], mx[16];
+        int nan[16];
+        for (int k = 0; k < 16; ++k) {
+            mn[k] = INFINITY;
+            mx[k] = -INFINITY;
+            nan[k] = 0;
+        }
+        for (int64_t z = lo[2]; z <= hi[2]; ++z)
+            for (int64_t y = lo[1]; y <= hi[1]; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x) {
+                    int slot = 0;
+                    for (int s = 0; s < n_src; ++s) {
+                        if (!((mask >> s) & 1u)) continue;
+                        double v[4];
+                        orc_fetch(&src[s], orc_axis_index(x, n[0], src[s].guard),
+                                  orc_axis_index(y, n[1], src[s].guard),
+                                  orc_axis_index(z, n[2], src[s].guard), v);
+                        for (int c = 0; c < src[s].fdim; ++c, ++slot) {
+                            if (v[c] != v[c]) nan[slot] = 1;
+                            if (v[c] < mn[slot]) mn[slot] = v[c];
+                            if (v[c] > mx[slot]) mx[slot] = v[c];
+                        }
+                    }
+                }
+        for (int k = 0; k < slots; ++k) {
+            out[(g * slots + k) * 2] = nan[k] ? -INFINITY : (float)mn[k];
+            out[(g * slots + k) * 2 + 1] = nan[k] ? INFINITY : (float)mx[k];
+        }
+    }
+    (void)n_threads;
+    return 0;
+}
+
 /* Test hook: apply a functor chain to one value of dimension dim (Sec. 3.3).
  * Returns 0, or -1 if the chain is invalid for that dimension. */
 int orc_chain_eval(const orc_chain *ch, const double *v_in, int32_t dim, double *out)

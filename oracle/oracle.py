@@ -90,6 +90,9 @@ def _load():
         lib.orc_opacity_grid.argtypes = [C.POINTER(_Source), C.POINTER(_Chain), C.c_void_p,
                                          C.c_void_p, C.c_int32, C.c_void_p, C.c_uint32,
                                          C.c_int32, C.c_void_p, C.c_int32]
+        lib.orc_range_grid.restype = C.c_int
+        lib.orc_range_grid.argtypes = [C.POINTER(_Source), C.c_int32, C.c_void_p, C.c_uint32,
+                                       C.c_int32, C.c_void_p, C.c_int32]
         lib.orc_lowp_copy.restype = C.c_int
         lib.orc_lowp_copy.argtypes = [C.POINTER(_Source), C.c_void_p, C.c_int32, C.c_void_p,
                                       C.c_void_p]
@@ -127,6 +130,35 @@ def classify(lut, x: float) -> np.ndarray:
     lut = np.ascontiguousarray(lut, np.float32).reshape(256, 4)
     out = np.zeros(4, np.float64)
     _load().orc_classify_eval(lut.ctypes.data, float(x), out.ctypes.data)
+    return out
+
+
+def range_grid(scene, cell: int = 16, threads: int = 0, mask=None) -> np.ndarray:
+    """Value-range grid of ``scene``'s active sources: shape (ceil(nz/cell),
+    ceil(ny/cell), ceil(nx/cell), slots, 2), float32 (min, max) per active
+    component in source order, over the same boxes as ``opacity_grid``."""
+    lib = _load()
+    n_src = len(scene.sources)
+    srcs = (_Source * n_src)()
+    keep = []
+    for s, src in enumerate(scene.sources):
+        data = np.ascontiguousarray(src.data, dtype=np.float32)
+        keep.append(data)
+        srcs[s].data = data.ctypes.data
+        srcs[s].offset = int(src.offset)
+        for a in range(3):
+            srcs[s].stride[a] = int(src.strides[a])
+        srcs[s].cstride = int(src.cstride)
+        srcs[s].fdim = int(src.fdim)
+        srcs[s].guard = int(src.guard)
+    m = int(scene.mask if mask is None else mask)
+    slots = sum(int(src.fdim) for s, src in enumerate(scene.sources) if (m >> s) & 1)
+    n = np.asarray(scene.n, np.int64)
+    G = [(int(k) + cell - 1) // cell for k in scene.n]
+    out = np.zeros((G[2], G[1], G[0], slots, 2), np.float32)
+    rc = lib.orc_range_grid(srcs, n_src, n.ctypes.data, m, int(cell), out.ctypes.data, int(threads))
+    if rc:
+        raise ValueError("oracle rejected the range-grid request")
     return out
 
 

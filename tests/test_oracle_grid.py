@@ -58,3 +58,51 @@ def test_grid_constant_and_empty():
     sc.luts = sc.luts.copy()
     sc.luts[..., 3] = 0.0
     assert np.all(oracle.opacity_grid(sc, 8) == 0.0)
+
+
+@pytest.mark.parametrize("cell", [3, 8])
+def test_range_grid_bruteforce(cell):
+    """Per macro cell and component, min and max over the apron box of the
+    cells as read (guards for the vector source, clamped border for the
+    scalar), written out with numpy slicing -- no oracle code."""
+    rng = np.random.default_rng(10 + cell)
+    n = (11, 7, 9)
+    g = 1
+    vec = rng.normal(0, 1, (n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g, 3)).astype(np.float32)
+    sca = rng.uniform(-3, 3, (n[2], n[1], n[0])).astype(np.float32)
+    sc = make_scene([vec], [[("length",)]], [const_lut((1, 1, 1, 0.1))], [1.0], n,
+                    ortho_down_z(n, 4, 4), 4, 4, guard=g)
+    sc.sources.append(synth.source_from_zyx(sca, 0))
+    sc.chains.append([])
+    sc.luts = np.stack([sc.luts[0], sc.luts[0]])
+    sc.weights = np.array([1.0, 1.0], np.float32)
+    got = oracle.range_grid(sc, cell)
+    zz, yy, xx = [np.arange(-1, k + 1) for k in n[::-1]]
+    V = vec[np.ix_(zz + g, yy + g, xx + g)]
+    S = sca[np.ix_(np.clip(zz, 0, n[2] - 1), np.clip(yy, 0, n[1] - 1), np.clip(xx, 0, n[0] - 1))]
+    comps = [V[..., 0], V[..., 1], V[..., 2], S]
+    G = [(k + cell - 1) // cell for k in n]
+    assert got.shape == (G[2], G[1], G[0], 4, 2)
+    for k in range(G[2]):
+        for j in range(G[1]):
+            for i in range(G[0]):
+                sl = (slice(k * cell, min((k + 1) * cell, n[2]) + 2),
+                      slice(j * cell, min((j + 1) * cell, n[1]) + 2),
+                      slice(i * cell, min((i + 1) * cell, n[0]) + 2))
+                for c, f in enumerate(comps):
+                    assert got[k, j, i, c, 0] == f[sl].min()
+                    assert got[k, j, i, c, 1] == f[sl].max()
+
+
+def test_range_grid_nan_and_mask():
+    n = (8, 8, 8)
+    f = np.zeros(n, np.float32)
+    f[2, 3, 4] = np.nan
+    sc = make_scene([f, np.ones(n, np.float32)], [[], []], [const_lut((1, 1, 1, 0.1))] * 2,
+                    [1.0, 1.0], n, ortho_down_z(n, 4, 4), 4, 4)
+    r = oracle.range_grid(sc, 4)
+    assert r.shape == (2, 2, 2, 2, 2)
+    assert np.isinf(r[0, 0, 1, 0]).all() and r[0, 0, 1, 0, 0] < 0 < r[0, 0, 1, 0, 1]
+    assert (r[1, 1, 0, 0] == 0).all()          # far from the NaN: a plain range
+    r1 = oracle.range_grid(sc, 4, mask=0b10)   # only the constant source
+    assert r1.shape == (2, 2, 2, 1, 2) and (r1 == 1).all()
