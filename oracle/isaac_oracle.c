@@ -513,6 +513,197 @@ static void orc_pixel(const orc_frame *F, int64_t pix, const orc_outputs *out, i
     }
 }
 
+/* ------------------------------------------------------- iso surfaces */
+
+/* Iso-surface rendering (Sec. 3 feature list; Sec. 4.2 shows such images).
+ * The paper states no algorithm; this is the reading both sides implement:
+ *
+ *   samples t_k = t0 + k*step exactly as in the volume mode (same sample grid,
+ *   same [t_in, t_out]); at each sample every active source s gives its chain
+ *   value v_s (interpolated as in the volume mode);
+ *   the surface is met at the first sample k where some v_s(k) >= iso[s];
+ *   for each such source the crossing is refined by one secant step between
+ *   k-1 and k: t = t_{k-1} + step*(iso - v(k-1)) / (v(k) - v(k-1)), or t = t_k
+ *   when k is the ray's first sample; the smallest t wins (ties: lower s);
+ *   at the hit point q the winning source's gradient is taken by central
+ *   differences g_a = (v(q + e_a) - v(q - e_a)) / 2 (same interpolation);
+ *   n = -g/|g| (n = -d if g = 0), turned towards the viewer (n.(-d) >= 0);
+ *   headlight Blinn-Phong with light, view and half vector all -d:
+ *   rgb = LUT_s(iso[s]).rgb * (1/4 + 3/4 * n.(-d)) + 1/4 * (n.(-d))^32,
+ *   clamped to [0, 1], alpha 1; a ray without a hit shows the background.
+ *
+ * margin[6] per pixel: entry and exit (steps, as in the volume mode), the
+ * smallest |v_s(k) - iso[s]| over the samples up to the hit (or all samples),
+ * |v(k) - v(k-1)| of the winning refinement (INF at a first-sample hit),
+ * |g|, and the hit distance t (-1 without a hit). */
+static double orc_source_value(const orc_frame *F, int s, const double pos[3])
+{
+    double v[4];
+    orc_sample(&F->src[s], F->p->n, pos, F->p->interp, v);
+    return orc_chain_apply(&F->ch[s], v, F->src[s].fdim);
+}
+
+static void orc_pixel_iso(const orc_frame *F, const double *iso, int64_t pix, double *rgba,
+                          uint8_t *rgba8, double *margin)
+{
+    const orc_params *p = F->p;
+    int64_t px = pix % p->width, py = pix / p->width;
+    double m_in = ORC_INF, m_out = ORC_INF, m_iso = ORC_INF, m_slope = ORC_INF, m_grad = ORC_INF;
+    double t_hit = -1.0;
+    double res[4] = {p->bg[0], p->bg[1], p->bg[2], p->bg[3]};
+
+    double xn = 2.0 * ((double)px + 0.5) / (double)p->width - 1.0;
+    double yn = 1.0 - 2.0 * ((double)py + 0.5) / (double)p->height;
+    double nw[3], fw[3], o[3], d[3];
+    orc_unproject(F->Minv, xn, yn, -1.0, nw);
+    orc_unproject(F->Minv, xn, yn, 1.0, fw);
+    for (int a = 0; a < 3; ++a) {
+        o[a] = nw[a] + 0.5 * (double)p->gn[a];
+        d[a] = fw[a] - nw[a];
+    }
+    double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] /= len;
+    int miss = 0;
+    double t0 = 0.0, tg1 = ORC_INF, tl0 = 0.0, t_out = ORC_INF;
+    for (int a = 0; a < 3; ++a) {
+        double g_lo = 0.0, g_hi = (double)p->gn[a];
+        double l_lo = (double)p->off[a], l_hi = (double)(p->off[a] + p->n[a]);
+        if (d[a] != 0.0) {
+            double ta = (g_lo - o[a]) / d[a], tb = (g_hi - o[a]) / d[a];
+            double lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+            if (lo > t0) t0 = lo;
+            if (hi < tg1) tg1 = hi;
+            ta = (l_lo - o[a]) / d[a];
+            tb = (l_hi - o[a]) / d[a];
+            lo = ta < tb ? ta : tb;
+            hi = ta < tb ? tb : ta;
+            if (lo > tl0) tl0 = lo;
+            if (hi < t_out) t_out = hi;
+        } else if (o[a] < l_lo || o[a] >= l_hi) {
+            miss = 1;
+        }
+    }
+    if (t0 >= tg1) miss = 1;
+    double t_in = tl0 > t0 ? tl0 : t0;
+    for (int i = 0; i < p->n_clip && !miss; ++i) {
+        const double *pl = p->clip[i];
+        double sd = pl[0] * o[0] + pl[1] * o[1] + pl[2] * o[2] + pl[3];
+        double r = pl[0] * d[0] + pl[1] * d[1] + pl[2] * d[2];
+        if (r > 0.0) {
+            double tc = -sd / r;
+            if (tc > t_in) t_in = tc;
+        } else if (r < 0.0) {
+            double tc = -sd / r;
+            if (tc < t_out) t_out = tc;
+        } else if (sd < 0.0) {
+            miss = 1;
+        }
+    }
+    int raised = t_in > t0;
+    double ol[3] = {o[0] - (double)p->off[0], o[1] - (double)p->off[1], o[2] - (double)p->off[2]};
+    if (!miss && t_in < t_out) {
+        double ein = (t_in - t0) / p->step, eout = (t_out - t0) / p->step;
+        int64_t kf = raised ? (int64_t)ceil(ein) : 0;
+        int64_t ke = (int64_t)ceil(eout);
+        if (raised) m_in = orc_dist_int(ein);
+        m_out = orc_dist_int(eout);
+        double prev[ORC_MAX_SRC];
+        int win = -1;
+        for (int64_t k = kf; k < ke && win < 0; ++k) {
+            double t = t0 + (double)k * p->step;
+            double pos[3] = {ol[0] + t * d[0], ol[1] + t * d[1], ol[2] + t * d[2]};
+            double best = ORC_INF;
+            for (int s = 0; s < F->n_src; ++s) {
+                if (!((p->active_mask >> s) & 1u)) continue;
+                double v = orc_source_value(F, s, pos);
+                double m = fabs(v - iso[s]);
+                if (m < m_iso) m_iso = m;
+                if (v >= iso[s]) {
+                    double th = t, slope = ORC_INF;
+                    if (k > kf) {
+                        slope = v - prev[s];
+                        th = t - p->step + p->step * (iso[s] - prev[s]) / slope;
+                    }
+                    if (th < best) {
+                        best = th;
+                        win = s;
+                        m_slope = fabs(slope);
+                    }
+                }
+                prev[s] = v;
+            }
+            if (win >= 0) t_hit = best;
+        }
+        if (win >= 0) {
+            double q[3] = {ol[0] + t_hit * d[0], ol[1] + t_hit * d[1], ol[2] + t_hit * d[2]};
+            double g[3];
+            for (int a = 0; a < 3; ++a) {
+                double qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
+                qp[a] += 1.0;
+                qm[a] -= 1.0;
+                g[a] = 0.5 * (orc_source_value(F, win, qp) - orc_source_value(F, win, qm));
+            }
+            double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            m_grad = gl;
+            double nrm[3];
+            for (int a = 0; a < 3; ++a) nrm[a] = gl > 0.0 ? -g[a] / gl : -d[a];
+            double ndl = -(nrm[0] * d[0] + nrm[1] * d[1] + nrm[2] * d[2]);
+            if (ndl < 0.0) ndl = -ndl;
+            double spec = pow(ndl, 32.0);
+            double col[4];
+            orc_classify(F->luts + (size_t)win * 256 * 4, iso[win], col);
+            for (int c = 0; c < 3; ++c) {
+                double x = col[c] * (0.25 + 0.75 * ndl) + 0.25 * spec;
+                res[c] = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+            }
+            res[3] = 1.0;
+        }
+    }
+    memcpy(rgba, res, sizeof res);
+    for (int c = 0; c < 4; ++c) rgba8[c] = orc_quant8(res[c]);
+    margin[0] = m_in;
+    margin[1] = m_out;
+    margin[2] = m_iso;
+    margin[3] = m_slope;
+    margin[4] = m_grad;
+    margin[5] = t_hit;
+}
+
+int orc_render_iso(const orc_params *p, const orc_source *src, const orc_chain *ch,
+                   const float *luts, const double *iso, int32_t n_src, double *rgba,
+                   uint8_t *rgba8, double *margin, int32_t n_threads)
+{
+    if (!p || !src || !ch || !luts || !iso || !rgba || !rgba8 || !margin) return -1;
+    if (n_src < 1 || n_src > ORC_MAX_SRC || p->width < 1 || p->height < 1 || !(p->step > 0.0))
+        return -1;
+    if (p->n_clip < 0 || p->n_clip > ORC_MAX_CLIP) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (p->n[a] < 1 || p->off[a] < 0 || p->off[a] + p->n[a] > p->gn[a]) return -1;
+    for (int s = 0; s < n_src; ++s)
+        if (((p->active_mask >> s) & 1u) &&
+            (src[s].fdim < 1 || src[s].fdim > 4 || orc_chain_check(&ch[s], src[s].fdim)))
+            return -1;
+    orc_frame F;
+    F.p = p;
+    F.src = src;
+    F.ch = ch;
+    F.luts = luts;
+    F.w = NULL;
+    F.n_src = n_src;
+    double M[16];
+    orc_matmul4(p->projection, p->modelview, M);
+    if (orc_invert4(M, F.Minv)) return -1;
+    int64_t count = (int64_t)p->width * p->height;
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(n_threads)
+#endif
+    for (int64_t i = 0; i < count; ++i)
+        orc_pixel_iso(&F, iso, i, rgba + i * 4, rgba8 + i * 4, margin + i * 6);
+    (void)n_threads;
+    return 0;
+}
+
 /* Render the listed pixels (row-major index y*width + x; NULL = all pixels
  * in order) of one frame.  Output slot i belongs to the i-th listed pixel.
  * Returns 0, or -1 on invalid arguments. */

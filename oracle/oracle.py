@@ -93,6 +93,10 @@ def _load():
         lib.orc_range_grid.restype = C.c_int
         lib.orc_range_grid.argtypes = [C.POINTER(_Source), C.c_int32, C.c_void_p, C.c_uint32,
                                        C.c_int32, C.c_void_p, C.c_int32]
+        lib.orc_render_iso.restype = C.c_int
+        lib.orc_render_iso.argtypes = [C.POINTER(_Params), C.POINTER(_Source), C.POINTER(_Chain),
+                                       C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int32]
         lib.orc_lowp_copy.restype = C.c_int
         lib.orc_lowp_copy.argtypes = [C.POINTER(_Source), C.c_void_p, C.c_int32, C.c_void_p,
                                       C.c_void_p]
@@ -247,6 +251,68 @@ def _chain(spec, fdim: int) -> _Chain:
         for j, a in enumerate(args[:4]):
             ch.ops[i].arg[j] = float(a)
     return ch
+
+
+def _frame_args(scene, mask=None):
+    """(params, sources, chains, luts, keepalive) of ``scene`` for the C side."""
+    n_src = len(scene.sources)
+    P = _Params()
+    for a in range(3):
+        P.n[a] = int(scene.n[a])
+        P.gn[a] = int(scene.gn[a])
+        P.off[a] = int(scene.off[a])
+    for i in range(16):
+        P.modelview[i] = float(scene.modelview[i])
+        P.projection[i] = float(scene.projection[i])
+    P.width, P.height = int(scene.width), int(scene.height)
+    if len(scene.clip) > MAX_CLIP:
+        raise ValueError("too many clip planes for the oracle")
+    P.n_clip = len(scene.clip)
+    for i, pl in enumerate(scene.clip):
+        for j in range(4):
+            P.clip[i][j] = float(pl[j])
+    P.step = float(scene.step)
+    P.interp = int(scene.interp)
+    P.term = float(scene.term)
+    for j in range(4):
+        P.bg[j] = float(scene.bg[j])
+    P.active_mask = int(scene.mask if mask is None else mask)
+    srcs = (_Source * n_src)()
+    chains = (_Chain * n_src)()
+    keep = []
+    for s, src in enumerate(scene.sources):
+        data = np.ascontiguousarray(src.data, dtype=np.float32)
+        keep.append(data)
+        srcs[s].data = data.ctypes.data
+        srcs[s].offset = int(src.offset)
+        for a in range(3):
+            srcs[s].stride[a] = int(src.strides[a])
+        srcs[s].cstride = int(src.cstride)
+        srcs[s].fdim = int(src.fdim)
+        srcs[s].guard = int(src.guard)
+        chains[s] = _chain(scene.chains[s], src.fdim)
+    luts = np.ascontiguousarray(scene.luts, dtype=np.float32).reshape(n_src, 256, 4)
+    return P, srcs, chains, luts, keep
+
+
+def render_iso(scene, iso, threads: int = 0, mask=None) -> dict:
+    """Iso-surface frame of ``scene`` in FP64 (the reading stated at
+    orc_render_iso): ``iso`` holds one threshold per source.  Returns ``rgba``
+    (float64, (H, W, 4)), ``rgba8`` (uint8) and ``margin`` (float64,
+    (H, W, 6): entry, exit, |v - iso|, refinement slope, |gradient|, t_hit)."""
+    lib = _load()
+    P, srcs, chains, luts, keep = _frame_args(scene, mask)
+    n_src = len(scene.sources)
+    iso = np.ascontiguousarray(iso, dtype=np.float64).reshape(n_src)
+    H, W = int(scene.height), int(scene.width)
+    rgba = np.zeros((H, W, 4), np.float64)
+    rgba8 = np.zeros((H, W, 4), np.uint8)
+    margin = np.zeros((H, W, 6), np.float64)
+    rc = lib.orc_render_iso(C.byref(P), srcs, chains, luts.ctypes.data, iso.ctypes.data, n_src,
+                            rgba.ctypes.data, rgba8.ctypes.data, margin.ctypes.data, int(threads))
+    if rc:
+        raise ValueError("oracle rejected the iso-surface frame")
+    return {"rgba": rgba, "rgba8": rgba8, "margin": margin}
 
 
 def render(scene, pixels=None, threads: int = 0, mask=None) -> dict:
