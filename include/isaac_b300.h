@@ -239,6 +239,61 @@ int isaac_opacity_grid(const isaac_source *sources, const isaac_chain *chains, i
                        int32_t cell, float *grid, int64_t grid_len, void *stream);
 
 /*
+ * Classical empty-space skipping (no counterpart in the paper, which skips
+ * only deactivated sources, Sec. 3.2).
+ *
+ * isaac_range_grid -- per macro cell of `cell`^3 cells (the boxes of
+ * isaac_opacity_grid, i.e. with the one-cell trilinear apron) and per
+ * component of each active source, the smallest and largest value read from
+ * the box's cells ([-inf, +inf] if any is NaN).  ranges: device floats,
+ * ceil(n/cell)^3 cells x (sum of the active sources' f_dim) x 2, layout
+ * [cell (x fastest)][component, active sources in order][min, max].  It
+ * depends on the data only: recompute it when the fields change, not when
+ * the transfer functions or chains do.  cell: 2..1024.
+ */
+int isaac_range_grid(const isaac_source *sources, int32_t n_sources, const isaac_render_opts *opts,
+                     int32_t cell, float *ranges, int64_t ranges_len, void *stream);
+
+/*
+ * isaac_render_skip -- isaac_render (same arguments, same image bit for bit)
+ * that jumps over macro cells where no sample can be visible: from `ranges`
+ * (isaac_range_grid of the same sources, n, cell and active_mask) it bounds,
+ * with outward-rounded interval arithmetic, each source's chain result over
+ * the cell and the LUT opacity over the entries that result can reach; a
+ * cell where every source with weight > 0 gets opacity exactly 0 (and every
+ * reachable LUT entry is finite) is skipped along each ray.  Those samples
+ * would composite nothing, so only the nsamples output differs: it counts
+ * the samples actually evaluated.
+ */
+int isaac_render_skip(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                      const float *luts, const float *weights, const isaac_camera *camera,
+                      const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
+                      const isaac_framebuffer *fb, const float *ranges, int64_t ranges_len,
+                      int32_t cell, void *stream);
+
+/*
+ * isaac_render_iso -- iso-surface rendering (Sec. 3 feature list; the
+ * renderings of Sec. 4.2).  The paper gives no algorithm; this call
+ * implements one reading:
+ *   the samples of isaac_render (same grid, same [t_in, t_out]); at each,
+ *   every active source's chain value v_s; the surface is met at the first
+ *   sample where some v_s >= iso_values[s]; each crossing source refines the
+ *   crossing by one secant step towards the previous sample (none at the
+ *   ray's first sample), the nearest crossing wins (ties: lower source);
+ *   the normal is that source's central-difference gradient (one voxel,
+ *   same interpolation), turned towards the viewer; with a headlight,
+ *   rgb = LUT_s(iso_values[s]).rgb * (1/4 + 3/4 * n.v) + 1/4 * (n.v)^32,
+ *   clamped to [0, 1], alpha 1.  Rays without a crossing show the background.
+ * iso_values: host, n_sources floats (finite for active sources).  The
+ * other arguments as for isaac_render (weights are not used); nsamples, if
+ * given, counts the samples evaluated.
+ */
+int isaac_render_iso(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
+                     const float *luts, const float *iso_values, const isaac_camera *camera,
+                     const isaac_plane *clip, int32_t n_clip, const isaac_render_opts *opts,
+                     const isaac_framebuffer *fb, void *stream);
+
+/*
  * isaac_render_noalloc -- the frame of isaac_render (same arguments, same
  * kernels, same image) for callers that must not allocate device memory.
  * The paper has no counterpart.  isaac_render allocates its per-stream ray

@@ -49,11 +49,16 @@ int choose_lanes(long long rect_pixels, int hint, int corner_bytes = 0);
 // overrides it, 1 = one chunk per atomic.  Scheduling only: the image does not
 // depend on it.
 int march_grab();
-// Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays.
-int bind_workspace(KParams &p, cudaStream_t st);
+// Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays /
+// p.longs; `extra` more bytes after them, returned in *extra_ptr.
+int bind_workspace(KParams &p, cudaStream_t st, size_t extra = 0, void **extra_ptr = nullptr);
+// Empty-space flags of the macro cells (one byte each) from a value-range grid.
+int launch_empty_flags(const KParams &p, int nact, const float *ranges, int slots, long long cells,
+                       unsigned char *flags, cudaStream_t st);
 // Background + ray setup + optional hook + march kernel `fn` (null: background
-// only).  long_list: a hook may fill the long-ray list (not in label mode).
+// only).  fn_long: the long-ray march of the same sources; with a hook and
+// fn_long the hook may fill the long-ray list, which fn_long marches before fn.
 int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook,
-                      bool long_list = true);
+                      FrameLaunch fn_long = nullptr);
 
 }  // namespace isaac

@@ -420,12 +420,17 @@ struct PackedShader {
     }
 };
 
-template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL>
+// LONG: the long-ray march (MODE_LONG of k_raycast) instead of the march.
+template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL, bool LONG = false>
 __global__ void __launch_bounds__(128, 8) k_raycast_packed(const __grid_constant__ KParams p)
 {
     __shared__ float4 s_lut[NACT * 256];
     load_luts<NACT>(p, s_lut);
-    march<NACT, PackedShader<NACT, SIG, DT, PAD, INTERP>, RL>(p, s_lut);
+    using Shader = PackedShader<NACT, SIG, DT, PAD, INTERP>;
+    if constexpr (LONG)
+        march_long<Shader>(p, s_lut);
+    else
+        march<NACT, Shader, RL>(p, s_lut);
 }
 
 // ------------------------------------------------------------- dispatch
@@ -443,6 +448,7 @@ struct PackedEntry {
     int pad;
     int interp;
     int rl;
+    bool longpass;       // the long-ray march
     PackedLaunch fn;
 };
 

@@ -215,7 +215,7 @@ static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains
     p.bx = (int)((vol->n[0] + 9) / 8);
     p.by = (int)((vol->n[1] + 9) / 8);
 
-    PackedLaunch fn = nullptr;
+    PackedLaunch fn = nullptr, fn_long = nullptr;
     int rl = 1;
     if (opts->active_mask != 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
@@ -226,7 +226,7 @@ static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains
         for (int i = 0; i < T->n_entries; ++i) {
             const PackedEntry &e = T->entries[i];
             if (e.nact != vol->n_src || e.interp != opts->interp || e.pad != vol->pad) continue;
-            if (e.sig != (spec ? sig : 0u)) continue;
+            if (e.sig != (spec ? sig : 0u) || e.longpass) continue;
             if (!best || e.rl == want ||
                 (best->rl != want && std::abs(e.rl - want) < std::abs(best->rl - want)))
                 best = &e;
@@ -234,12 +234,19 @@ static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains
         if (!best) return fail(ISAAC_ENOTSUP, "no packed kernel for this layout");
         fn = best->fn;
         rl = best->rl;
+        if (proposal)
+            for (int i = 0; i < T->n_entries; ++i) {
+                const PackedEntry &e = T->entries[i];
+                if (e.longpass && e.nact == vol->n_src && e.interp == opts->interp &&
+                    e.pad == vol->pad && e.sig == (spec ? sig : 0u))
+                    fn_long = e.fn;
+            }
     }
     if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered for packed copies");
     FrameHook hook;
     rc = proposal_hook(proposal, opts, &hook);
     if (rc) return rc;
-    return launch_frame_with(p, fn, rl, (cudaStream_t)stream, proposal ? &hook : nullptr);
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream, proposal ? &hook : nullptr, fn_long);
 }
 
 extern "C" int isaac_render_packed(const isaac_packed *vol, const isaac_chain *chains,

@@ -85,9 +85,17 @@ struct WsCounters {
 constexpr int kLongRay = -2;
 // A proposal puts a ray in the long-ray list when it keeps more samples than this.
 constexpr int kLongRaySamples = 96;
+// Lanes per ray and samples per lane and step on the long-ray list.  A long
+// ray's time is its chain of dependent gathers (about one DRAM latency per
+// step), so a whole warp takes the ray and each lane gathers 4 samples per
+// step: 128 samples' loads in flight per step.
+constexpr int kLongRayLanes = 32;
+constexpr int kLongRaySteps = 4;
 
-// March modes: plain, footprint bitmap, visible-span labels.
-enum : int { MODE_PLAIN = 0, MODE_TOUCH = 1, MODE_LABEL = 2 };
+// March modes: plain (skipping rays on the long-ray list), footprint bitmap,
+// visible-span labels, the long-ray list alone, plain with empty-space
+// skipping over the macro cells that KParams::empty marks, iso surfaces.
+enum : int { MODE_PLAIN = 0, MODE_TOUCH = 1, MODE_LABEL = 2, MODE_LONG = 3, MODE_SKIP = 4, MODE_ISO = 5 };
 
 struct KParams {
     double minv[16];                 // inverse of projection * modelview, column-major
@@ -106,6 +114,11 @@ struct KParams {
     int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
     int max_steps;                   // samples on the longest chord of the local box
     int grab;                        // march: most chunks of 32/RL rays a warp takes per atomic
+    // empty-space skipping: one byte per macro cell of skip_cell^3 cells
+    // (1 = every sample whose position lies in it has opacity 0)
+    const unsigned char *empty;
+    int skip_cell, sgx, sgy, sgz;
+    float iso[ISAAC_MAX_ACTIVE];     // iso-surface mode: threshold of each active source
     KSource src[ISAAC_MAX_ACTIVE];
     KChain ch[ISAAC_MAX_ACTIVE];
     const float4 *lut[ISAAC_MAX_ACTIVE];
@@ -194,6 +207,110 @@ __device__ __forceinline__ float run_chain(const KChain &ch, float v[4])
         }
     }
     return v[0];
+}
+
+// Interval form of run_chain: given, per component, an interval [lo, hi]
+// that holds the value, an interval that holds the chain's result as run_chain
+// computes it in FP32.  Sums, products, FMAs and square roots round outward
+// (directed rounding); pow and log, which have no directed forms, are widened
+// by 10^-6 relative (many ulps of their error).  A NaN anywhere widens the
+// result to everything.
+__device__ __forceinline__ void chain_interval(const KChain &ch, float lo[4], float hi[4])
+{
+    const float inf = __int_as_float(0x7f800000);
+    for (int i = 0; i < ch.n; ++i) {
+        const KOp &o = ch.op[i];
+        const int d = o.dim;
+        switch (o.code) {
+        case K_AFFINE:
+            for (int c = 0; c < 4; ++c) {
+                const float a = o.a[c], b = o.b[c];
+                const float l = a >= 0.0f ? __fmaf_rd(a, lo[c], b) : __fmaf_rd(a, hi[c], b);
+                const float h = a >= 0.0f ? __fmaf_ru(a, hi[c], b) : __fmaf_ru(a, lo[c], b);
+                lo[c] = l;
+                hi[c] = h;
+            }
+            break;
+        case K_ADD:
+            for (int c = 0; c < 4; ++c) {
+                lo[c] = __fadd_rd(lo[c], o.a[c]);
+                hi[c] = __fadd_ru(hi[c], o.a[c]);
+            }
+            break;
+        case K_MUL:
+            for (int c = 0; c < 4; ++c) {
+                const float a = o.a[c];
+                const float l = a >= 0.0f ? __fmul_rd(lo[c], a) : __fmul_rd(hi[c], a);
+                const float h = a >= 0.0f ? __fmul_ru(hi[c], a) : __fmul_ru(lo[c], a);
+                lo[c] = l;
+                hi[c] = h;
+            }
+            break;
+        case K_LENGTH:
+        case K_SUM: {
+            float sl = 0.0f, sh = 0.0f;
+            for (int c = 0; c < 4; ++c) {
+                if (c >= d) break;
+                float ql = lo[c], qh = hi[c];
+                if (o.code == K_LENGTH) {   // the square's interval
+                    const float m = fmaxf(fabsf(lo[c]), fabsf(hi[c]));
+                    const float n = (lo[c] > 0.0f) ? lo[c] : (hi[c] < 0.0f ? -hi[c] : 0.0f);
+                    ql = __fmul_rd(n, n);
+                    qh = __fmul_ru(m, m);
+                }
+                sl = __fadd_rd(sl, ql);
+                sh = __fadd_ru(sh, qh);
+            }
+            if (o.code == K_LENGTH) {
+                sl = __fsqrt_rd(fmaxf(sl, 0.0f));
+                sh = __fsqrt_ru(sh);
+            }
+            lo[0] = sl;
+            hi[0] = sh;
+        } break;
+        case K_SQRT:
+            for (int c = 0; c < 4; ++c)
+                if (c < d) {
+                    lo[c] = lo[c] > 0.0f ? __fsqrt_rd(lo[c]) : 0.0f;
+                    hi[c] = hi[c] > 0.0f ? __fsqrt_ru(hi[c]) : 0.0f;
+                }
+            break;
+        case K_POW:
+            for (int c = 0; c < 4; ++c)
+                if (c < d) {
+                    const float a = o.a[c];
+                    float l, h;
+                    if (hi[c] <= 0.0f) {
+                        l = h = 0.0f;
+                    } else {
+                        const float pl = lo[c] > 0.0f ? powf(lo[c], a) : (a > 0.0f ? 0.0f : (a < 0.0f ? inf : 1.0f));
+                        const float ph = powf(hi[c], a);
+                        l = fminf(pl, ph);
+                        h = fmaxf(pl, ph);
+                        if (lo[c] <= 0.0f) l = 0.0f;            // v <= 0 gives 0
+                        l = l - fabsf(l) * 1e-6f;
+                        h = h + fabsf(h) * 1e-6f;
+                    }
+                    lo[c] = l;
+                    hi[c] = h;
+                }
+            break;
+        case K_LOG:
+            for (int c = 0; c < 4; ++c)
+                if (c < d) {
+                    const float l = logf(fmaxf(lo[c], 1e-30f)), h = logf(fmaxf(hi[c], 1e-30f));
+                    lo[c] = l - (fabsf(l) + 1.0f) * 1e-6f;
+                    hi[c] = h + (fabsf(h) + 1.0f) * 1e-6f;
+                }
+            break;
+        default:
+            break;
+        }
+    }
+    if (!(lo[0] == lo[0]) || !(hi[0] == hi[0])) {
+        lo[0] = -inf;
+        hi[0] = inf;
+    }
 }
 
 // Transfer function: clamp to [0,1], entries at j/255, linear in between.
@@ -500,25 +617,59 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
 // group evaluate samples k+0 .. k+RL-1 together; every lane then composites
 // the group's RL samples in order, stopping at the termination sample, so all
 // lanes hold the same C and A.
-template <class Shader, int RL, bool LABEL>
+// S > 1 (long rays): each lane evaluates S samples per step, k + s*RL + sub
+// for s < S, so that a step has RL*S samples' gathers in flight at once; they
+// are composited in sample order like the rest.
+template <class Shader, int RL, bool LABEL, bool SKIP_LONG = false, bool SKIP_EMPTY = false, int S = 1>
 __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut, unsigned idx,
                                           int lane)
 {
     const int sub = lane & (RL - 1);
     const RayRec r = p.rays[idx];
-    if (RL < 32 && p.longs && r.jf == kLongRay) return;   // marched by a whole warp
+    if (SKIP_LONG && p.longs && r.jf == kLongRay) return;   // marched from the long-ray list
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     int ns = 0, jf = -1, jl = -1;
     const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
-    for (int k = r.kbeg; k < r.nsteps; k += RL) {
-        const int kk = k + sub;
-        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (kk < r.nsteps) {
-            const float s = (float)kk * p.step;
-            c = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey), fmaf(s, r.dz, r.ez));
+    for (int k = r.kbeg; k < r.nsteps; k += RL * S) {
+        if (SKIP_EMPTY) {
+            // The macro cell that owns sample k's position: if it is marked
+            // empty, jump to the first sample at or past the ray's exit from its
+            // box [m*c, (m+1)*c) per axis.  Every skipped sample lies in that box
+            // (up to FP32 rounding, far inside the one-cell apron the marking
+            // covers), so it has opacity 0 and compositing it changes nothing.
+            const float s0 = (float)k * p.step;
+            const float x = fmaf(s0, r.dx, r.ex), y = fmaf(s0, r.dy, r.ey), z = fmaf(s0, r.dz, r.ez);
+            const float cz = (float)p.skip_cell;
+            const int mx = min(max((int)floorf(x / cz), 0), p.sgx - 1);
+            const int my = min(max((int)floorf(y / cz), 0), p.sgy - 1);
+            const int mz = min(max((int)floorf(z / cz), 0), p.sgz - 1);
+            if (p.empty[((long long)mz * p.sgy + my) * p.sgx + mx]) {
+                const float inf = __int_as_float(0x7f800000);
+                const float ex = r.dx > 0.0f ? ((float)(mx + 1) * cz - x) / r.dx
+                               : (r.dx < 0.0f ? ((float)mx * cz - x) / r.dx : inf);
+                const float ey = r.dy > 0.0f ? ((float)(my + 1) * cz - y) / r.dy
+                               : (r.dy < 0.0f ? ((float)my * cz - y) / r.dy : inf);
+                const float ez = r.dz > 0.0f ? ((float)(mz + 1) * cz - z) / r.dz
+                               : (r.dz < 0.0f ? ((float)mz * cz - z) / r.dz : inf);
+                const float se = fminf(ex, fminf(ey, ez));
+                const int jump = se > 0.0f ? (int)fminf(ceilf(se / p.step), 1.0e9f) : 1;
+                k += max(jump, 1) - RL * S;   // the loop adds RL * S
+                continue;
+            }
+        }
+        float4 cs[S];
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const int kk = k + q * RL + sub;
+            cs[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (kk < r.nsteps) {
+                const float s = (float)kk * p.step;
+                cs[q] = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey),
+                                      fmaf(s, r.dz, r.ez));
+            }
         }
         bool done = false;
-        auto composite = [&](int j) {
+        auto composite = [&](const float4 &c, int kq, int j) {
             float4 cj = c;
             if (RL > 1) {
                 cj.x = __shfl_sync(gmask, c.x, j, RL);
@@ -526,11 +677,11 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
                 cj.z = __shfl_sync(gmask, c.z, j, RL);
                 cj.w = __shfl_sync(gmask, c.w, j, RL);
             }
-            if (!done && k + j < r.nsteps) {
+            if (!done && kq + j < r.nsteps) {
                 const float a = clamp01(cj.w);
                 if (LABEL && a > 0.0f) {
-                    if (jf < 0) jf = k + j;
-                    jl = k + j;
+                    if (jf < 0) jf = kq + j;
+                    jl = kq + j;
                 }
                 const float t = (1.0f - A) * a;
                 C0 = fmaf(t, cj.x, C0);
@@ -541,12 +692,15 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
                 done = A >= p.term;
             }
         };
-        if constexpr (RL <= 8) {
 #pragma unroll
-            for (int j = 0; j < RL; ++j) composite(j);
-        } else {   // whole-warp rays: a partly rolled loop keeps the register count down
+        for (int q = 0; q < S; ++q) {
+            if constexpr (RL <= 8) {
+#pragma unroll
+                for (int j = 0; j < RL; ++j) composite(cs[q], k + q * RL, j);
+            } else {   // wide groups: a partly rolled loop keeps the register count down
 #pragma unroll 4
-            for (int j = 0; j < RL; ++j) composite(j);
+                for (int j = 0; j < RL; ++j) composite(cs[q], k + q * RL, j);
+            }
         }
         if (done) break;
     }
@@ -563,33 +717,13 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
 // rays from the list, as many per atomic as 1/(2W) of what was left at its
 // previous take (W warps in the grid; at most p.grab, at least one), so that
 // long lists need few atomics on the one shared counter while the last
-// chunks stay small enough to balance the warps.
-//
-// With a long-ray list (rays an interval proposal left long among mostly
-// short ones), warps first take its rays one at a time with all 32 lanes, so
-// that the few long rays do not leave a tail of sequential gathers; the
-// short-ray pass then skips them.  The lane count never changes a pixel.
-template <class Shader>
-__device__ __noinline__ void march_long_rays(const KParams &p, const float4 *s_lut)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned n_long = *(volatile unsigned *)&p.ctr->n_long;
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(&p.ctr->next_long, 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if (i >= n_long) break;
-        march_ray<Shader, 32, false>(p, s_lut, p.longs[i], lane);
-    }
-}
-
-template <int NACT, class Shader, int RL, bool LABEL = false>
+// chunks stay small enough to balance the warps.  Rays on the long-ray list
+// are skipped: the long-ray march has taken them.
+template <int NACT, class Shader, int RL, bool LABEL = false, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
 {
     constexpr unsigned RAYS = 32 / RL;
     const int lane = threadIdx.x & 31;
-    // (a separate function, so that its registers do not add to the short pass's)
-    if (!LABEL && RL < 32 && p.longs) march_long_rays<Shader>(p, s_lut);
     const unsigned n_rays = *(volatile unsigned *)&p.ctr->n_rays;
     const unsigned cap = (unsigned)max(p.grab, 1);
     const unsigned per_take = RAYS * 2u * gridDim.x * (blockDim.x >> 5);
@@ -604,8 +738,159 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
         for (unsigned c = 0; c < grab; ++c) {
             const unsigned idx = first + c * RAYS + (unsigned)(lane / RL);
             if (first + c * RAYS >= n_rays) break;
-            if (idx < n_rays) march_ray<Shader, RL, LABEL>(p, s_lut, idx, lane);
+            if (idx < n_rays) march_ray<Shader, RL, LABEL, !LABEL, SKIP_EMPTY>(p, s_lut, idx, lane);
         }
+    }
+}
+
+// The long-ray march: the rays an interval proposal left long (a few among
+// many short ones), kLongRayLanes lanes per ray and kLongRaySteps samples per
+// lane and step, launched before the march of the rest.
+template <class Shader>
+__device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut)
+{
+    constexpr unsigned RAYS = 32 / kLongRayLanes;
+    const int lane = threadIdx.x & 31;
+    const unsigned n_long = *(volatile unsigned *)&p.ctr->n_long;
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(&p.ctr->next_long, RAYS);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n_long) break;
+        const unsigned k = i + (unsigned)(lane / kLongRayLanes);
+        if (k < n_long) march_ray<Shader, kLongRayLanes, false, false, false, kLongRaySteps>(p, s_lut, p.longs[k], lane);
+    }
+}
+
+// ---------------------------------------------------------- iso surfaces
+
+// Chain value of active source I at a sample.
+template <int I, unsigned SIG, int INTERP, typename Idx>
+__device__ __forceinline__ float source_value(const KParams &p, const Geo &g)
+{
+    float v[4];
+    fetch_source<I, SIG, INTERP, Idx>(p, g, v);
+    return run_chain(p.ch[I], v);
+}
+
+template <unsigned SIG, int INTERP, typename Idx, int... Is>
+__device__ __forceinline__ void source_values(const KParams &p, const Geo &g, float *v,
+                                              std::integer_sequence<int, Is...>)
+{
+    ((v[Is] = source_value<Is, SIG, INTERP, Idx>(p, g)), ...);
+}
+
+// Chain value of active source `which` (a run-time index) at a position.
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int I = 0>
+__device__ __forceinline__ float value_of(const KParams &p, int which, float x, float y, float z)
+{
+    if constexpr (I + 1 < NACT) {
+        if (which != I) return value_of<NACT, SIG, INTERP, Idx, I + 1>(p, which, x, y, z);
+    }
+    return source_value<I, SIG, INTERP, Idx>(p, sample_geo<INTERP>(x, y, z));
+}
+
+// One ray in iso-surface mode (the reading: samples on the same grid as the
+// volume mode; the surface is met at the first sample where some active
+// source's chain value reaches its threshold; each crossing source refines
+// the crossing by one secant step towards the previous sample, the nearest
+// wins (ties: lower source); the normal is the winning source's central-
+// difference gradient (one voxel), turned towards the viewer; headlight
+// Blinn-Phong: rgb = LUT(iso).rgb * (1/4 + 3/4 n.v) + 1/4 (n.v)^32, alpha 1).
+// The RL lanes of a group evaluate consecutive samples; a ballot finds the
+// first one that crosses.
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL>
+__device__ __forceinline__ void iso_ray(const KParams &p, unsigned idx, int lane)
+{
+    const int sub = lane & (RL - 1);
+    const int base = lane & ~(RL - 1);
+    const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << base);
+    const RayRec r = p.rays[idx];
+    float prev[NACT];
+#pragma unroll
+    for (int i = 0; i < NACT; ++i) prev[i] = 0.0f;
+    int win = -1, ns = 0;
+    float s_hit = 0.0f;
+    for (int k = r.kbeg; k < r.nsteps; k += RL) {
+        const int kk = k + sub;
+        float v[NACT];
+        bool cross = false;
+#pragma unroll
+        for (int i = 0; i < NACT; ++i) v[i] = -__int_as_float(0x7f800000);
+        if (kk < r.nsteps) {
+            const float s = (float)kk * p.step;
+            const Geo g = sample_geo<INTERP>(fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey), fmaf(s, r.dz, r.ez));
+            source_values<SIG, INTERP, Idx>(p, g, v, std::make_integer_sequence<int, NACT>{});
+#pragma unroll
+            for (int i = 0; i < NACT; ++i) cross |= v[i] >= p.iso[i];
+        }
+        const unsigned m = (__ballot_sync(gmask, cross) >> base) & (RL == 32 ? 0xffffffffu : ((1u << RL) - 1u));
+        if (m) {
+            const int j = __ffs(m) - 1;
+            const int kj = k + j;
+            const float sj = (float)kj * p.step;
+            float best = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int i = 0; i < NACT; ++i) {
+                const float vj = __shfl_sync(gmask, v[i], j, RL);
+                const float vq = __shfl_sync(gmask, v[i], j > 0 ? j - 1 : 0, RL);
+                const float vp = j > 0 ? vq : prev[i];
+                if (vj >= p.iso[i]) {
+                    const float th = kj == r.kbeg ? sj
+                                   : (sj - p.step) + p.step * (p.iso[i] - vp) / (vj - vp);
+                    if (th < best) {
+                        best = th;
+                        win = i;
+                    }
+                }
+            }
+            s_hit = best;
+            ns += j + 1;
+            break;
+        }
+#pragma unroll
+        for (int i = 0; i < NACT; ++i) prev[i] = __shfl_sync(gmask, v[i], RL - 1, RL);
+        ns += min(RL, r.nsteps - k);
+    }
+    if (sub != 0) return;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    if (win >= 0) {
+        const float qx = fmaf(s_hit, r.dx, r.ex), qy = fmaf(s_hit, r.dy, r.ey), qz = fmaf(s_hit, r.dz, r.ez);
+        const float gx = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx + 1.0f, qy, qz) -
+                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx - 1.0f, qy, qz));
+        const float gy = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy + 1.0f, qz) -
+                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy - 1.0f, qz));
+        const float gz = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, qz + 1.0f) -
+                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, qz - 1.0f));
+        const float gl = sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
+        const float ndl = gl > 0.0f ? fabsf(fmaf(gx, r.dx, fmaf(gy, r.dy, gz * r.dz))) / gl : 1.0f;
+        float spec = ndl;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) spec *= spec;          // ndl^32
+        const float4 col = classify(p.lut[win], p.iso[win]);
+        const float diff = fmaf(0.75f, ndl, 0.25f);
+        C0 = clamp01(fmaf(col.x, diff, 0.25f * spec));
+        C1 = clamp01(fmaf(col.y, diff, 0.25f * spec));
+        C2 = clamp01(fmaf(col.z, diff, 0.25f * spec));
+        A = 1.0f;
+    }
+    write_pixel(p, r.pix, C0, C1, C2, A, ns);
+}
+
+// Persistent warps over the ray list, iso-surface mode.
+template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL>
+__device__ __forceinline__ void march_iso(const KParams &p)
+{
+    constexpr unsigned RAYS = 32 / RL;
+    const int lane = threadIdx.x & 31;
+    const unsigned n_rays = *(volatile unsigned *)&p.ctr->n_rays;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctr->next, RAYS);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_rays) break;
+        const unsigned idx = base + (unsigned)(lane / RL);
+        if (idx < n_rays) iso_ray<NACT, SIG, INTERP, Idx, RL>(p, idx, lane);
     }
 }
 
@@ -622,8 +907,13 @@ __global__ void __launch_bounds__(128, 8) k_raycast(const __grid_constant__ KPar
 {
     __shared__ float4 s_lut[NACT * 256];
     load_luts<NACT>(p, s_lut);
-    march<NACT, ZeroCopyShader<NACT, SIG, INTERP, Idx, MODE == MODE_TOUCH>, RL, MODE == MODE_LABEL>(
-        p, s_lut);
+    using Shader = ZeroCopyShader<NACT, SIG, INTERP, Idx, MODE == MODE_TOUCH>;
+    if constexpr (MODE == MODE_LONG)
+        march_long<Shader>(p, s_lut);
+    else if constexpr (MODE == MODE_ISO)
+        march_iso<NACT, SIG, INTERP, Idx, RL>(p);
+    else
+        march<NACT, Shader, RL, MODE == MODE_LABEL, MODE == MODE_SKIP>(p, s_lut);
 }
 
 // Copy the ray list (at most `cap` records) and its length out of the workspace.

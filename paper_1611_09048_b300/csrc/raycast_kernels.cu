@@ -34,6 +34,21 @@ static const ZcEntry k_entries[] = {
     ISAAC_Z2(3, 0u, 1, false, MODE_TOUCH), ISAAC_Z2(4, 0u, 1, false, MODE_TOUCH),
     ISAAC_Z2(1, 0u, 4, false, MODE_LABEL), ISAAC_Z2(2, 0u, 4, false, MODE_LABEL),
     ISAAC_Z2(3, 0u, 4, false, MODE_LABEL), ISAAC_Z2(4, 0u, 4, false, MODE_LABEL),
+    // iso surfaces
+    ISAAC_Z2(1, 0x9u, 4, false, MODE_ISO), ISAAC_Z2(3, 0x9BBu, 4, false, MODE_ISO),
+    ISAAC_Z2(1, 0u, 4, false, MODE_ISO), ISAAC_Z2(2, 0u, 4, false, MODE_ISO),
+    ISAAC_Z2(3, 0u, 4, false, MODE_ISO), ISAAC_Z2(4, 0u, 4, false, MODE_ISO),
+    // marches with empty-space skipping
+    ISAAC_Z2(1, 0x9u, 4, false, MODE_SKIP), ISAAC_Z2(3, 0x9BBu, 8, false, MODE_SKIP),
+    ISAAC_Z2(1, 0u, 4, false, MODE_SKIP), ISAAC_Z2(2, 0u, 4, false, MODE_SKIP),
+    ISAAC_Z2(3, 0u, 4, false, MODE_SKIP), ISAAC_Z2(4, 0u, 4, false, MODE_SKIP),
+    // long-ray marches (after an interval proposal): a warp per ray
+    ISAAC_Z2(1, 0x9u, 32, false, MODE_LONG), ISAAC_Z2(3, 0x9BBu, 32, false, MODE_LONG),
+    ISAAC_Z2(3, 0x933u, 32, false, MODE_LONG),
+    ISAAC_Z2(1, 0u, 32, false, MODE_LONG), ISAAC_Z2(2, 0u, 32, false, MODE_LONG),
+    ISAAC_Z2(3, 0u, 32, false, MODE_LONG), ISAAC_Z2(4, 0u, 32, false, MODE_LONG),
+    ISAAC_Z2(1, 0u, 32, true, MODE_LONG), ISAAC_Z2(2, 0u, 32, true, MODE_LONG),
+    ISAAC_Z2(3, 0u, 32, true, MODE_LONG), ISAAC_Z2(4, 0u, 32, true, MODE_LONG),
 };
 #undef ISAAC_Z2
 #undef ISAAC_Z

@@ -27,10 +27,11 @@ struct Workspace {
 static std::mutex g_ws_mu;
 static std::vector<Workspace> g_ws;
 
-int bind_workspace(KParams &p, cudaStream_t st)
+int bind_workspace(KParams &p, cudaStream_t st, size_t extra, void **extra_ptr)
 {
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-    const size_t need = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * (sizeof(RayRec) + sizeof(unsigned));
+    const size_t lists = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * (sizeof(RayRec) + sizeof(unsigned));
+    const size_t need = lists + extra;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
     std::lock_guard<std::mutex> lock(g_ws_mu);
@@ -59,6 +60,7 @@ int bind_workspace(KParams &p, cudaStream_t st)
     p.ctr = static_cast<WsCounters *>(w->ptr);
     p.rays = reinterpret_cast<RayRec *>(static_cast<char *>(w->ptr) + kWsHeader);
     p.longs = reinterpret_cast<unsigned *>(p.rays + std::max(1LL, rect));
+    if (extra_ptr) *extra_ptr = static_cast<char *>(w->ptr) + lists;
     return ISAAC_OK;
 }
 
@@ -111,7 +113,7 @@ int march_grab()
 static thread_local cudaEvent_t t_march_start = nullptr, t_march_stop = nullptr;
 
 int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const FrameHook *hook,
-                      bool long_list)
+                      FrameLaunch fn_long)
 {
     const bool any = fn && p.rx1 > p.rx0 && p.ry1 > p.ry0;
     if (!any) {   // nothing to ray cast: the background covers every pixel
@@ -122,7 +124,7 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const
     }
     int rc = bind_workspace(p, st);
     if (rc) return rc;
-    if (!hook || !long_list) p.longs = nullptr;   // only a proposal fills the long-ray list
+    if (!hook || !fn_long) p.longs = nullptr;   // only a proposal fills the long-ray list
     p.grab = march_grab();
     launch_fill(p, st);
     launch_setup(p, st);
@@ -134,6 +136,7 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const
     const long long want = (rect * rl + 127) / 128;
     const long long cap = (long long)sm_count() * 8;
     if (t_march_start) cudaEventRecord(t_march_start, st);
+    if (p.longs) fn_long(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
     fn(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
     if (t_march_stop) cudaEventRecord(t_march_stop, st);
     return check_cuda("render launch");
@@ -254,15 +257,19 @@ static int render_mode(const isaac_source *sources, const isaac_chain *chains, i
     rc = prepare_fb(fb, p);
     if (rc) return rc;
     if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered here");
-    FrameLaunch fn = nullptr;
+    FrameLaunch fn = nullptr, fn_long = nullptr;
     int rl = 1;
     if (nact > 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
         fn = find_zc(nact, sig, opts->interp, wide, mode,
                      choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact)), &rl);
         if (!fn) return fail(ISAAC_ENOTSUP, "no kernel for %d sources in this mode", nact);
+        if (hook && mode == MODE_PLAIN) {
+            int rl_long = 0;
+            fn_long = find_zc(nact, sig, opts->interp, wide, MODE_LONG, kLongRayLanes, &rl_long);
+        }
     }
-    return launch_frame_with(p, fn, rl, st, hook, mode != MODE_LABEL);
+    return launch_frame_with(p, fn, rl, st, hook, fn_long);
 }
 
 extern "C" int isaac_trace(const isaac_source *sources, const isaac_chain *chains,
@@ -307,6 +314,95 @@ extern "C" int isaac_render_learned(const isaac_source *sources, const isaac_cha
     KParams p;
     return render_mode(sources, chains, n_sources, luts, weights, camera, clip, n_clip, opts, fb,
                        (cudaStream_t)stream, MODE_PLAIN, &hook, p);
+}
+
+extern "C" int isaac_render_skip(const isaac_source *sources, const isaac_chain *chains,
+                                 int32_t n_sources, const float *luts, const float *weights,
+                                 const isaac_camera *camera, const isaac_plane *clip,
+                                 int32_t n_clip, const isaac_render_opts *opts,
+                                 const isaac_framebuffer *fb, const float *ranges,
+                                 int64_t ranges_len, int32_t cell, void *stream)
+{
+    clear_error();
+    KParams p;
+    memset(&p, 0, sizeof p);
+    int rc = prepare_frame(camera, clip, n_clip, opts, p);
+    if (rc) return rc;
+    int nact = 0;
+    unsigned sig = 0;
+    bool wide = false;
+    rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, p, &nact, &sig, &wide);
+    if (rc) return rc;
+    rc = prepare_fb(fb, p);
+    if (rc) return rc;
+    if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered here");
+    if (!ranges || ((uintptr_t)ranges) % 8) return fail(ISAAC_EINVAL, "ranges must be 8-byte aligned device memory");
+    if (cell < 2 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 2..1024", cell);
+    p.skip_cell = cell;
+    p.sgx = (p.nx + cell - 1) / cell;
+    p.sgy = (p.ny + cell - 1) / cell;
+    p.sgz = (p.nz + cell - 1) / cell;
+    const long long cells = (long long)p.sgx * p.sgy * p.sgz;
+    int slots = 0;
+    for (int a = 0; a < nact; ++a) slots += p.src[a].fdim;
+    if (ranges_len < cells * slots * 2)
+        return fail(ISAAC_EINVAL, "ranges holds %lld floats; the active sources need %lld (same n, "
+                    "cell and active_mask as isaac_range_grid)", (long long)ranges_len, cells * slots * 2);
+    const cudaStream_t st = (cudaStream_t)stream;
+    FrameLaunch fn = nullptr;
+    int rl = 1;
+    if (nact > 0 && p.rx1 > p.rx0 && p.ry1 > p.ry0) {
+        const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
+        fn = find_zc(nact, sig, opts->interp, wide, MODE_SKIP,
+                     choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact)), &rl);
+        if (!fn) return fail(ISAAC_ENOTSUP, "no empty-space-skipping kernel for %d sources", nact);
+        void *flags = nullptr;
+        rc = bind_workspace(p, st, (size_t)cells, &flags);
+        if (rc) return rc;
+        p.empty = static_cast<const unsigned char *>(flags);
+        rc = launch_empty_flags(p, nact, ranges, slots, cells, static_cast<unsigned char *>(flags), st);
+        if (rc) return rc;
+    }
+    return launch_frame_with(p, fn, rl, st, nullptr);
+}
+
+extern "C" int isaac_render_iso(const isaac_source *sources, const isaac_chain *chains,
+                                int32_t n_sources, const float *luts, const float *iso_values,
+                                const isaac_camera *camera, const isaac_plane *clip, int32_t n_clip,
+                                const isaac_render_opts *opts, const isaac_framebuffer *fb,
+                                void *stream)
+{
+    clear_error();
+    if (!iso_values) return fail(ISAAC_EINVAL, "iso_values is required");
+    if (n_sources < 1 || n_sources > ISAAC_MAX_SOURCES)
+        return fail(ISAAC_EINVAL, "n_sources %d outside 1..%d", n_sources, ISAAC_MAX_SOURCES);
+    float ones[ISAAC_MAX_SOURCES];
+    for (int s = 0; s < ISAAC_MAX_SOURCES; ++s) ones[s] = 1.0f;
+    KParams p;
+    memset(&p, 0, sizeof p);
+    int rc = prepare_frame(camera, clip, n_clip, opts, p);
+    if (rc) return rc;
+    int nact = 0;
+    unsigned sig = 0;
+    bool wide = false;
+    rc = prepare_sources(sources, chains, n_sources, luts, ones, opts, p, &nact, &sig, &wide);
+    if (rc) return rc;
+    rc = prepare_fb(fb, p);
+    if (rc) return rc;
+    if (p.touched) return fail(ISAAC_ENOTSUP, "the footprint output is not offered here");
+    int a = 0;
+    for (int s = 0; s < n_sources; ++s) {
+        if (!((opts->active_mask >> s) & 1u)) continue;
+        if (!std::isfinite(iso_values[s])) return fail(ISAAC_EINVAL, "iso value %d is not finite", s);
+        p.iso[a++] = iso_values[s];
+    }
+    FrameLaunch fn = nullptr;
+    int rl = 1;
+    if (nact > 0) {
+        fn = find_zc(nact, sig, opts->interp, wide, MODE_ISO, 4, &rl);
+        if (!fn) return fail(ISAAC_ENOTSUP, "no iso-surface kernel for %d sources (64-bit offsets?)", nact);
+    }
+    return launch_frame_with(p, fn, rl, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int isaac_release_workspaces(void)

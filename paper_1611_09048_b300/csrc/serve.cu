@@ -289,16 +289,20 @@ static int launch_batch(isaac_server *s, Batch &b, int si)
     int tiles = 0;
     for (int i = 0; i < nreq; ++i) {
         const Request &r = b.reqs[i];
-        KParams q = s->base;
-        memcpy(q.minv, r.frame.minv, sizeof q.minv);
-        q.ndc_sx = r.frame.ndc_sx;
-        q.ndc_sy = r.frame.ndc_sy;
-        q.W = r.frame.W;
-        q.H = r.frame.H;
-        q.rx0 = r.frame.rx0;
-        q.rx1 = r.frame.rx1;
-        q.ry0 = r.frame.ry0;
-        q.ry1 = r.frame.ry1;
+        // the request's frame (camera, rectangle, options) with the server's
+        // volume part (sources or packed copy, chains, LUTs, weights)
+        KParams q = r.frame;
+        memcpy(q.src, s->base.src, sizeof q.src);
+        memcpy(q.ch, s->base.ch, sizeof q.ch);
+        memcpy(q.lut, s->base.lut, sizeof q.lut);
+        memcpy(q.comp_off, s->base.comp_off, sizeof q.comp_off);
+        q.rec = s->base.rec;
+        q.scales = s->base.scales;
+        q.pad = s->base.pad;
+        q.bx = s->base.bx;
+        q.by = s->base.by;
+        q.grab = 1;
+        q.longs = nullptr;
         q.fb8 = reinterpret_cast<uchar4 *>(blk + fb_at);
         q.fb32 = nullptr;
         q.nsamp = nullptr;

@@ -31,7 +31,8 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_render_packed_learned", "isaac_mlp_sync", "isaac_mlp_features",
            "isaac_mlp_forward", "isaac_mlp_train_step", "isaac_server_create",
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
-           "isaac_server_destroy", "isaac_time_march")
+           "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
+           "isaac_render_iso")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -200,6 +201,16 @@ def load(path: Optional[str] = None):
         lib.isaac_server_outstanding.argtypes = [C.c_void_p]
         lib.isaac_server_destroy.restype = C.c_int
         lib.isaac_server_destroy.argtypes = [C.c_void_p]
+        lib.isaac_range_grid.restype = C.c_int
+        lib.isaac_range_grid.argtypes = [C.POINTER(Source), C.c_int32, C.POINTER(RenderOpts),
+                                         C.c_int32, C.c_void_p, C.c_int64, C.c_void_p]
+        lib.isaac_render_skip.restype = C.c_int
+        lib.isaac_render_skip.argtypes = list(lib.isaac_render.argtypes[:-1]) + \
+            [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]
+        lib.isaac_render_iso.restype = C.c_int
+        lib.isaac_render_iso.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32, C.c_void_p,
+                                         C.c_void_p, C.POINTER(Camera), C.POINTER(Plane), C.c_int32,
+                                         C.POINTER(RenderOpts), C.POINTER(Framebuffer), C.c_void_p]
         lib.isaac_time_march.restype = C.c_int
         lib.isaac_time_march.argtypes = [C.c_void_p, C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
@@ -377,6 +388,73 @@ class DeviceScene:
                                         C.byref(opts), int(cell), out.data_ptr(), out.numel(),
                                         _stream_handle(stream)))
         return out
+
+    def range_grid(self, cell=16, mask=None, stream=None, out=None):
+        """Value-range grid (Gz, Gy, Gx, components, 2) float32 on the device."""
+        import torch
+        sc = self.scene
+        m = int(sc.mask if mask is None else mask)
+        slots = sum(int(src.fdim) for i, src in enumerate(sc.sources) if (m >> i) & 1)
+        G = [(int(k) + cell - 1) // cell for k in sc.n]
+        if out is None:
+            out = torch.empty((G[2], G[1], G[0], slots, 2), dtype=torch.float32, device=self.device)
+        opts = make_opts(sc, m)
+        check(load().isaac_range_grid(self.sources, len(sc.sources), C.byref(opts), int(cell),
+                                      out.data_ptr(), out.numel(), _stream_handle(stream)))
+        return out
+
+    def prepare_skip(self, ranges, cell, mv=None, proj=None, out=None, rgba32=None, nsamples=None,
+                     mask=None, lanes=None):
+        args, keep = self.prepare(mv, proj, out, rgba32, nsamples, mask, None, lanes)
+        return args + (ranges.data_ptr(), ranges.numel(), int(cell)), keep + (ranges,)
+
+    @staticmethod
+    def launch_skip(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render_skip(*args, _stream_handle(stream)))
+
+    def render_skip(self, ranges, cell=16, mv=None, proj=None, out=None, stream=None, mask=None,
+                    want_f32=False, want_nsamp=False, lanes=None):
+        """isaac_render with empty-space skipping over ``ranges`` (range_grid)."""
+        import torch
+        W, H = self.scene.width, self.scene.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=self.device) if want_nsamp else None
+        self.launch_skip(self.prepare_skip(ranges, cell, mv, proj, out, f32, ns, mask, lanes), stream)
+        return out, f32, ns
+
+    def prepare_iso(self, iso, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None):
+        """Marshal one iso-surface frame (``iso``: one threshold per source)."""
+        sc = self.scene
+        cam = make_camera(sc.modelview if mv is None else mv,
+                          sc.projection if proj is None else proj, sc.width, sc.height)
+        planes, n_clip = make_planes(sc.clip)
+        fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
+                         nsamples.data_ptr() if nsamples is not None else None, None)
+        opts = make_opts(sc, mask)
+        iso_arr = (C.c_float * len(sc.sources))(*[float(v) for v in iso])
+        keep = (cam, planes, fb, opts, iso_arr)
+        return (self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
+                C.cast(iso_arr, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
+                C.byref(fb)), keep
+
+    @staticmethod
+    def launch_iso(prepared, stream=None):
+        args, _keep = prepared
+        check(load().isaac_render_iso(*args, _stream_handle(stream)))
+
+    def render_iso(self, iso, mv=None, proj=None, out=None, stream=None, mask=None,
+                   want_f32=False, want_nsamp=False):
+        import torch
+        W, H = self.scene.width, self.scene.height
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
+        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        ns = torch.empty((H, W), dtype=torch.int32, device=self.device) if want_nsamp else None
+        self.launch_iso(self.prepare_iso(iso, mv, proj, out, f32, ns, mask), stream)
+        return out, f32, ns
 
     def trace(self, mv=None, proj=None, out=None, proposal=None, capacity=None, stream=None,
               lanes=None, want_f32=False, want_nsamp=False):

@@ -242,3 +242,16 @@ def test_time_march_wants_both_events_or_neither():
     assert lib.isaac_time_march(C.c_void_p(FAKE), None) == isaac.EINVAL
     assert "both" in lib.isaac_last_error().decode()
     assert lib.isaac_time_march(None, None) == isaac.OK
+
+
+def test_range_grid_and_skip_validate_before_any_launch():
+    lib = isaac.load()
+    a = _valid_call_args()
+    assert lib.isaac_range_grid(a["src"], 1, C.byref(a["opts"]), 1, FAKE, 1 << 20, None) == isaac.EINVAL
+    assert "cell" in lib.isaac_last_error().decode()
+    # 8 x 8 x 8 cells, cell 4: 2^3 macro cells x 1 component x 2 floats
+    assert lib.isaac_range_grid(a["src"], 1, C.byref(a["opts"]), 4, FAKE, 15, None) == isaac.ENOMEM
+    rc = lib.isaac_render_skip(a["src"], a["chains"], 1, a["luts"], C.cast(a["weights"], C.c_void_p),
+                               C.byref(a["cam"]), None, 0, C.byref(a["opts"]), C.byref(a["fb"]),
+                               FAKE, 15, 4, None)
+    assert rc == isaac.EINVAL and "ranges holds 15" in lib.isaac_last_error().decode()
