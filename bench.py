@@ -236,6 +236,7 @@ def run_ours(args, rank, world, local_rank):
 
     variants = {} if args.no_variants else \
         run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
+    iso = None if args.no_variants else run_iso(args, ds, cams, stream, flush)
     learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
     serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
@@ -300,6 +301,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(W * H * 4)},
         "clocks": clocks.summary(),
         "variants": variants,
+        "iso": iso,
         "learned": learned,
         "serving": serving,
     }
@@ -367,6 +369,46 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
         del pv, prep
         torch.cuda.empty_cache()
     return out
+
+
+def run_iso(args, ds, cams, stream, flush):
+    """Iso-surface frames (isaac_render_iso) over the same cameras: E and B
+    lengths and the density at seeded thresholds of their normalised chain
+    outputs; time per frame, samples evaluated per second, pixels hit."""
+    import torch
+    iso = [0.6, 0.6, 0.55]
+    W, H = ds.scene.width, ds.scene.height
+    fb = torch.empty((H, W, 4), dtype=torch.uint8, device=ds.device)
+    ns = torch.empty((H, W), dtype=torch.int32, device=ds.device)
+    samples, hits = 0, 0
+    with torch.cuda.stream(stream):
+        for mv, proj in cams:
+            ds.render_iso(iso, mv, proj, out=fb, stream=stream, want_nsamp=False)
+    torch.cuda.synchronize()
+    prep = [ds.prepare_iso(iso, mv, proj, out=fb, nsamples=ns) for mv, proj in cams]
+    with torch.cuda.stream(stream):
+        for j in range(len(cams)):
+            ds.launch_iso(prep[j], stream)
+            samples += int(ns.sum(dtype=torch.int64).item())
+            hits += int((fb[..., 3] == 255).sum().item())
+    prep = [ds.prepare_iso(iso, mv, proj, out=fb) for mv, proj in cams]
+    steps = min(args.steps, 2 * len(cams))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        torch.cuda.nvtx.range_push("timed_iso")
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ds.launch_iso(prep[i % len(cams)], stream)
+            ev[i][1].record(stream)
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    per_frame = samples / len(cams)
+    return {"iso": iso, "ms_per_frame": ms, "fps": 1e3 / ms,
+            "samples_per_frame": per_frame, "samples_per_s": per_frame / (ms * 1e-3),
+            "hit_pixels_per_frame": hits / len(cams), "steps": steps}
 
 
 def run_learned(args, dev, stream, flush):

@@ -66,7 +66,7 @@ typedef enum {
  * `extent` is the number of elements addressable from `ptr`; every cell the
  * renderer can reach must lie in [0, extent) or the call fails with
  * ISAAC_EGUARD.  Sources whose active_mask bit is clear are never read and
- * may be NULL (Sec. 3.2, "a deactivated source is not touched at all"). */
+ * may be NULL (Sec. 3.2: deactivated sources are never read). */
 typedef struct {
     const void *ptr;         /* device memory, owned by the caller */
     int64_t extent;
@@ -112,7 +112,7 @@ typedef struct {
     int64_t global_n[3];     /* cells of the global volume; {0,0,0} = equal to n */
     int64_t offset[3];       /* first cell of the local volume inside the global one */
     float step;              /* sample spacing along the ray, in voxels, > 0 */
-    int32_t interp;          /* 1 = trilinear (Sec. 3 "data interpolation"), 0 = nearest cell */
+    int32_t interp;          /* 1 = trilinear (Sec. 3 feature list: interpolation), 0 = nearest cell */
     float term_alpha;        /* a ray stops once its opacity A >= term_alpha; > 1 disables */
     float bg[4];             /* background RGBA (premultiplied) blended behind the volume */
     uint32_t active_mask;    /* bit s set: source s is rendered (Sec. 3.2) */
@@ -134,10 +134,10 @@ typedef struct {
 } isaac_framebuffer;
 
 /*
- * isaac_render -- one frame of the volume ray caster (Sec. 3.2: "for every
- * scan point ... iterates over all sources ... applies a functor chain ...
- * classifies it to a color and opacity ... global color and opacity ...
- * classical front to back ray cast").  Per pixel:
+ * isaac_render -- one frame of the volume ray caster (Sec. 3.2: at every
+ * sample point each active source passes its functor chain and transfer
+ * function, the sources combine into one colour and opacity, and the ray
+ * composites front to back).  Per pixel:
  *   ray through the pixel centre; entry t0 into the global box (not before
  *   the near plane); the local box and the clip planes bound [t_in, t_out];
  *   samples t0 + k*step with t_in <= t < t_out (one global sample grid); per
@@ -281,7 +281,8 @@ int isaac_render_skip(const isaac_source *sources, const isaac_chain *chains, in
  *   crossing by one secant step towards the previous sample (none at the
  *   ray's first sample), the nearest crossing wins (ties: lower source);
  *   the normal is that source's central-difference gradient (one voxel,
- *   same interpolation), turned towards the viewer; with a headlight,
+ *   the two positions clamped into the local box [0, n], same
+ *   interpolation), turned towards the viewer; with a headlight,
  *   rgb = LUT_s(iso_values[s]).rgb * (1/4 + 3/4 * n.v) + 1/4 * (n.v)^32,
  *   clamped to [0, 1], alpha 1.  Rays without a crossing show the background.
  * iso_values: host, n_sources floats (finite for active sources).  The
@@ -438,7 +439,7 @@ int isaac_render_packed_learned(const isaac_packed *vol, const isaac_chain *chai
 
 /*
  * Serving loop.  The paper has no counterpart kernel: its central server
- * (Sec. 3.5 "Steering arbitrary HPC applications using open standards")
+ * (Sec. 3.5, steering through a central server)
  * forwards one application's frames to many clients, each of which may steer
  * the camera, transfer functions and functor chains.  Here one process renders
  * many such viewers' requests against one device-resident volume with

@@ -9,11 +9,10 @@
  * definition.  It shares no code, header, table or constant with the CUDA
  * library; its own structures below are deliberately separate.
  *
- * What it computes, per pixel, serially and in double precision (Sec. 3.2,
- * "for every scan point ... iterates over all sources ... applies a functor
- * chain ... classifies it to a color and opacity ... calculate a global color
- * and opacity for the scan point to be used in the classical front to back ray
- * cast algorithm"):
+ * What it computes, per pixel, serially and in double precision (Sec. 3.2:
+ * at every sample point of a pixel's ray, each source's value goes through
+ * its functor chain and transfer function, the sources' colours and
+ * opacities are combined into one, and the ray composites front to back):
  *
  *   1. camera: M = P * MV, inverted by Gauss-Jordan elimination with partial
  *      pivoting; the pixel centre is unprojected at NDC depth -1 and +1 and
@@ -22,15 +21,15 @@
  *      t0 (not before the near plane, t >= 0); the node's local box
  *      [off, off+n)^3 (Sec. 3.1: every node owns a disjoint cuboid of the
  *      global volume) and every clip plane (keep nx*x+ny*y+nz*z+d >= 0 in
- *      global voxel coordinates, Sec. 3 feature list "clipping planes") give
+ *      global voxel coordinates, Sec. 3 feature list: clipping planes) give
  *      the sampled interval [t_in, t_out];
  *   3. samples t_k = t0 + k*step for integer k with t_in <= t_k < t_out: one
  *      sample grid anchored at the unclipped global entry, so that local
  *      images of neighbouring nodes composite to the image of the whole;
- *   4. per active source (Sec. 3.2, "2^n render functions": inactive sources
- *      are never read): cell-centred trilinear interpolation (value i sits at
+ *   4. per active source (Sec. 3.2 compiles one render function per subset
+ *      of active sources: inactive sources are never read): cell-centred trilinear interpolation (value i sits at
  *      i + 1/2; guard cells are read when present, otherwise indices clamp to
- *      the border, Sec. 3.1/3.2 "guards"), or the nearest cell when
+ *      the border, Sec. 3.1/3.2 guard cells), or the nearest cell when
  *      interpolation is off; then the source's functor chain (Sec. 3.3,
  *      Table 1, default reduction to the first component), then the 256-entry
  *      RGBA transfer function with linear interpolation between entries;
@@ -189,8 +188,8 @@ static void orc_fetch(const orc_source *s, int64_t ix, int64_t iy, int64_t iz, d
 }
 
 /* Value of a source at voxel position p: cell-centred trilinear interpolation,
- * or the containing cell when interpolation is off (Sec. 3 "data
- * interpolation"). */
+ * or the containing cell when interpolation is off (Sec. 3 feature list:
+ * optional interpolation). */
 static void orc_sample(const orc_source *s, const int64_t n[3], const double p[3], int interp,
                        double *v)
 {
@@ -296,7 +295,7 @@ static int orc_chain_check(const orc_chain *ch, int dim)
 
 /* ------------------------------------------------------- classification */
 
-/* Transfer function (Sec. 3 "freely definable transfer functions"): the
+/* Transfer function (Sec. 3 feature list: user-defined transfer functions): the
  * scalar is clamped to [0,1] (NaN -> 0) and the 256 RGBA entries, entry j at
  * j/255, are interpolated linearly. */
 static void orc_classify(const float *lut, double x, double rgba[4])
@@ -526,7 +525,8 @@ static void orc_pixel(const orc_frame *F, int64_t pix, const orc_outputs *out, i
  *   k-1 and k: t = t_{k-1} + step*(iso - v(k-1)) / (v(k) - v(k-1)), or t = t_k
  *   when k is the ray's first sample; the smallest t wins (ties: lower s);
  *   at the hit point q the winning source's gradient is taken by central
- *   differences g_a = (v(q + e_a) - v(q - e_a)) / 2 (same interpolation);
+ *   differences g_a = (v(q+) - v(q-)) / (q+ - q-)_a with q+- = q +- e_a, each
+ *   clamped into the local box [0, n] along a (same interpolation);
  *   n = -g/|g| (n = -d if g = 0), turned towards the viewer (n.(-d) >= 0);
  *   headlight Blinn-Phong with light, view and half vector all -d:
  *   rgb = LUT_s(iso[s]).rgb * (1/4 + 3/4 * n.(-d)) + 1/4 * (n.(-d))^32,
@@ -639,9 +639,10 @@ static void orc_pixel_iso(const orc_frame *F, const double *iso, int64_t pix, do
             double g[3];
             for (int a = 0; a < 3; ++a) {
                 double qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
-                qp[a] += 1.0;
-                qm[a] -= 1.0;
-                g[a] = 0.5 * (orc_source_value(F, win, qp) - orc_source_value(F, win, qm));
+                qp[a] = q[a] + 1.0 < (double)p->n[a] ? q[a] + 1.0 : (double)p->n[a];
+                qm[a] = q[a] - 1.0 > 0.0 ? q[a] - 1.0 : 0.0;
+                double h = qp[a] - qm[a];
+                g[a] = h > 0.0 ? (orc_source_value(F, win, qp) - orc_source_value(F, win, qm)) / h : 0.0;
             }
             double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
             m_grad = gl;

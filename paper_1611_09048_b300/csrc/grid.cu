@@ -26,12 +26,14 @@ struct KGrid {
 };
 
 constexpr int kGridThreads = 352;   // 11 warps: one pass over the 18 x 18 columns of a 16^3 cell
-constexpr int kGridZ = 8;           // z-cells whose loads are in flight together
+// z-cells whose loads a thread issues together: 16 on the scalar fast paths
+// (a walk is bound by the loads in flight), 8 where a cell has several values
+template <int FD> constexpr int grid_z() { return FD == 1 ? 16 : 8; }
 
 // One block per column (i, j) of macro cells.  Each thread owns (x, y)
 // columns of the column's apron-extended footprint -- consecutive threads
 // take consecutive x, so a warp's loads are coalesced -- and walks its column
-// once in z, kGridZ cells at a time with their loads issued together.  Cell z
+// once in z, grid_z() cells at a time with their loads issued together.  Cell z
 // belongs to macro cells k with k*cell - 1 <= z <= (k+1)*cell (at most two
 // for cell >= 2), so a thread keeps two running maxima, for the lowest open
 // macro cell and the next; when z leaves the lower one, the warp's maximum
@@ -42,6 +44,7 @@ constexpr int kGridZ = 8;           // z-cells whose loads are in flight togethe
 template <int NS, int FD>
 static __global__ void __launch_bounds__(kGridThreads, 2) k_opacity_grid(const __grid_constant__ KGrid p)
 {
+    constexpr int kGridZ = grid_z<(NS == 1 && FD == 1) ? 1 : 4>();
     __shared__ float s_alpha[ISAAC_MAX_ACTIVE * 256];
     const int nact = NS ? NS : p.nact;
     for (int i = threadIdx.x; i < nact * 256; i += blockDim.x) s_alpha[i] = __ldg(&p.lut[i >> 8][i & 255].w);
@@ -174,6 +177,7 @@ static __global__ void k_range_decode(unsigned *r, long long n)
 template <int FD>
 static __global__ void __launch_bounds__(kGridThreads, 2) k_range_grid(const __grid_constant__ KRange p)
 {
+    constexpr int kGridZ = grid_z<FD>();
     const float inf = __int_as_float(0x7f800000);
     const KSource &q = p.src;
     const int gi = blockIdx.x % p.gx, gj = blockIdx.x / p.gx;

@@ -86,10 +86,13 @@ constexpr int kLongRay = -2;
 // A proposal puts a ray in the long-ray list when it keeps more samples than this.
 constexpr int kLongRaySamples = 96;
 // Lanes per ray and samples per lane and step on the long-ray list.  A long
-// ray's time is its chain of dependent gathers (about one DRAM latency per
-// step), so a whole warp takes the ray and each lane gathers 4 samples per
-// step: 128 samples' loads in flight per step.
-constexpr int kLongRayLanes = 32;
+// ray's time is its chain of dependent steps, each about one DRAM latency of
+// gathers plus the in-order compositing of the step's samples; every lane of
+// a group composites every sample, so compositing costs RL/32 warp steps per
+// sample.  16 lanes x 4 samples (64 samples' loads in flight per step)
+// balance the two; 32 x 4 was measured issue-bound (20 warp instructions of
+// compositing per sample).
+constexpr int kLongRayLanes = 16;
 constexpr int kLongRaySteps = 4;
 
 // March modes: plain (skipping rays on the long-ray list), footprint bitmap,
@@ -795,7 +798,8 @@ __device__ __forceinline__ float value_of(const KParams &p, int which, float x, 
 // source's chain value reaches its threshold; each crossing source refines
 // the crossing by one secant step towards the previous sample, the nearest
 // wins (ties: lower source); the normal is the winning source's central-
-// difference gradient (one voxel), turned towards the viewer; headlight
+// difference gradient (one voxel, positions clamped into the box), turned
+// towards the viewer; headlight
 // Blinn-Phong: rgb = LUT(iso).rgb * (1/4 + 3/4 n.v) + 1/4 (n.v)^32, alpha 1).
 // The RL lanes of a group evaluate consecutive samples; a ballot finds the
 // first one that crosses.
@@ -856,12 +860,16 @@ __device__ __forceinline__ void iso_ray(const KParams &p, unsigned idx, int lane
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     if (win >= 0) {
         const float qx = fmaf(s_hit, r.dx, r.ex), qy = fmaf(s_hit, r.dy, r.ey), qz = fmaf(s_hit, r.dz, r.ez);
-        const float gx = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx + 1.0f, qy, qz) -
-                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx - 1.0f, qy, qz));
-        const float gy = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy + 1.0f, qz) -
-                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy - 1.0f, qz));
-        const float gz = 0.5f * (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, qz + 1.0f) -
-                                 value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, qz - 1.0f));
+        // central differences over one voxel, positions clamped into the box
+        const float xp = fminf(qx + 1.0f, (float)p.nx), xm = fmaxf(qx - 1.0f, 0.0f);
+        const float yp = fminf(qy + 1.0f, (float)p.ny), ym = fmaxf(qy - 1.0f, 0.0f);
+        const float zp = fminf(qz + 1.0f, (float)p.nz), zm = fmaxf(qz - 1.0f, 0.0f);
+        const float gx = xp > xm ? (value_of<NACT, SIG, INTERP, Idx>(p, win, xp, qy, qz) -
+                                    value_of<NACT, SIG, INTERP, Idx>(p, win, xm, qy, qz)) / (xp - xm) : 0.0f;
+        const float gy = yp > ym ? (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, yp, qz) -
+                                    value_of<NACT, SIG, INTERP, Idx>(p, win, qx, ym, qz)) / (yp - ym) : 0.0f;
+        const float gz = zp > zm ? (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, zp) -
+                                    value_of<NACT, SIG, INTERP, Idx>(p, win, qx, qy, zm)) / (zp - zm) : 0.0f;
         const float gl = sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
         const float ndl = gl > 0.0f ? fabsf(fmaf(gx, r.dx, fmaf(gy, r.dy, gz * r.dz))) / gl : 1.0f;
         float spec = ndl;

@@ -12,7 +12,7 @@ Every generator takes an explicit seed and uses ``numpy.random.default_rng``.
 Conventions shared by every scene (the readings of the paper's silent points):
 
 * A field lives on the interior grid of ``n = (nx, ny, nz)`` cells plus
-  ``guard`` ghost cells per side (Sec. 3.1 "guards").  Cell ``i`` holds the
+  ``guard`` ghost cells per side (Sec. 3.1 guard cells).  Cell ``i`` holds the
   value at voxel coordinate ``i + 0.5``; the interior box is ``[0, n)``.
 * World coordinates are voxel coordinates shifted so that the box centre is the
   origin: ``world = voxel - n / 2``.  Camera matrices are OpenGL-style,
