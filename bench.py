@@ -295,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
                         "peak": l2_peak, "unit": "GB/s",
                         "frac": (lts / (mean_launch_ms * 1e-3) / 1e9 / l2_peak) if lts else None,
                         "bytes": "ncu lts__t_bytes per k_raycast launch (profiles/traffic.json)",
-                        "peak_kind": "measured here: copy within half the L2 (read + write bytes), best of 10"},
+                        "peak_kind": "measured here: isaac_probe_read over half the L2, best of 10"},
         "e2e": {"value": all_samp / (e2e_ms * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(luts_host.numel() * 4),
                 "d2h_bytes_per_step": int(W * H * 4)},
@@ -549,13 +549,7 @@ def run_serving(args, ds, dev):
     torch.cuda.synchronize()
     rng = np.random.default_rng(2024)
     sizes = [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
-    n_cl, rate, dur = args.serve_clients, args.serve_rate, args.serve_seconds
-    n_req = int(rate * dur)
-    gaps = rng.exponential(1.0 / rate, n_req)
-    t_arr = np.cumsum(gaps)
-    who = rng.integers(0, n_cl, n_req)
-    size_of = rng.integers(0, len(sizes), n_req)
-    steer = rng.uniform(0, 1, n_req) < args.serve_steer
+    n_cl = args.serve_clients
     state = [{"theta": rng.uniform(0, 2 * math.pi), "phi": rng.uniform(-0.5, 0.5),
               "luts": None, "chains": None} for _ in range(n_cl)]
     base_chains = [list(c) for c in sc.chains]
@@ -564,11 +558,17 @@ def run_serving(args, ds, dev):
     bufs = [torch.empty(1920 * 1080 * 4, dtype=torch.uint8).pin_memory() for _ in range(n_buf)]
     free = list(range(n_buf))
 
-    def make(i):
-        c = state[who[i]]
+    def schedule(rate, dur):
+        n = int(rate * dur)
+        return {"rate": rate, "n": n, "t": np.cumsum(rng.exponential(1.0 / rate, n)),
+                "who": rng.integers(0, n_cl, n), "size": rng.integers(0, len(sizes), n),
+                "steer": rng.uniform(0, 1, n) < args.serve_steer}
+
+    def make(sch, i):
+        c = state[sch["who"][i]]
         c["theta"] += math.radians(rng.normal(0, 2.0))
         c["phi"] = float(np.clip(c["phi"] + math.radians(rng.normal(0, 2.0)), -1.2, 1.2))
-        if steer[i]:
+        if sch["steer"][i]:
             if rng.uniform() < 0.5:
                 c["luts"] = np.stack([synth.lut_from_points(int(rng.integers(1 << 30)))
                                       for _ in range(pv.luts.shape[0])])
@@ -578,34 +578,49 @@ def run_serving(args, ds, dev):
                 ch[0] = [(op[0], tuple(a * f for a in op[1])) if op[0] == "mul" else op
                          for op in ch[0]]
                 c["chains"] = ch
-        W, H = sizes[size_of[i]]
+        W, H = sizes[sch["size"][i]]
         mv, proj = synth.orbit_camera(sc.n, W, H, c["theta"], c["phi"], dist_factor=2.0)
         return mv, proj, W, H, c["luts"], c["chains"]
 
-    def run_open(srv):
+    def run_open(srv, sch):
         res, stalls, t0 = [], 0, time.perf_counter()
         held = {}
-        i = 0
-        while i < n_req or held:
+        i, n, t_arr = 0, sch["n"], sch["t"]
+        while i < n or held:
             now = time.perf_counter() - t0
-            if i < n_req and now >= t_arr[i]:
+            if i < n and now >= t_arr[i]:
                 if not free:
                     stalls += 1
                     for r in srv.poll(wait=0.001):
                         free.append(held.pop(r["tag"]))
                         res.append(r)
                     continue
-                mv, proj, W, H, luts, chains = make(i)
+                mv, proj, W, H, luts, chains = make(sch, i)
                 b = free.pop()
                 out = bufs[b][: W * H * 4]
                 held[srv.submit(mv, proj, W, H, out, luts=luts, chains=chains)] = b
                 i += 1
                 continue
-            wait = max(0.0, (t_arr[i] - now) if i < n_req else 0.002)
+            wait = max(0.0, (t_arr[i] - now) if i < n else 0.002)
             for r in srv.poll(wait=min(wait, 0.002)):
                 free.append(held.pop(r["tag"]))
                 res.append(r)
-        return res, stalls
+        assert all(r["status"] == 0 for r in res)
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+        qwait = np.array([r["t_launch"] - r["t_submit"] for r in res]) * 1e3
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        px = sum(sizes[k][0] * sizes[k][1] for k in sch["size"])
+        bs = np.array([r["batch_size"] for r in res])
+        return {"offered_rate_per_s": sch["rate"], "requests": n,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p90": float(np.percentile(lat, 90)),
+                               "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                               "mean": float(lat.mean())},
+                "queue_ms": {"p50": float(np.percentile(qwait, 50)),
+                             "p99": float(np.percentile(qwait, 99))},
+                "fps": n / span, "mpix_per_s": px / span / 1e6,
+                "batch_size": {"mean": float(bs.mean()), "max": int(bs.max())},
+                "generator_stalls": stalls}
 
     with isaac.Server(pv, budget=args.serve_budget << 20, n_streams=args.serve_streams,
                       max_batch=args.serve_max_batch) as srv:
@@ -614,7 +629,9 @@ def run_serving(args, ds, dev):
             mv, proj = synth.orbit_camera(sc.n, *sizes[k % 4], 0.1 * k, 0.1)
             srv.submit(mv, proj, *sizes[k % 4], bufs[k][: sizes[k % 4][0] * sizes[k % 4][1] * 4])
         srv.drain()
-        res, stalls = run_open(srv)
+        main = run_open(srv, schedule(args.serve_rate, args.serve_seconds))
+        stress = run_open(srv, schedule(args.serve_stress_rate, args.serve_stress_seconds)) \
+            if args.serve_stress_seconds > 0 else None
         # closed loop: keep every buffer in flight, 1080p only
         burst = []
         held = {}
@@ -631,53 +648,41 @@ def run_serving(args, ds, dev):
                 free.append(held.pop(r["tag"]))
                 burst.append(r)
         t_burst = time.perf_counter() - t0
-    assert all(r["status"] == 0 for r in res + burst)
-    lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
-    qwait = np.array([r["t_launch"] - r["t_submit"] for r in res]) * 1e3
-    t_first = min(r["t_submit"] for r in res)
-    t_last = max(r["t_done"] for r in res)
-    px = sum(sizes[size_of[i]][0] * sizes[size_of[i]][1] for i in range(n_req))
-    bs = np.array([r["batch_size"] for r in res])
-    return {
+    assert all(r["status"] == 0 for r in burst)
+    res = {
         "workload": "serve_pic512_bf16",
-        "clients": n_cl, "offered_rate_per_s": rate, "requests": n_req,
-        "sizes": [f"{w}x{h}" for w, h in sizes], "steering_share": args.serve_steer,
-        "budget_mib": args.serve_budget, "streams": args.serve_streams,
-        "max_batch": args.serve_max_batch,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
-                       "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
-                       "mean": float(lat.mean())},
-        "queue_ms": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
-        "fps": n_req / (t_last - t_first),
-        "mpix_per_s": px / (t_last - t_first) / 1e6,
-        "batch_size": {"mean": float(bs.mean()), "max": int(bs.max())},
-        "generator_stalls": stalls,
+        "clients": n_cl, "sizes": [f"{w}x{h}" for w, h in sizes],
+        "steering_share": args.serve_steer, "budget_mib": args.serve_budget,
+        "streams": args.serve_streams, "max_batch": args.serve_max_batch,
         "saturated_1080p_fps": len(burst) / t_burst,
         "latency_note": "submit -> RGBA8 image in pinned host memory, measured by the server's own "
                         "clock; includes queueing, the batch's kernels and its device-to-host copy",
     }
+    res.update(main)
+    res["stress"] = stress
+    return res
 
 
 def _l2_peak(dev):
-    """L2 bandwidth probe: copies between two buffers that together fill half
-    the L2 (resident after the first pass), read + write bytes, best of 10
-    runs of 20 copies, CUDA events."""
+    """L2 read bandwidth: isaac_probe_read (16-byte loads cached in L2 only)
+    over a buffer of half the L2, resident after the first pass; best of 10
+    runs of 20 passes, CUDA events."""
     import torch
-    n = torch.cuda.get_device_properties(dev).L2_cache_size // 4 // 4
-    a = torch.ones(n, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    for _ in range(3):
-        b.copy_(a)
+    from paper_1611_09048_b300 import isaac
+    n = torch.cuda.get_device_properties(dev).L2_cache_size // 2
+    buf = torch.ones(n // 4, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1024, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    isaac.probe_read(buf, 3, sink, stream)
     best = float("inf")
     for _ in range(10):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(20):
-            b.copy_(a)
-        e1.record()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        isaac.probe_read(buf, 20, sink, stream)
+        b.record(stream)
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 20)
-    return 2 * n * 4 / (best * 1e-3) / 1e9
+        best = min(best, a.elapsed_time(b))
+    return 20 * buf.numel() * 4 / (best * 1e-3) / 1e9
 
 
 def _ncu_traffic(workload):
@@ -776,6 +781,9 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--serve-max-batch", type=int, default=16)
     ap.add_argument("--serve-buffers", type=int, default=64)
+    ap.add_argument("--serve-stress-rate", type=float, default=3000.0,
+                    help="second open-loop point, above what one request at a time sustains")
+    ap.add_argument("--serve-stress-seconds", type=float, default=4.0)
     ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--preroll", type=float, default=1.0,
                     help="seconds of untimed frames inside the clock-sampling window")

@@ -532,6 +532,12 @@ int isaac_server_destroy(isaac_server *server);
  * NULL, NULL stops it; one NULL and one event is ISAAC_EINVAL. */
 int isaac_time_march(void *start_event, void *stop_event);
 
+/* Measurement aid (no counterpart in the paper): read `bytes` of device
+ * memory at `buf` (16-byte aligned) `passes` times with 16-byte loads cached
+ * in L2 only; sink: device memory of 1024 uint32 the kernel may write.  The
+ * bench times it on a buffer of half the L2 for the L2 bandwidth it reports. */
+int isaac_probe_read(const void *buf, int64_t bytes, int32_t passes, uint32_t *sink, void *stream);
+
 /* Free the render workspaces of the current device (synchronises the device). */
 int isaac_release_workspaces(void);
 

@@ -297,6 +297,7 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
     }
     p.step = opt->step;
     p.step_d = (double)opt->step;
+    p.inv_step_d = 1.0 / p.step_d;
     // every ray's samples lie on one chord of the local box
     const double diag = std::sqrt((double)opt->n[0] * opt->n[0] + (double)opt->n[1] * opt->n[1] +
                                   (double)opt->n[2] * opt->n[2]);

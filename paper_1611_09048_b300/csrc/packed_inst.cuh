@@ -25,10 +25,10 @@ static void launch_pack(const KPack &p, cudaStream_t st)
 
 // {nact, sig, pad, interp, rl, long, launcher}; pad of a specialised signature
 // is next_pow2(component total), the generic kernels use pad 8.  The long-ray
-// marches (16 lanes per ray) exist for every layout a proposal can meet.
+// marches (a warp per ray) exist for every layout a proposal can meet.
 #define ISAAC_E(N, S, P, I, R) {N, S, P, I, R, false, launch_packed<N, S, ISAAC_DT, P, I, R, false>}
 #define ISAAC_E2(N, S, P, R) ISAAC_E(N, S, P, 0, R), ISAAC_E(N, S, P, 1, R)
-#define ISAAC_L(N, S, P, I) {N, S, P, I, 16, true, launch_packed<N, S, ISAAC_DT, P, I, 16, true>}
+#define ISAAC_L(N, S, P, I) {N, S, P, I, 32, true, launch_packed<N, S, ISAAC_DT, P, I, 32, true>}
 #define ISAAC_L2(N, S, P) ISAAC_L(N, S, P, 0), ISAAC_L(N, S, P, 1)
 static const PackedEntry k_entries[] = {
     ISAAC_E2(1, 0x1u, 1, 1), ISAAC_E2(1, 0x1u, 1, 2), ISAAC_E2(1, 0x1u, 1, 4),

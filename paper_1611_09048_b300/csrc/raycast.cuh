@@ -85,14 +85,13 @@ struct WsCounters {
 constexpr int kLongRay = -2;
 // A proposal puts a ray in the long-ray list when it keeps more samples than this.
 constexpr int kLongRaySamples = 96;
-// Lanes per ray and samples per lane and step on the long-ray list.  A long
-// ray's time is its chain of dependent steps, each about one DRAM latency of
-// gathers plus the in-order compositing of the step's samples; every lane of
-// a group composites every sample, so compositing costs RL/32 warp steps per
-// sample.  16 lanes x 4 samples (64 samples' loads in flight per step)
-// balance the two; 32 x 4 was measured issue-bound (20 warp instructions of
-// compositing per sample).
-constexpr int kLongRayLanes = 16;
+// Lanes per ray and samples per lane and step on the long-ray list: a warp
+// per ray, 128 samples' gathers in flight per step.  Measured at 1080p over
+// the 512^3 bubble (about 4e3 long rays, 3e6 samples): 32 x 4 194 us, 16 x 4
+// 217 us, 16 x 4 with one block per SM 473 us.  Every lane of a group
+// composites every sample in order, so wide groups spend RL/32 warp steps of
+// compositing per sample; the kernel is issue-bound at 32 x 4.
+constexpr int kLongRayLanes = 32;
 constexpr int kLongRaySteps = 4;
 
 // March modes: plain (skipping rays on the long-ray list), footprint bitmap,
@@ -107,7 +106,7 @@ struct KParams {
     double llo[3], lhi[3];           // local box in global voxel coordinates
     double clip[ISAAC_MAX_CLIP][4];
     double ndc_sx, ndc_sy;           // 2 / W, 2 / H
-    double step_d;
+    double step_d, inv_step_d;
     float step;
     float term;
     float bg[4];
@@ -476,6 +475,19 @@ struct ZeroCopyShader {
 // sample index range).  The discrete decisions (first/last sample) are taken
 // in double so they match an FP64 reference except at exact ties; the first
 // sample's position and the direction are then rounded to FP32 for the march.
+// FP64 reciprocal from the FP32 one and two Newton steps (error ~1 ulp of
+// double, against some twenty FP64 operations for a division); operands
+// outside the FP32 range take the division.
+__device__ __forceinline__ double drcp(double x)
+{
+    const float rf = __frcp_rn((float)x);
+    if (!(fabsf(rf) < 1.0e38f) || !(fabsf(rf) > 1.0e-37f)) return 1.0 / x;
+    double r = (double)rf;
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    return r;
+}
+
 __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
 {
     RayRec r;
@@ -496,7 +508,7 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
         nb[i] = b - m[8 + i];
         fb[i] = b + m[8 + i];
     }
-    const double inw = 1.0 / nb[3], ifw = 1.0 / fb[3];
+    const double inw = drcp(nb[3]), ifw = drcp(fb[3]);
     double o[3], d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -518,7 +530,7 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (d[a] != 0.0) {
-            const double inv = 1.0 / d[a];
+            const double inv = drcp(d[a]);
             double ta = (0.0 - o[a]) * inv, tb = (p.gn[a] - o[a]) * inv;
             t0 = fmax(t0, fmin(ta, tb));
             tg1 = fmin(tg1, fmax(ta, tb));
@@ -537,17 +549,17 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
         const double s = fma(pl[0], o[0], fma(pl[1], o[1], fma(pl[2], o[2], pl[3])));
         const double rr = fma(pl[0], d[0], fma(pl[1], d[1], pl[2] * d[2]));
         if (rr > 0.0) {
-            tin = fmax(tin, -s / rr);
+            tin = fmax(tin, -s * drcp(rr));
         } else if (rr < 0.0) {
-            tout = fmin(tout, -s / rr);
+            tout = fmin(tout, -s * drcp(rr));
         } else if (s < 0.0) {
             miss = true;
         }
     }
     // the local box is bounded, so a ray inside it has a finite exit
     if (miss || !(tin < tout) || !(tout < 1e299)) return r;
-    const long long kf = (tin > t0) ? (long long)ceil((tin - t0) / p.step_d) : 0LL;
-    const long long ke = (long long)ceil((tout - t0) / p.step_d);
+    const long long kf = (tin > t0) ? (long long)ceil((tin - t0) * p.inv_step_d) : 0LL;
+    const long long ke = (long long)ceil((tout - t0) * p.inv_step_d);
     if (ke <= kf) return r;
     const double tf = t0 + (double)kf * p.step_d;
     r.ex = (float)(fma(tf, d[0], o[0]) - p.llo[0]);

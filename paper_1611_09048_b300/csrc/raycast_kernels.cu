@@ -42,13 +42,13 @@ static const ZcEntry k_entries[] = {
     ISAAC_Z2(1, 0x9u, 4, false, MODE_SKIP), ISAAC_Z2(3, 0x9BBu, 8, false, MODE_SKIP),
     ISAAC_Z2(1, 0u, 4, false, MODE_SKIP), ISAAC_Z2(2, 0u, 4, false, MODE_SKIP),
     ISAAC_Z2(3, 0u, 4, false, MODE_SKIP), ISAAC_Z2(4, 0u, 4, false, MODE_SKIP),
-    // long-ray marches (after an interval proposal): 16 lanes per ray
-    ISAAC_Z2(1, 0x9u, 16, false, MODE_LONG), ISAAC_Z2(3, 0x9BBu, 16, false, MODE_LONG),
-    ISAAC_Z2(3, 0x933u, 16, false, MODE_LONG),
-    ISAAC_Z2(1, 0u, 16, false, MODE_LONG), ISAAC_Z2(2, 0u, 16, false, MODE_LONG),
-    ISAAC_Z2(3, 0u, 16, false, MODE_LONG), ISAAC_Z2(4, 0u, 16, false, MODE_LONG),
-    ISAAC_Z2(1, 0u, 16, true, MODE_LONG), ISAAC_Z2(2, 0u, 16, true, MODE_LONG),
-    ISAAC_Z2(3, 0u, 16, true, MODE_LONG), ISAAC_Z2(4, 0u, 16, true, MODE_LONG),
+    // long-ray marches (after an interval proposal): a warp per ray
+    ISAAC_Z2(1, 0x9u, 32, false, MODE_LONG), ISAAC_Z2(3, 0x9BBu, 32, false, MODE_LONG),
+    ISAAC_Z2(3, 0x933u, 32, false, MODE_LONG),
+    ISAAC_Z2(1, 0u, 32, false, MODE_LONG), ISAAC_Z2(2, 0u, 32, false, MODE_LONG),
+    ISAAC_Z2(3, 0u, 32, false, MODE_LONG), ISAAC_Z2(4, 0u, 32, false, MODE_LONG),
+    ISAAC_Z2(1, 0u, 32, true, MODE_LONG), ISAAC_Z2(2, 0u, 32, true, MODE_LONG),
+    ISAAC_Z2(3, 0u, 32, true, MODE_LONG), ISAAC_Z2(4, 0u, 32, true, MODE_LONG),
 };
 #undef ISAAC_Z2
 #undef ISAAC_Z

@@ -437,3 +437,31 @@ extern "C" int isaac_time_march(void *start_event, void *stop_event)
     t_march_stop = static_cast<cudaEvent_t>(stop_event);
     return ISAAC_OK;
 }
+
+// Measurement aid: stream `bytes` of device memory `passes` times through
+// 16-byte loads (an L2 bandwidth probe when the buffer fits in L2).
+static __global__ void k_probe_read(const uint4 *__restrict__ buf, long long n, int passes,
+                                    unsigned *sink)
+{
+    unsigned acc = 0;
+    for (int r = 0; r < passes; ++r)
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x9e3779b9u) sink[blockIdx.x & 1023] = acc;   // keeps the loads alive
+}
+
+extern "C" int isaac_probe_read(const void *buf, int64_t bytes, int32_t passes, uint32_t *sink,
+                                void *stream)
+{
+    clear_error();
+    if (!buf || !sink || bytes < 16 || passes < 1 || ((uintptr_t)buf) % 16)
+        return fail(ISAAC_EINVAL, "a 16-byte aligned buffer of >= 16 bytes, passes >= 1 and a sink are required");
+    const long long n = bytes / 16;
+    const int blocks = sm_count() * 8;
+    k_probe_read<<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<const uint4 *>(buf), n, passes,
+                                                          sink);
+    return check_cuda("isaac_probe_read launch");
+}

@@ -32,7 +32,7 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_mlp_forward", "isaac_mlp_train_step", "isaac_server_create",
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
            "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
-           "isaac_render_iso")
+           "isaac_render_iso", "isaac_probe_read")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -211,6 +211,8 @@ def load(path: Optional[str] = None):
         lib.isaac_render_iso.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32, C.c_void_p,
                                          C.c_void_p, C.POINTER(Camera), C.POINTER(Plane), C.c_int32,
                                          C.POINTER(RenderOpts), C.POINTER(Framebuffer), C.c_void_p]
+        lib.isaac_probe_read.restype = C.c_int
+        lib.isaac_probe_read.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
         lib.isaac_time_march.restype = C.c_int
         lib.isaac_time_march.argtypes = [C.c_void_p, C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
@@ -282,6 +284,12 @@ def time_march(start=None, stop=None):
     recorded once before, so that their CUDA handles exist."""
     check(load().isaac_time_march(C.c_void_p(start.cuda_event) if start is not None else None,
                                   C.c_void_p(stop.cuda_event) if stop is not None else None))
+
+
+def probe_read(buf, passes, sink, stream=None):
+    """Read device tensor ``buf`` ``passes`` times (isaac_probe_read)."""
+    check(load().isaac_probe_read(buf.data_ptr(), buf.numel() * buf.element_size(), int(passes),
+                                  sink.data_ptr(), _stream_handle(stream)))
 
 
 def _stream_handle(stream):
