@@ -36,6 +36,17 @@ METRIC = "ray samples/s & fps at 1080p/512^3; learned+lowprec vs plain at ≤1 L
 L2_FLUSH_BYTES = 256 << 20
 
 
+def reduce_over_ranks(values, op, device):
+    """Max or sum of ``values`` over the ranks of the default process group
+    (the values themselves without one)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -240,14 +251,9 @@ def run_ours(args, rank, world, local_rank):
     learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
     serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
-    # max over ranks
-    vals = torch.tensor([dev_ms, e2e_ms, t_wall], dtype=torch.float64, device=dev)
-    tot = torch.tensor([float(n_samp)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.SUM)
-    dev_ms, e2e_ms, t_wall = (float(v) for v in vals.tolist())
-    all_samp = float(tot.item())
+    # times: max over ranks; samples: sum over ranks (whole-job throughput)
+    dev_ms, e2e_ms, t_wall = reduce_over_ranks([dev_ms, e2e_ms, t_wall], "max", dev)
+    (all_samp,) = reduce_over_ranks([float(n_samp)], "sum", dev)
     if rank != 0:
         return None
 
@@ -325,12 +331,14 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
             ds.launch(prepared_f32[j], stream)
             ref_imgs.append(fb_f32.clone())
     torch.cuda.synchronize()
+    read_bytes = sum(t.numel() * t.element_size() for t in ds.data)   # the sources, read once
     for fmt in ("f32", "bf16", "f16", "e4m3"):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pv = ds.pack(fmt, stream=stream)      # allocates the copy (untimed)
         torch.cuda.synchronize()
         flush.zero_()
         e0.record(stream)
-        pv = ds.pack(fmt, stream=stream)
+        pv.repack(stream=stream)              # the per-time-step conversion
         e1.record(stream)
         torch.cuda.synchronize()
         pack_ms = e0.elapsed_time(e1)
@@ -362,7 +370,9 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
         ms = sum(a.elapsed_time(b) for a, b in ev)
         ns = sum(samples[(args.warmup + i) % n_cam] for i in range(steps))
         out[fmt] = {"samples_per_s": ns / (ms * 1e-3), "ms_per_frame": ms / steps,
-                    "pack_ms": pack_ms, "bytes": int(pv.data.numel()) +
+                    "pack_ms": pack_ms,
+                    "pack_gb_per_s": (read_bytes + pv.data.numel()) / (pack_ms * 1e-3) / 1e9,
+                    "bytes": int(pv.data.numel()) +
                     (int(pv.scales.numel()) * 4 if pv.scales is not None else 0),
                     "lsb_vs_f32_mean": lsb_sum / max(1, npx), "lsb_vs_f32_max": lsb_max,
                     "steps": steps}

@@ -521,7 +521,9 @@ class DeviceScene:
                              scales.data_ptr() if scales is not None else None, sb.value,
                              C.byref(out), _stream_handle(stream)))
         srcs = [s for i, s in enumerate(range(len(sc.sources))) if (mask >> i) & 1]
-        return PackedVolume(self, out, data, scales, srcs)
+        pv = PackedVolume(self, out, data, scales, srcs)
+        pv.mask, pv.dtype = mask, dtype
+        return pv
 
 
 class PackedVolume:
@@ -534,6 +536,20 @@ class PackedVolume:
         self.chains = (Chain * n)(*[ds.chains[i] for i in src_index])
         self.weights = (C.c_float * n)(*[ds.weights[i] for i in src_index])
         self.luts = ds.luts[src_index].contiguous()
+
+    def repack(self, stream=None):
+        """Pack the scene's current source data again into this copy's buffers
+        (the per-time-step refresh; allocates nothing)."""
+        sc = self.ds.scene
+        n = (C.c_int64 * 3)(*[int(v) for v in sc.n])
+        out = Packed()
+        check(load().isaac_pack(self.ds.sources, len(sc.sources), self.mask, C.cast(n, C.c_void_p),
+                                DTYPES[self.dtype], self.data.data_ptr(), self.data.numel(),
+                                self.scales.data_ptr() if self.scales is not None else None,
+                                self.scales.numel() * 4 if self.scales is not None else 0,
+                                C.byref(out), _stream_handle(stream)))
+        self.desc = out
+        return self
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
                 lanes=None):

@@ -33,3 +33,38 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = _run(1, 2)
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def _ranks(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        mx = bench.reduce_over_ranks([1.0 + rank, 10.0 - rank, 0.5], "max", "cpu")
+        sm = bench.reduce_over_ranks([float(100 * (rank + 1))], "sum", "cpu")
+        out.put((rank, mx, sm))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_over_ranks_gloo_world2():
+    """The bench's multi-rank reduction (max of times, sum of samples) on two
+    CPU ranks over gloo."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_ranks, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, mx, sm in got:
+        assert mx == [2.0, 10.0, 0.5] and sm == [300.0]
