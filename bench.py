@@ -248,6 +248,7 @@ def run_ours(args, rank, world, local_rank):
     variants = {} if args.no_variants else \
         run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
     iso = None if args.no_variants else run_iso(args, ds, cams, stream, flush)
+    comp = None if args.no_variants else run_composite(args, dev, stream, flush)
     learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
     serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
@@ -308,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "variants": variants,
         "iso": iso,
+        "composite": comp,
         "learned": learned,
         "serving": serving,
     }
@@ -419,6 +421,41 @@ def run_iso(args, ds, cams, stream, flush):
     return {"iso": iso, "ms_per_frame": ms, "fps": 1e3 / ms,
             "samples_per_frame": per_frame, "samples_per_s": per_frame / (ms * 1e-3),
             "hit_pixels_per_frame": hits / len(cams), "steps": steps}
+
+
+def run_composite(args, dev, stream, flush, n_layers=8, W=1920, H=1080):
+    """Sort-last compositing (isaac_composite) of n_layers 1080p partial images
+    (premultiplied RGBA32 + depth, seeded): time per composite and its bytes
+    (n_layers * 20 B read + 20 B written per pixel) against the HBM peak."""
+    import torch
+    from paper_1611_09048_b300 import isaac
+    g = torch.Generator(device=dev).manual_seed(11)
+    layers = []
+    for _ in range(n_layers):
+        a = torch.rand((H, W, 1), device=dev, generator=g) * 0.5
+        c = torch.cat([torch.rand((H, W, 3), device=dev, generator=g) * a, a], -1).contiguous()
+        d = torch.rand((H, W), device=dev, generator=g) * 1000.0
+        layers.append((c, d))
+    out8 = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+    out32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        isaac.composite(layers, out=out8, rgba32=out32, stream=stream)
+    steps = max(8, min(args.steps, 32))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            isaac.composite(layers, out=out8, rgba32=out32, stream=stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    nbytes = W * H * (n_layers * 20 + 20)
+    peak, kind = _peaks()
+    return {"layers": n_layers, "width": W, "height": H, "ms": ms,
+            "gb_per_s": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+            "peak_kind": kind, "bytes_per_pixel": n_layers * 20 + 20}
 
 
 def run_learned(args, dev, stream, flush):

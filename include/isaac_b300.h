@@ -26,7 +26,7 @@
 extern "C" {
 #endif
 
-#define ISAAC_ABI_VERSION 1
+#define ISAAC_ABI_VERSION 2
 #define ISAAC_MAX_SOURCES 8   /* sources described per call */
 #define ISAAC_MAX_ACTIVE 4    /* sources rendered per call (active_mask bits) */
 #define ISAAC_MAX_FUNCTORS 8  /* functors per chain */
@@ -131,6 +131,11 @@ typedef struct {
      * of an array of ceil((nx+2)(ny+2)(nz+2)/32) words.  Bits are OR-ed in;
      * the caller clears the array.  Measurement aid (slower path). */
     uint32_t *touched;
+    /* optional: width*height floats, the distance along the pixel's ray (unit
+     * direction, from the near plane) to its first sample on the global grid,
+     * +inf where it has none: the per-pixel visibility key of sort-last
+     * compositing (isaac_composite). */
+    float *depth;
 } isaac_framebuffer;
 
 /*
@@ -532,7 +537,25 @@ int isaac_server_destroy(isaac_server *server);
  * NULL, NULL stops it; one NULL and one event is ISAAC_EINVAL. */
 int isaac_time_march(void *start_event, void *stop_event);
 
-/* Measurement aid (no counterpart in the paper): read `bytes` of device
+/*
+ * isaac_composite -- sort-last compositing of partial images (Sec. 3.4: the
+ * nodes' images of their sub-volumes are merged in visibility order; the
+ * paper uses IceT over MPI).  layers_rgba32 / layers_depth: host arrays of
+ * n_layers (1..16) device pointers to the rgba32 and depth outputs of frames
+ * of disjoint local boxes of one global volume, rendered with the same camera
+ * and a zero background.  Per pixel the layers are taken front to back by
+ * depth (ties keep layer order) and merged with the over operator
+ * C += (1-A) c, A += (1-A) a; the background bg (host, 4 floats) is blended
+ * behind the result, which goes to rgba8 (required) and rgba32 (optional),
+ * both device, width*height pixels.  With early termination off the result
+ * equals the frame of the whole volume up to FP32 rounding (one global
+ * sample grid); with it, each layer terminates on its own.
+ */
+int isaac_composite(const float *const *layers_rgba32, const float *const *layers_depth,
+                    int32_t n_layers, int32_t width, int32_t height, const float *bg,
+                    uint8_t *rgba8, float *rgba32, void *stream);
+
+/* Measurement aid (no counterpart in the paper): read `bytes` of device/* Measurement aid (no counterpart in the paper): read `bytes` of device
  * memory at `buf` (16-byte aligned) `passes` times with 16-byte loads cached
  * in L2 only; sink: device memory of 1024 uint32 the kernel may write.  The
  * bench times it on a buffer of half the L2 for the L2 bandwidth it reports. */

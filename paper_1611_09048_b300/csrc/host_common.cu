@@ -354,6 +354,8 @@ int prepare_fb(const isaac_framebuffer *fb, KParams &p)
     p.nsamp = fb->nsamples;
     if (((uintptr_t)fb->touched) % 4) return fail(ISAAC_EINVAL, "fb->touched is misaligned");
     p.touched = reinterpret_cast<unsigned *>(fb->touched);
+    if (((uintptr_t)fb->depth) % 4) return fail(ISAAC_EINVAL, "fb->depth is misaligned");
+    p.depth = fb->depth;
     return ISAAC_OK;
 }
 

@@ -127,6 +127,7 @@ struct KParams {
     uchar4 *fb8;
     float4 *fb32;
     int *nsamp;
+    float *depth;                    // optional: distance to the ray's first sample (+inf: none)
     unsigned *touched;               // optional footprint bitmap over [-1, n]^3
     WsCounters *ctr;                 // workspace counters
     RayRec *rays;                    // workspace ray list
@@ -488,7 +489,7 @@ __device__ __forceinline__ double drcp(double x)
     return r;
 }
 
-__device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
+__device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, float *t_first = nullptr)
 {
     RayRec r;
     r.nsteps = 0;
@@ -562,6 +563,7 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py)
     const long long ke = (long long)ceil((tout - t0) * p.inv_step_d);
     if (ke <= kf) return r;
     const double tf = t0 + (double)kf * p.step_d;
+    if (t_first) *t_first = (float)tf;
     r.ex = (float)(fma(tf, d[0], o[0]) - p.llo[0]);
     r.ey = (float)(fma(tf, d[1], o[1]) - p.llo[1]);
     r.ez = (float)(fma(tf, d[2], o[2]) - p.llo[2]);
@@ -598,6 +600,7 @@ static __global__ void k_fill_background(const __grid_constant__ KParams p)
         const int y = (int)(i / (size_t)p.W), x = (int)(i - (size_t)y * p.W);
         if (x >= p.rx0 && x < p.rx1 && y >= p.ry0 && y < p.ry1) continue;
         write_pixel(p, (int)i, 0.0f, 0.0f, 0.0f, 0.0f, 0);
+        if (p.depth) p.depth[i] = __int_as_float(0x7f800000);
     }
 }
 
@@ -613,7 +616,8 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
     const bool inside = px < p.rx1 && py < p.ry1;
     RayRec r;
     r.nsteps = 0;
-    if (inside) r = setup_ray(p, px, py);
+    float tf = 0.0f;
+    if (inside) r = setup_ray(p, px, py, &tf);
     const bool hit = inside && r.nsteps > 0;
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     unsigned base = 0;
@@ -624,6 +628,7 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
     } else if (inside) {
         write_pixel(p, py * p.W + px, 0.0f, 0.0f, 0.0f, 0.0f, 0);
     }
+    if (inside && p.depth) p.depth[py * p.W + px] = hit ? tf : __int_as_float(0x7f800000);
 }
 
 // ------------------------------------------------------------------ march

@@ -32,7 +32,7 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_mlp_forward", "isaac_mlp_train_step", "isaac_server_create",
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
            "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
-           "isaac_render_iso", "isaac_probe_read")
+           "isaac_render_iso", "isaac_probe_read", "isaac_composite")
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -69,7 +69,7 @@ class RenderOpts(C.Structure):
 
 class Framebuffer(C.Structure):
     _fields_ = [("rgba8", C.c_void_p), ("rgba32", C.c_void_p), ("nsamples", C.c_void_p),
-                ("touched", C.c_void_p)]
+                ("touched", C.c_void_p), ("depth", C.c_void_p)]
 
 
 class Packed(C.Structure):
@@ -211,6 +211,9 @@ def load(path: Optional[str] = None):
         lib.isaac_render_iso.argtypes = [C.POINTER(Source), C.POINTER(Chain), C.c_int32, C.c_void_p,
                                          C.c_void_p, C.POINTER(Camera), C.POINTER(Plane), C.c_int32,
                                          C.POINTER(RenderOpts), C.POINTER(Framebuffer), C.c_void_p]
+        lib.isaac_composite.restype = C.c_int
+        lib.isaac_composite.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.isaac_probe_read.restype = C.c_int
         lib.isaac_probe_read.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
         lib.isaac_time_march.restype = C.c_int
@@ -286,6 +289,23 @@ def time_march(start=None, stop=None):
                                   C.c_void_p(stop.cuda_event) if stop is not None else None))
 
 
+def composite(layers, bg=(0.0, 0.0, 0.0, 0.0), out=None, rgba32=None, stream=None):
+    """Sort-last compositing (isaac_composite) of ``layers``: a list of
+    (rgba32, depth) device tensors of shape (H, W, 4) and (H, W)."""
+    import torch
+    H, W = layers[0][1].shape
+    n = len(layers)
+    rp = (C.c_void_p * n)(*[l[0].data_ptr() for l in layers])
+    dp = (C.c_void_p * n)(*[l[1].data_ptr() for l in layers])
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=layers[0][0].device)
+    bga = (C.c_float * 4)(*[float(v) for v in bg])
+    check(load().isaac_composite(rp, dp, n, W, H, bga, out.data_ptr(),
+                                 rgba32.data_ptr() if rgba32 is not None else None,
+                                 _stream_handle(stream)))
+    return out, rgba32
+
+
 def probe_read(buf, passes, sink, stream=None):
     """Read device tensor ``buf`` ``passes`` times (isaac_probe_read)."""
     check(load().isaac_probe_read(buf.data_ptr(), buf.numel() * buf.element_size(), int(passes),
@@ -346,7 +366,7 @@ class DeviceScene:
         return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
-                touched=None, lanes=None):
+                touched=None, lanes=None, depth=None):
         """Marshal one frame's arguments (camera, opts, framebuffer) once; the
         returned tuple can be launched repeatedly with ``launch``."""
         sc = self.scene
@@ -355,7 +375,8 @@ class DeviceScene:
         planes, n_clip = make_planes(sc.clip)
         fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
                          nsamples.data_ptr() if nsamples is not None else None,
-                         touched.data_ptr() if touched is not None else None)
+                         touched.data_ptr() if touched is not None else None,
+                         depth.data_ptr() if depth is not None else None)
         opts = make_opts(sc, mask, lanes)
         keep = (cam, planes, fb, opts)
         return (self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
@@ -368,9 +389,10 @@ class DeviceScene:
         check(load().isaac_render(*args, _stream_handle(stream)))
 
     def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
-               mask=None, want_f32=False, want_nsamp=False, touched=None, lanes=None):
+               mask=None, want_f32=False, want_nsamp=False, touched=None, lanes=None,
+               depth=None):
         """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
-        as device tensors."""
+        as device tensors (``depth``: optional (H, W) float32 output)."""
         import torch
         W, H = self.scene.width, self.scene.height
         if out is None:
@@ -379,7 +401,7 @@ class DeviceScene:
             rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         if nsamples is None and want_nsamp:
             nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
-        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes), stream)
+        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes, depth), stream)
         return out, rgba32, nsamples
 
 

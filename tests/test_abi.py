@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version():
-    assert isaac.load().isaac_abi_version() == 1
+    assert isaac.load().isaac_abi_version() == 2
 
 
 def test_struct_sizes_match_header_layout():
@@ -43,6 +43,7 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(isaac.Functor) == 4 + 4 + 16
     assert C.sizeof(isaac.Chain) == 4 + 24 * isaac.MAX_FUNCTORS
     assert C.sizeof(isaac.Camera) == 256 + 8
+    assert C.sizeof(isaac.Framebuffer) == 5 * 8
     # 9 int64, step, interp, term_alpha, bg[4], active_mask, lanes_per_ray -> 108, 8-aligned
     assert C.sizeof(isaac.RenderOpts) == 112
 
@@ -255,3 +256,16 @@ def test_range_grid_and_skip_validate_before_any_launch():
                                C.byref(a["cam"]), None, 0, C.byref(a["opts"]), C.byref(a["fb"]),
                                FAKE, 15, 4, None)
     assert rc == isaac.EINVAL and "ranges holds 15" in lib.isaac_last_error().decode()
+
+
+def test_composite_validates_before_any_launch():
+    lib = isaac.load()
+    one = (C.c_void_p * 1)(FAKE)
+    bg = (C.c_float * 4)(0, 0, 0, 0)
+    assert lib.isaac_composite(one, one, 0, 4, 4, bg, FAKE, None, None) == isaac.EINVAL
+    assert lib.isaac_composite(one, one, 17, 4, 4, bg, FAKE, None, None) == isaac.EINVAL
+    bad = (C.c_void_p * 1)(FAKE + 4)
+    assert lib.isaac_composite(bad, one, 1, 4, 4, bg, FAKE, None, None) == isaac.EINVAL
+    assert "misaligned" in lib.isaac_last_error().decode()
+    nan = (C.c_float * 4)(float("nan"), 0, 0, 0)
+    assert lib.isaac_composite(one, one, 1, 4, 4, nan, FAKE, None, None) == isaac.EINVAL
