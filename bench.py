@@ -249,6 +249,7 @@ def run_ours(args, rank, world, local_rank):
         run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
     iso = None if args.no_variants else run_iso(args, ds, cams, stream, flush)
     comp = None if args.no_variants else run_composite(args, dev, stream, flush)
+    copy = None if args.no_variants else run_source_copy(args, ds, stream, flush)
     learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
     serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
@@ -310,6 +311,7 @@ def run_ours(args, rank, world, local_rank):
         "variants": variants,
         "iso": iso,
         "composite": comp,
+        "source_copy": copy,
         "learned": learned,
         "serving": serving,
     }
@@ -456,6 +458,42 @@ def run_composite(args, dev, stream, flush, n_layers=8, W=1920, H=1080):
     return {"layers": n_layers, "width": W, "height": H, "ms": ms,
             "gb_per_s": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak,
             "peak_kind": kind, "bytes_per_pixel": n_layers * 20 + 20}
+
+
+def run_source_copy(args, ds, stream, flush):
+    """Non-persistent sources (isaac_copy_source): copy every source of the
+    workload through its accessor (interior + one guard layer) into a buffer
+    of its own; time one copy of all sources and its bytes (4 B read + 4 B
+    written per copied element) against the HBM peak."""
+    import torch
+    from paper_1611_09048_b300 import isaac
+    n = ds.scene.n
+    srcs = [isaac.Source.from_buffer_copy(ds.sources[s]) for s in range(len(ds.scene.sources))]
+    bufs = [torch.empty(isaac.copy_bytes(n, d.f_dim, d.guard) // 4, dtype=torch.float32,
+                        device=ds.device) for d in srcs]
+
+    def copy_all():
+        for d, b in zip(srcs, bufs):
+            isaac.copy_source(d, n, b, stream)
+    for _ in range(3):
+        copy_all()
+    steps = max(4, min(args.steps, 16))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            copy_all()
+            b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    nbytes = 2 * sum(b.numel() * 4 for b in bufs)
+    peak, kind = _peaks()
+    del bufs
+    return {"sources": len(srcs), "copied_bytes": nbytes // 2, "ms": ms,
+            "gb_per_s": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+            "peak_kind": kind, "launches": len(srcs)}
 
 
 def run_learned(args, dev, stream, flush):

@@ -544,7 +544,7 @@ int isaac_time_march(void *start_event, void *stop_event);
  * n_layers (1..16) device pointers to the rgba32 and depth outputs of frames
  * of disjoint local boxes of one global volume, rendered with the same camera
  * and a zero background.  Per pixel the layers are taken front to back by
- * depth (ties keep layer order) and merged with the over operator
+ * depth (ties keep layer order; a NaN depth counts as +inf) and merged with the over operator
  * C += (1-A) c, A += (1-A) a; the background bg (host, 4 floats) is blended
  * behind the result, which goes to rgba8 (required) and rgba32 (optional),
  * both device, width*height pixels.  With early termination off the result
@@ -554,6 +554,44 @@ int isaac_time_march(void *start_event, void *stop_event);
 int isaac_composite(const float *const *layers_rgba32, const float *const *layers_depth,
                     int32_t n_layers, int32_t width, int32_t height, const float *bg,
                     uint8_t *rgba8, float *rgba32, void *stream);
+
+/*
+ * The rest of the source contract (Sec. 3.2): the per-source update callback
+ * and sources whose memory is not persistent.
+ *
+ * isaac_set_update_hook -- installs fn for the calling host thread (NULL
+ * removes it; returns ISAAC_OK).  While set, these calls made by that thread
+ * call fn(s, enabled, user) for every source s = 0 .. n_sources-1 in order,
+ * enabled = bit s of the active mask, before they read any source descriptor:
+ * isaac_render, isaac_trace, isaac_render_learned, isaac_render_skip,
+ * isaac_render_iso, isaac_opacity_grid, isaac_range_grid, isaac_pack and
+ * isaac_server_create.  The render calls validate the camera and options
+ * first; a call that fails there, or whose n_sources is outside
+ * 1..ISAAC_MAX_SOURCES, calls no hook.  The hook is where an application
+ * passes per-frame information to its sources or (re)computes a derived field:
+ * it may enqueue device work on the frame's stream and rewrite, through its
+ * own pointer, the descriptor array the caller passed (the library reads it
+ * only after the hooks return).  isaac_render_noalloc calls no hook: its host
+ * path does nothing but validate and launch.
+ *
+ * isaac_copy_source -- for a source whose memory is not persistent (say one
+ * scratch buffer that several derived fields take turns in): copies, through
+ * the accessor (strides, component stride, guards), every cell a frame can
+ * read -- the interior and, when the source has guard cells, one guard layer
+ * -- into dst, and describes the copy in *out; a frame renders *out exactly
+ * like the original.  dst: device memory, 16-byte aligned, dst_bytes >=
+ * 4 f_dim (n0+2g)(n1+2g)(n2+2g) with g = min(guard, 1), cells x fastest with
+ * their components adjacent; the caller owns it.  The copy is enqueued on
+ * `stream`: work that the application orders after it on that stream (for
+ * example the next source's update) may overwrite the original.  Errors:
+ * ISAAC_EINVAL (NULL pointers, n outside 1..2^20, misaligned dst, a
+ * descriptor the renderer would reject), ISAAC_EGUARD (the reachable cells
+ * leave the extent), ISAAC_ENOMEM (dst too small); nothing is enqueued then.
+ */
+typedef void (*isaac_update_fn)(int32_t source, int32_t enabled, void *user);
+int isaac_set_update_hook(isaac_update_fn fn, void *user);
+int isaac_copy_source(const isaac_source *src, const int64_t n[3], void *dst, int64_t dst_bytes,
+                      isaac_source *out, void *stream);
 
 /* Measurement aid (no counterpart in the paper): read `bytes` of device/* Measurement aid (no counterpart in the paper): read `bytes` of device
  * memory at `buf` (16-byte aligned) `passes` times with 16-byte loads cached

@@ -25,6 +25,10 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
                    int elem, KSource &ks, unsigned *nib, bool *wide);
 int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
 int prepare_fb(const isaac_framebuffer *fb, KParams &p);
+// Calls the calling thread's update hook (isaac_set_update_hook), if any, for
+// every source in order (with its active bit), before an entry point reads the
+// descriptors.
+void update_sources(int32_t n_sources, uint32_t active_mask);
 
 // Validate the sources of isaac_render and fill their part of KParams.
 int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,

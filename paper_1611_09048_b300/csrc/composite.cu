@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "common.h"
 #include "raycast.cuh"
@@ -21,32 +22,49 @@ struct KComposite {
     float4 *out32;
 };
 
-// One thread per pixel: the layers' depths in registers, an insertion sort of
-// their indices (stable: equal depths keep layer order), then the over
-// operator front to back.  Reads n * 20 bytes and writes 4 (+16) per pixel.
+// One thread per pixel, N = the number of layers (compile time, so every
+// array lives in registers).  All 5N loads are issued first.  The rank of
+// layer l is the number of layers m whose key (depth, m) is smaller (a NaN
+// depth counts as +inf), a permutation, so equal depths keep layer order.
+// The over operator then runs front to back in rank order, each step picking
+// its layer by register selects.  Reads N * 20 bytes and writes 4 (+16) per
+// pixel.
+template <int N>
 static __global__ void __launch_bounds__(256) k_composite(const __grid_constant__ KComposite p)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.npix;
          i += (long long)gridDim.x * blockDim.x) {
-        float d[kMaxLayers];
-        int order[kMaxLayers];
-        for (int l = 0; l < p.n; ++l) {
+        float d[N];
+        float4 c[N];
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
             d[l] = __ldg(p.depth[l] + i);
-            order[l] = l;
-            for (int m = l; m > 0 && d[order[m - 1]] > d[order[m]]; --m) {
-                const int t = order[m - 1];
-                order[m - 1] = order[m];
-                order[m] = t;
-            }
+            c[l] = __ldg(p.rgba[l] + i);
+        }
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+            if (d[l] != d[l]) d[l] = __int_as_float(0x7f800000);
+        int rank[N];
+#pragma unroll
+        for (int l = 0; l < N; ++l) {
+            int r = 0;
+#pragma unroll
+            for (int m = 0; m < N; ++m)
+                if (m != l) r += (d[m] < d[l] || (m < l && d[m] == d[l])) ? 1 : 0;
+            rank[l] = r;
         }
         float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-        for (int m = 0; m < p.n; ++m) {
-            const float4 c = __ldg(p.rgba[order[m]] + i);
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            float4 q = c[0];
+#pragma unroll
+            for (int l = 1; l < N; ++l)
+                if (rank[l] == r) q = c[l];
             const float T = 1.0f - A;
-            C0 = fmaf(T, c.x, C0);
-            C1 = fmaf(T, c.y, C1);
-            C2 = fmaf(T, c.z, C2);
-            A = fmaf(T, c.w, A);
+            C0 = fmaf(T, q.x, C0);
+            C1 = fmaf(T, q.y, C1);
+            C2 = fmaf(T, q.z, C2);
+            A = fmaf(T, q.w, A);
         }
         const float T = 1.0f - A;
         const float o0 = fmaf(T, p.bg[0], C0), o1 = fmaf(T, p.bg[1], C1);
@@ -54,6 +72,15 @@ static __global__ void __launch_bounds__(256) k_composite(const __grid_constant_
         p.out8[i] = make_uchar4(quant8(o0), quant8(o1), quant8(o2), quant8(o3));
         if (p.out32) p.out32[i] = make_float4(o0, o1, o2, o3);
     }
+}
+
+using CompositeFn = void (*)(KComposite);
+
+template <int... Ns>
+static CompositeFn composite_fn(int n, std::integer_sequence<int, Ns...>)
+{
+    static const CompositeFn table[] = {k_composite<Ns + 1>...};
+    return table[n - 1];
 }
 
 }  // namespace isaac
@@ -94,6 +121,7 @@ extern "C" int isaac_composite(const float *const *layers_rgba32, const float *c
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
     const long long blocks = std::max(1LL, std::min((p.npix + 255) / 256, (long long)sms * 8));
-    k_composite<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+    composite_fn(n_layers, std::make_integer_sequence<int, kMaxLayers>{})
+        <<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
     return check_cuda("isaac_composite launch");
 }

@@ -365,6 +365,7 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
     if (grid_len < cells)
         return fail(ISAAC_ENOMEM, "grid holds %lld values, %lld needed", (long long)grid_len, cells);
     if (cells > 0x7fffffffLL) return fail(ISAAC_ENOTSUP, "too many macro cells");
+    update_sources(n_sources, opts->active_mask);
     for (int s = 0; s < n_sources; ++s) {
         if (!((opts->active_mask >> s) & 1u)) continue;
         if (p.nact == ISAAC_MAX_ACTIVE)
@@ -424,6 +425,7 @@ extern "C" int isaac_range_grid(const isaac_source *sources, int32_t n_sources,
     const long long cells = (long long)r.gx * r.gy * r.gz;
     KSource ks[ISAAC_MAX_SOURCES];
     int nact = 0, slots = 0;
+    update_sources(n_sources, opts->active_mask);
     for (int s = 0; s < n_sources; ++s) {
         if (!((opts->active_mask >> s) & 1u)) continue;
         if (nact == ISAAC_MAX_ACTIVE) return fail(ISAAC_ENOTSUP, "more than %d active sources", ISAAC_MAX_ACTIVE);

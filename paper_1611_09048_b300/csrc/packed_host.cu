@@ -98,6 +98,7 @@ extern "C" int isaac_pack(const isaac_source *sources, int32_t n_sources, uint32
                           float *scales, int64_t scale_bytes, isaac_packed *out, void *stream)
 {
     clear_error();
+    update_sources(n_sources, mask);
     isaac_packed L;
     int64_t need_d = 0, need_s = 0;
     int rc = layout_of(sources, n_sources, mask, n, dtype, &L, &need_d, &need_s);

@@ -221,6 +221,7 @@ extern "C" int isaac_render(const isaac_source *sources, const isaac_chain *chai
     int nact = 0;
     unsigned sig = 0;
     bool wide = false;
+    update_sources(n_sources, opts->active_mask);
     rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, p, &nact, &sig, &wide);
     if (rc) return rc;
     rc = prepare_fb(fb, p);
@@ -252,6 +253,7 @@ static int render_mode(const isaac_source *sources, const isaac_chain *chains, i
     int nact = 0;
     unsigned sig = 0;
     bool wide = false;
+    update_sources(n_sources, opts->active_mask);
     rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, p, &nact, &sig, &wide);
     if (rc) return rc;
     rc = prepare_fb(fb, p);
@@ -331,6 +333,7 @@ extern "C" int isaac_render_skip(const isaac_source *sources, const isaac_chain 
     int nact = 0;
     unsigned sig = 0;
     bool wide = false;
+    update_sources(n_sources, opts->active_mask);
     rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, p, &nact, &sig, &wide);
     if (rc) return rc;
     rc = prepare_fb(fb, p);
@@ -385,6 +388,7 @@ extern "C" int isaac_render_iso(const isaac_source *sources, const isaac_chain *
     int nact = 0;
     unsigned sig = 0;
     bool wide = false;
+    update_sources(n_sources, opts->active_mask);
     rc = prepare_sources(sources, chains, n_sources, luts, ones, opts, p, &nact, &sig, &wide);
     if (rc) return rc;
     rc = prepare_fb(fb, p);

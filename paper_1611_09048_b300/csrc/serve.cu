@@ -462,6 +462,7 @@ extern "C" int isaac_server_create(const isaac_source *sources, const isaac_chai
     const bool packed = vol != nullptr;
     if (!packed) {
         bool wide = false;
+        update_sources(n_sources, opts->active_mask);
         rc = prepare_sources(sources, chains, n_sources, luts, weights, opts, s->base, &s->nact, &sig, &wide);
         if (rc) return rc;
         if (wide) return fail(ISAAC_ENOTSUP, "the server needs 32-bit element offsets");

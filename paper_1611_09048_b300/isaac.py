@@ -32,7 +32,11 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_mlp_forward", "isaac_mlp_train_step", "isaac_server_create",
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
            "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
-           "isaac_render_iso", "isaac_probe_read", "isaac_composite")
+           "isaac_render_iso", "isaac_probe_read", "isaac_composite", "isaac_copy_source",
+           "isaac_set_update_hook")
+
+# fn(source, enabled, user) of isaac_set_update_hook
+UPDATE_FN = C.CFUNCTYPE(None, C.c_int32, C.c_int32, C.c_void_p)
 
 # lanes per ray used when a call does not pass one (0 = the library chooses)
 LANES_PER_RAY = int(os.environ.get("ISAAC_LANES_PER_RAY", "0"))
@@ -216,6 +220,11 @@ def load(path: Optional[str] = None):
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.isaac_probe_read.restype = C.c_int
         lib.isaac_probe_read.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
+        lib.isaac_copy_source.restype = C.c_int
+        lib.isaac_copy_source.argtypes = [C.POINTER(Source), C.POINTER(C.c_int64), C.c_void_p,
+                                          C.c_int64, C.POINTER(Source), C.c_void_p]
+        lib.isaac_set_update_hook.restype = C.c_int
+        lib.isaac_set_update_hook.argtypes = [UPDATE_FN, C.c_void_p]
         lib.isaac_time_march.restype = C.c_int
         lib.isaac_time_march.argtypes = [C.c_void_p, C.c_void_p]
         lib.isaac_last_error.restype = C.c_char_p
@@ -306,6 +315,40 @@ def composite(layers, bg=(0.0, 0.0, 0.0, 0.0), out=None, rgba32=None, stream=Non
     return out, rgba32
 
 
+_update_keep = {}
+
+
+def set_update_hook(fn):
+    """Install ``fn(source, enabled)`` as this thread's per-source update
+    callback (isaac_set_update_hook); None removes it."""
+    import threading
+    tid = threading.get_ident()
+    if fn is None:
+        check(load().isaac_set_update_hook(UPDATE_FN(), None))
+        _update_keep.pop(tid, None)
+        return
+    cb = UPDATE_FN(lambda s, en, _u: fn(int(s), bool(en)))
+    _update_keep[tid] = cb            # the C side keeps only the pointer
+    check(load().isaac_set_update_hook(cb, None))
+
+
+def copy_bytes(n, fdim, guard):
+    """Bytes isaac_copy_source writes for an n-cell source."""
+    g = 1 if guard >= 1 else 0
+    return 4 * fdim * (n[0] + 2 * g) * (n[1] + 2 * g) * (n[2] + 2 * g)
+
+
+def copy_source(src: "Source", n, dst, stream=None) -> "Source":
+    """Copy a (non-persistent) source into device tensor ``dst``
+    (isaac_copy_source); returns the descriptor of the copy."""
+    out = Source()
+    nn = (C.c_int64 * 3)(*[int(v) for v in n])
+    check(load().isaac_copy_source(C.byref(src), nn, dst.data_ptr(),
+                                   dst.numel() * dst.element_size(), C.byref(out),
+                                   _stream_handle(stream)))
+    return out
+
+
 def probe_read(buf, passes, sink, stream=None):
     """Read device tensor ``buf`` ``passes`` times (isaac_probe_read)."""
     check(load().isaac_probe_read(buf.data_ptr(), buf.numel() * buf.element_size(), int(passes),
@@ -354,6 +397,17 @@ class DeviceScene:
         d.comp_stride = int(src.cstride)
         d.f_dim = int(src.fdim)
         d.guard = int(src.guard)
+
+    def copy_source(self, s, stream=None):
+        """Replace source ``s`` by a copy made through its accessor
+        (isaac_copy_source); the copy's buffer is kept with the scene."""
+        import torch
+        src = self.sources[s]
+        nb = copy_bytes(self.scene.n, src.f_dim, src.guard)
+        buf = torch.empty(nb // 4, dtype=torch.float32, device=self.device)
+        self.sources[s] = copy_source(src, self.scene.n, buf, stream)
+        self.data.append(buf)
+        return buf
 
     def set_luts(self, luts):
         self.luts.copy_(self.luts.new_tensor(np.asarray(luts, np.float32)).reshape(self.luts.shape))

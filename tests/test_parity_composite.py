@@ -88,3 +88,46 @@ def test_depth_is_first_sample_distance(cuda_ok):
     assert both.sum() > 100
     assert np.all(deps[1][both] < deps[0][both])     # the camera is on the +x side
     assert np.isinf(deps[0]).any()
+
+
+def _over_numpy(L, bg):
+    D = np.stack([np.where(np.isnan(d), np.inf, d) for _, d in L])
+    order = np.argsort(D, axis=0, kind="stable")
+    H, W = D.shape[1:]
+    C = np.zeros((H, W, 3), np.float32)
+    A = np.zeros((H, W, 1), np.float32)
+    S = np.stack([x for x, _ in L]).astype(np.float32)
+    for m in range(len(L)):
+        c = np.take_along_axis(S, order[m][None, ..., None], 0)[0]
+        C = (1 - A) * c[..., :3] + C
+        A = (1 - A) * c[..., 3:4] + A
+    return np.concatenate([C + (1 - A) * np.asarray(bg[:3], np.float32),
+                           A + (1 - A) * np.float32(bg[3])], -1)
+
+
+@pytest.mark.parametrize("n_layers", [1, 2, 5, 8, 16])
+def test_ties_nan_and_every_layer_count(cuda_ok, n_layers):
+    """Depths drawn from a few values (many ties), with NaN and +inf mixed in,
+    at every layer count the kernel is specialised for: the result equals the
+    over operator in stable depth order (NaN as +inf), on a ragged image."""
+    import torch
+    H, W = 37, 53
+    rng = np.random.default_rng(100 + n_layers)
+    L = []
+    for _ in range(n_layers):
+        a = rng.random((H, W, 1), np.float32) * 0.6
+        c = np.concatenate([rng.random((H, W, 3), np.float32) * a, a], -1)
+        d = rng.choice(np.array([1.0, 2.0, 3.0, np.inf, np.nan], np.float32), size=(H, W))
+        L.append((c, d))
+    bg = (0.2, 0.1, 0.4, 1.0)
+    layers = [(torch.from_numpy(np.ascontiguousarray(c)).cuda(),
+               torch.from_numpy(np.ascontiguousarray(d)).cuda()) for c, d in L]
+    out8 = torch.empty((H, W, 4), dtype=torch.uint8, device="cuda")
+    out32 = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    isaac.composite(layers, bg=bg, out=out8, rgba32=out32)
+    torch.cuda.synchronize()
+    want = _over_numpy(L, bg)
+    got = out32.cpu().numpy()
+    assert np.abs(got - want).max() <= 2e-6
+    q = np.minimum(255, np.floor(255 * np.clip(want.astype(np.float64), 0, 1) + 0.5)).astype(int)
+    assert np.abs(out8.cpu().numpy().astype(int) - q).max() <= 1
