@@ -295,6 +295,9 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
         p.llo[a] = (double)opt->offset[a];
         p.lhi[a] = (double)(opt->offset[a] + opt->n[a]);
     }
+    p.local_is_global = 1;
+    for (int a = 0; a < 3; ++a)
+        if (opt->offset[a] != 0 || opt->n[a] != gn[a]) p.local_is_global = 0;
     p.step = opt->step;
     p.step_d = (double)opt->step;
     p.inv_step_d = 1.0 / p.step_d;
@@ -309,14 +312,37 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
     p.term = opt->term_alpha;
     for (int c = 0; c < 4; ++c) p.bg[c] = opt->bg[c];
 
-    // Screen rectangle: project the 8 local-box corners; a pixel whose ray can
-    // reach the box lies in their bounding box (one-pixel margin for rounding).
+    // Screen rectangle: project the 8 corners of the local box, cut by the
+    // axis-aligned clip planes (others are ignored, which only widens it); a
+    // pixel whose ray can reach a sample lies in their bounding box (one-pixel
+    // margin for rounding).  A box cut to nothing keeps one face, so rays that
+    // graze it stay inside the margin.
+    double blo[3], bhi[3];
+    for (int a = 0; a < 3; ++a) {
+        blo[a] = p.llo[a];
+        bhi[a] = p.lhi[a];
+    }
+    for (int i = 0; i < n_clip; ++i) {
+        const double *pl = p.clip[i];
+        int axis = -1, nonzero = 0;
+        for (int a = 0; a < 3; ++a)
+            if (pl[a] != 0.0) {
+                axis = a;
+                ++nonzero;
+            }
+        if (nonzero != 1) continue;
+        const double c = -pl[3] / pl[axis];    // keep x_axis >= c (normal > 0) or <= c
+        if (pl[axis] > 0.0)
+            blo[axis] = std::fmin(std::fmax(blo[axis], c), bhi[axis]);
+        else
+            bhi[axis] = std::fmax(std::fmin(bhi[axis], c), blo[axis]);
+    }
     bool full = false;
     double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     for (int c = 0; c < 8; ++c) {
-        const double w[3] = {((c & 1) ? p.lhi[0] : p.llo[0]) - p.half_g[0],
-                             ((c & 2) ? p.lhi[1] : p.llo[1]) - p.half_g[1],
-                             ((c & 4) ? p.lhi[2] : p.llo[2]) - p.half_g[2]};
+        const double w[3] = {((c & 1) ? bhi[0] : blo[0]) - p.half_g[0],
+                             ((c & 2) ? bhi[1] : blo[1]) - p.half_g[1],
+                             ((c & 4) ? bhi[2] : blo[2]) - p.half_g[2]};
         double v[4];
         for (int r = 0; r < 4; ++r) v[r] = M[r] * w[0] + M[4 + r] * w[1] + M[8 + r] * w[2] + M[12 + r];
         if (!(v[3] > 1e-12)) {

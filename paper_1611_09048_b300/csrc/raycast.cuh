@@ -111,6 +111,7 @@ struct KParams {
     float term;
     float bg[4];
     int n_clip;
+    int local_is_global;             // the local box is the global box (no domain split)
     int nx, ny, nz;
     int W, H;
     int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
@@ -479,13 +480,14 @@ struct ZeroCopyShader {
 // FP64 reciprocal from the FP32 one and two Newton steps (error ~1 ulp of
 // double, against some twenty FP64 operations for a division); operands
 // outside the FP32 range take the division.
+template <int NEWTON = 2>
 __device__ __forceinline__ double drcp(double x)
 {
     const float rf = __frcp_rn((float)x);
     if (!(fabsf(rf) < 1.0e38f) || !(fabsf(rf) > 1.0e-37f)) return 1.0 / x;
     double r = (double)rf;
-    r = fma(r, fma(-x, r, 1.0), r);
-    r = fma(r, fma(-x, r, 1.0), r);
+#pragma unroll
+    for (int i = 0; i < NEWTON; ++i) r = fma(r, fma(-x, r, 1.0), r);
     return r;
 }
 
@@ -526,22 +528,33 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, fl
           isfinite(d[1]) && isfinite(d[2])))
         return r;
 
+    // Slab intervals of the global box (t0 = its entry: the origin of the
+    // sample grid) and of the local box.  The reciprocals take one Newton step
+    // (relative error ~2^-46, far below the tie margin of the sample decisions);
+    // without a domain split the two boxes coincide and one pass serves both.
     double t0 = 0.0, tg1 = 1e300, tl0 = 0.0, tout = 1e300;
     bool miss = false;
+    const bool one_box = p.local_is_global != 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (d[a] != 0.0) {
-            const double inv = drcp(d[a]);
+            const double inv = drcp<1>(d[a]);
             double ta = (0.0 - o[a]) * inv, tb = (p.gn[a] - o[a]) * inv;
             t0 = fmax(t0, fmin(ta, tb));
             tg1 = fmin(tg1, fmax(ta, tb));
-            ta = (p.llo[a] - o[a]) * inv;
-            tb = (p.lhi[a] - o[a]) * inv;
-            tl0 = fmax(tl0, fmin(ta, tb));
-            tout = fmin(tout, fmax(ta, tb));
+            if (!one_box) {
+                ta = (p.llo[a] - o[a]) * inv;
+                tb = (p.lhi[a] - o[a]) * inv;
+                tl0 = fmax(tl0, fmin(ta, tb));
+                tout = fmin(tout, fmax(ta, tb));
+            }
         } else if (o[a] < p.llo[a] || o[a] >= p.lhi[a]) {
             miss = true;
         }
+    }
+    if (one_box) {
+        tl0 = t0;
+        tout = tg1;
     }
     if (t0 >= tg1) miss = true;
     double tin = fmax(t0, tl0);
@@ -550,9 +563,9 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, fl
         const double s = fma(pl[0], o[0], fma(pl[1], o[1], fma(pl[2], o[2], pl[3])));
         const double rr = fma(pl[0], d[0], fma(pl[1], d[1], pl[2] * d[2]));
         if (rr > 0.0) {
-            tin = fmax(tin, -s * drcp(rr));
+            tin = fmax(tin, -s * drcp<1>(rr));
         } else if (rr < 0.0) {
-            tout = fmin(tout, -s * drcp(rr));
+            tout = fmin(tout, -s * drcp<1>(rr));
         } else if (s < 0.0) {
             miss = true;
         }

@@ -189,3 +189,22 @@ def test_pic_256_1080p_sampled(cuda_ok):
     r = oracle.render(sc, pixels=pix)
     rep = compare(g32, g8, gns, r, sel=pix)
     assert_parity(rep, 2e-3, "pic 256 1080p sampled")
+
+
+@pytest.mark.parametrize("clip", [
+    [(1.0, 0.0, 0.0, -16.0), (0.0, 0.0, -1.0, 9.0)],          # keep x >= 16 and z <= 9
+    [(-2.0, 0.0, 0.0, 10.0), (0.3, -0.5, 0.2, 3.0)],          # keep x <= 5, plus an oblique plane
+    [(0.0, 1.0, 0.0, -24.0)],                                 # keep y >= 24: one face only
+    [(0.0, 0.0, 1.0, -40.0)],                                 # keep z >= 40: nothing
+])
+def test_axis_aligned_clip_planes_shrink_the_rectangle(cuda_ok, clip):
+    """Axis-aligned clip planes cut the box whose projection bounds the pixels
+    that get a ray; every frame still equals the oracle's, pixel for pixel
+    (the pixels cut away are background on both sides)."""
+    sc = dataclasses.replace(small_pic_scene(n=24, guard=2, width=64, height=48, seed=6,
+                                             dist_factor=1.3), clip=clip)
+    rep, r, (g8, g32, gns) = _check(sc, f"clip {clip}")
+    if clip[0][3] <= -24.0:
+        assert rep.hit == 0 and np.all(gns == 0)
+    else:
+        assert rep.hit > 100
