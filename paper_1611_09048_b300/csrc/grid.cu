@@ -22,52 +22,77 @@ struct KGrid {
     int nx, ny, nz;
     int cell;
     int gx, gy, gz;
+    int W, H;             // columns per axis of the apron-extended volume: nx + 2, ny + 2
+    int kchunk, nchunks;  // macro cells per z chunk, chunks
+    float *cols;          // column maxima: (gz, H, W), workspace
     float *grid;
 };
 
-constexpr int kGridThreads = 352;   // 11 warps: one pass over the 18 x 18 columns of a 16^3 cell
 // z-cells whose loads a thread issues together: 16 on the scalar fast paths
 // (a walk is bound by the loads in flight), 8 where a cell has several values
 template <int FD> constexpr int grid_z() { return FD == 1 ? 16 : 8; }
 
-// One block per column (i, j) of macro cells.  Each thread owns (x, y)
-// columns of the column's apron-extended footprint -- consecutive threads
-// take consecutive x, so a warp's loads are coalesced -- and walks its column
-// once in z, grid_z() cells at a time with their loads issued together.  Cell z
-// belongs to macro cells k with k*cell - 1 <= z <= (k+1)*cell (at most two
-// for cell >= 2), so a thread keeps two running maxima, for the lowest open
-// macro cell and the next; when z leaves the lower one, the warp's maximum
-// is folded into the grid with one atomic max (opacities are >= 0, so their
-// bit patterns order like the values; the grid is zeroed first).
+// Blended opacity of the kGridZ cells zb .. zb+kGridZ-1 of the column whose
+// per-source element pointers are cp (z clamped to each source's readable range).
+template <int NS, int FD, int kGridZ>
+__device__ __forceinline__ void column_alpha(const KGrid &p, const float *const *cp, const float *s_alpha,
+                                             int nact, int zb, float (&a)[kGridZ])
+{
+#pragma unroll
+    for (int j = 0; j < kGridZ; ++j) a[j] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
+        if (s >= nact) break;
+        const KSource &q = p.src[s];
+        const int fd = (NS == 1 && FD) ? FD : q.fdim;
+        float v[kGridZ][4];
+#pragma unroll
+        for (int j = 0; j < kGridZ; ++j) {
+            const int zi = min(max(min(zb + j, p.nz), q.lo), p.nz - 1 + q.hi_pad);
+            const float *b = cp[s] + (long long)zi * q.sz;
+            v[j][0] = __ldg(b);
+#pragma unroll
+            for (int c = 1; c < 4; ++c) v[j][c] = c < fd ? __ldg(b + (long long)c * q.sc) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < kGridZ; ++j) {
+            float w[4] = {v[j][0], v[j][1], v[j][2], v[j][3]};
+            const float xv = run_chain(p.ch[s], w);
+            const float pos = clamp01(xv) * 255.0f;
+            const int k = min((int)pos, 254);
+            const float f = pos - (float)k;
+            a[j] = fmaf(q.w, lerp1(s_alpha[s * 256 + k], s_alpha[s * 256 + k + 1], f), a[j]);
+        }
+    }
+}
+
+// Pass 1: one thread per item = (x, y) column of the apron-extended volume
+// [-1, n]^2 and chunk of kchunk macro cells in z; consecutive threads take
+// consecutive x, so every load is coalesced, and each column is read once
+// (plus the two shared z-cells at chunk borders).  The thread walks z through
+// the chunk's cells [k0*cell - 1, k1*cell], kGridZ cells' loads at a time.
+// Cell z belongs to macro cells k with k*cell - 1 <= z <= (k+1)*cell (at most
+// two for cell >= 2), so the thread keeps two running maxima, for the lowest
+// open macro cell and the next, and stores the column maximum of each macro
+// cell when z leaves it: cols[k][y+1][x+1], every entry written once.
 // NS > 0: NS active sources known at compile time, and with NS == 1 and
 // FD > 0 the source's f_dim too (the scalar fast path); 0: read at run time.
 template <int NS, int FD>
-static __global__ void __launch_bounds__(kGridThreads, 2) k_opacity_grid(const __grid_constant__ KGrid p)
+static __global__ void __launch_bounds__(256, (NS == 1 && FD == 1) ? 4 : 2) k_grid_columns(const __grid_constant__ KGrid p)
 {
     constexpr int kGridZ = grid_z<(NS == 1 && FD == 1) ? 1 : 4>();
     __shared__ float s_alpha[ISAAC_MAX_ACTIVE * 256];
     const int nact = NS ? NS : p.nact;
     for (int i = threadIdx.x; i < nact * 256; i += blockDim.x) s_alpha[i] = __ldg(&p.lut[i >> 8][i & 255].w);
     __syncthreads();
-    const int gi = blockIdx.x % p.gx, gj = blockIdx.x / p.gx;
-    const int x0 = max(gi * p.cell - 1, -1), x1 = min((gi + 1) * p.cell, p.nx);
-    const int y0 = max(gj * p.cell - 1, -1), y1 = min((gj + 1) * p.cell, p.ny);
-    const int wx = x1 - x0 + 1, wy = y1 - y0 + 1;
-    const int lane = threadIdx.x & 31;
-    unsigned *grid_bits = reinterpret_cast<unsigned *>(p.grid);
-    auto flush = [&](int k, float m) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0 && m > 0.0f)
-            atomicMax(grid_bits + ((long long)k * p.gy + gj) * p.gx + gi, __float_as_uint(m));
-    };
-    // every thread of the block runs the same number of column passes, so the
-    // warp-wide reductions in flush() see all 32 lanes
-    const int passes = (wx * wy + (int)blockDim.x - 1) / (int)blockDim.x;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int col = pass * blockDim.x + threadIdx.x;
-        const bool live = col < wx * wy;
-        const int x = x0 + (live ? col % wx : 0), y = y0 + (live ? col / wx : 0);
+    const long long plane = (long long)p.W * p.H;
+    const long long items = plane * p.nchunks;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / plane);
+        const long long col = it - (long long)chunk * plane;
+        const int yy = (int)(col / p.W), xx = (int)(col - (long long)yy * p.W);
+        const int x = xx - 1, y = yy - 1;
         const float *cp[ISAAC_MAX_ACTIVE];
 #pragma unroll
         for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
@@ -79,184 +104,288 @@ static __global__ void __launch_bounds__(kGridThreads, 2) k_opacity_grid(const _
                 cp[s] = q.base + ((long long)xi * q.sx + (long long)yi * q.sy);
             }
         }
-        int ka = 0;                                         // lowest open macro cell
-        int end_a = min(p.cell, p.nz);                      // its last z
-        int start_b = p.gz > 1 ? p.cell - 1 : 0x7fffffff;   // first z of cell ka + 1
-        float ma = 0.0f, mb = 0.0f;                         // running maxima of cells ka, ka + 1
-        for (int zb = -1; zb <= p.nz; zb += kGridZ) {
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        const int zs = max(k0 * p.cell - 1, -1), ze = min(k1 * p.cell, p.nz);
+        int ka = k0;                                            // lowest open macro cell
+        int end_a = min((ka + 1) * p.cell, p.nz);               // its last z
+        int start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;   // first z of cell ka + 1
+        float ma = 0.0f, mb = 0.0f;                             // running maxima of cells ka, ka + 1
+        float *out = p.cols + col;
+        for (int zb = zs; zb <= ze; zb += kGridZ) {
             float a[kGridZ];
-#pragma unroll
-            for (int j = 0; j < kGridZ; ++j) a[j] = 0.0f;
-#pragma unroll
-            for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
-                if (s >= nact) break;
-                const KSource &q = p.src[s];
-                const int fd = (NS == 1 && FD) ? FD : q.fdim;
-                float v[kGridZ][4];
-#pragma unroll
-                for (int j = 0; j < kGridZ; ++j) {
-                    const int zi = min(max(min(zb + j, p.nz), q.lo), p.nz - 1 + q.hi_pad);
-                    const float *b = cp[s] + (long long)zi * q.sz;
-                    v[j][0] = __ldg(b);
-#pragma unroll
-                    for (int c = 1; c < 4; ++c) v[j][c] = c < fd ? __ldg(b + (long long)c * q.sc) : 0.0f;
-                }
-#pragma unroll
-                for (int j = 0; j < kGridZ; ++j) {
-                    float w[4] = {v[j][0], v[j][1], v[j][2], v[j][3]};
-                    const float xv = run_chain(p.ch[s], w);
-                    const float pos = clamp01(xv) * 255.0f;
-                    const int k = min((int)pos, 254);
-                    const float f = pos - (float)k;
-                    a[j] = fmaf(q.w, lerp1(s_alpha[s * 256 + k], s_alpha[s * 256 + k + 1], f), a[j]);
-                }
-            }
+            column_alpha<NS, FD, kGridZ>(p, cp, s_alpha, nact, zb, a);
 #pragma unroll
             for (int j = 0; j < kGridZ; ++j) {
                 const int z = zb + j;
-                if (z > p.nz) break;
-                if (z > end_a) {                  // z left cell ka: fold it, open the next
-                    flush(ka, ma);
+                if (z > ze) break;
+                if (z > end_a) {                  // z left cell ka: store it, open the next
+                    out[(long long)ka * plane] = ma;
                     ++ka;
                     ma = mb;
                     mb = 0.0f;
                     end_a = min((ka + 1) * p.cell, p.nz);
-                    start_b = ka + 1 < p.gz ? (ka + 1) * p.cell - 1 : 0x7fffffff;
+                    start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;
                 }
-                const float al = live ? clamp01(a[j]) : 0.0f;
+                const float al = clamp01(a[j]);
                 ma = fmaxf(ma, al);
                 mb = z >= start_b ? fmaxf(mb, al) : mb;
             }
         }
-        flush(ka, ma);
-        if (ka + 1 < p.gz) flush(ka + 1, mb);
+        out[(long long)ka * plane] = ma;          // ka == k1 - 1: the walk ends in it
+    }
+}
+
+// Pass 1, one scalar source with the identity chain and macro cells of CELL
+// cells (the learned proposal's configuration).  Macro cell k covers z in
+// [k*CELL - 1, (k+1)*CELL]: the pair {k*CELL - 1, k*CELL} it shares with k-1,
+// CELL-2 core cells, and the pair {(k+1)*CELL - 1, (k+1)*CELL} it shares with
+// k+1.  The walk loads one pair (entering the chunk) and then CELL cells per
+// macro cell: max(previous pair, core, next pair), branch-free.  Reads past the
+// volume's clipped range are clamped to the last readable cell, which that
+// macro cell already contains, so they do not change its maximum.  The alpha
+// table holds (a_k, a_{k+1} - a_k), so a lookup is one 8-byte load and the
+// interpolation fmaf(f, a_{k+1} - a_k, a_k) is the one lerp1 computes.
+template <int CELL>
+static __global__ void __launch_bounds__(256, 4) k_grid_columns_scalar(const __grid_constant__ KGrid p)
+{
+    __shared__ float2 s_pair[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float a0 = __ldg(&p.lut[0][i].w);
+        const float a1 = i < 255 ? __ldg(&p.lut[0][i + 1].w) : a0;
+        s_pair[i] = make_float2(a0, a1 - a0);
+    }
+    __syncthreads();
+    const KSource &q = p.src[0];
+    const int lo = q.lo, hi = p.nz - 1 + q.hi_pad;
+    const long long sz = q.sz;
+    const float w = q.w;
+    auto alpha = [&](float v) {
+        const float pos = clamp01(v) * 255.0f;
+        const int k = min((int)pos, 254);
+        const float2 e = s_pair[k];
+        return clamp01(fmaf(w, fmaf(pos - (float)k, e.y, e.x), 0.0f));
+    };
+    const long long plane = (long long)p.W * p.H;
+    const long long items = plane * p.nchunks;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / plane);
+        const long long col = it - (long long)chunk * plane;
+        const int yy = (int)(col / p.W), xx = (int)(col - (long long)yy * p.W);
+        const int xi = min(max(xx - 1, lo), p.nx - 1 + q.hi_pad);
+        const int yi = min(max(yy - 1, lo), p.ny - 1 + q.hi_pad);
+        const float *cp = q.base + ((long long)xi * q.sx + (long long)yi * q.sy);
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        float *out = p.cols + col;
+        float prev;
+        {
+            const int za = min(max(k0 * CELL - 1, lo), hi), zb = min(max(k0 * CELL, lo), hi);
+            prev = fmaxf(alpha(__ldg(cp + za * sz)), alpha(__ldg(cp + zb * sz)));
+        }
+        for (int k = k0; k < k1; ++k) {
+            const int z0 = k * CELL + 1;                 // cells z0 .. z0 + CELL - 1
+            float v[CELL];
+            if (z0 >= lo && z0 + CELL - 1 <= hi) {
+                const float *b = cp + (long long)z0 * sz;
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) v[j] = __ldg(b + j * sz);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) v[j] = __ldg(cp + (long long)min(max(z0 + j, lo), hi) * sz);
+            }
+            float core = 0.0f;
+#pragma unroll
+            for (int j = 0; j < CELL - 2; ++j) core = fmaxf(core, alpha(v[j]));
+            const float next = fmaxf(alpha(v[CELL - 2]), alpha(v[CELL - 1]));
+            out[(long long)k * plane] = fmaxf(fmaxf(prev, core), next);
+            prev = next;
+        }
+    }
+}
+
+// Pass 2: one warp per macro cell (i, j, k): the largest column maximum over
+// its columns x in [i*cell - 1, (i+1)*cell], y likewise (clipped to [-1, n]).
+static __global__ void __launch_bounds__(256) k_grid_reduce(const __grid_constant__ KGrid p)
+{
+    const int lane = threadIdx.x & 31;
+    const long long cells = (long long)p.gx * p.gy * p.gz;
+    const long long plane = (long long)p.W * p.H;
+    for (long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; m < cells;
+         m += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int gi = (int)(m % p.gx), gj = (int)((m / p.gx) % p.gy), k = (int)(m / ((long long)p.gx * p.gy));
+        const int xs = max(gi * p.cell - 1, -1) + 1, xe = min((gi + 1) * p.cell, p.nx) + 1;
+        const int ys = max(gj * p.cell - 1, -1) + 1, ye = min((gj + 1) * p.cell, p.ny) + 1;
+        const int wx = xe - xs + 1, n = wx * (ye - ys + 1);
+        const float *base = p.cols + (long long)k * plane + (long long)ys * p.W + xs;
+        float mx = 0.0f;
+        for (int e = lane; e < n; e += 32) {
+            const int r = e / wx;
+            mx = fmaxf(mx, __ldg(base + (long long)r * p.W + (e - r * wx)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) p.grid[m] = mx;
     }
 }
 
 // ------------------------------------------------------ value-range grid
 
-// Order-preserving map of non-NaN floats to unsigned (atomic min/max on floats).
-__device__ __forceinline__ unsigned ord_enc(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float ord_dec(unsigned u)
-{
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-
 struct KRange {
     KSource src;          // the source of this pass
     int nx, ny, nz, cell, gx, gy, gz;
     int slots, slot0;     // components per macro cell in all, first of this source
-    unsigned *r;          // (min, max) pairs, order-encoded until k_range_decode
+    int W, H;             // columns per axis of the apron-extended volume
+    int kchunk, nchunks;  // macro cells per z chunk, chunks
+    float2 *cols;         // per column, macro cell and component: (min, max), workspace
+    float *ranges;        // (min, max) per macro cell and slot
 };
 
-static __global__ void k_range_init(unsigned *r, long long pairs)
+// The (min, max) a value contributes: a NaN widens to [-inf, +inf].
+__device__ __forceinline__ float2 range_of(float v)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < pairs;
-         i += (long long)gridDim.x * blockDim.x) {
-        r[2 * i] = 0xff800000u;        // ord_enc(+inf)
-        r[2 * i + 1] = 0x007fffffu;    // ord_enc(-inf)
+    const float inf = __int_as_float(0x7f800000);
+    return v == v ? make_float2(v, v) : make_float2(-inf, inf);
+}
+__device__ __forceinline__ float2 range_join(float2 a, float2 b)
+{
+    return make_float2(fminf(a.x, b.x), fmaxf(a.y, b.y));
+}
+
+// Pass 1 of the value-range grid, one source: the same items and walk as
+// k_grid_columns (one thread per (x, y) column and z chunk, coalesced loads,
+// each column read once), keeping per component the (min, max) of the values
+// read for the open macro cell and the next; stored per column when z leaves
+// a macro cell: cols[((k * H + y+1) * W + x+1) * FD + c].  CELL > 0: macro
+// cells of CELL cells walked as shared pair / core / shared pair (the
+// branch-free form of k_grid_columns_scalar); 0: any cell size.
+template <int FD, int CELL>
+static __global__ void __launch_bounds__(256, CELL > 0 ? 4 : 2) k_range_columns(const __grid_constant__ KRange p)
+{
+    constexpr int kZ = CELL > 0 ? CELL : grid_z<FD>();
+    const float inf = __int_as_float(0x7f800000);
+    const KSource &q = p.src;
+    const int lo = q.lo, hi = p.nz - 1 + q.hi_pad;
+    const long long plane = (long long)p.W * p.H;
+    const long long items = plane * p.nchunks;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / plane);
+        const long long col = it - (long long)chunk * plane;
+        const int yy = (int)(col / p.W), xx = (int)(col - (long long)yy * p.W);
+        const int xi = min(max(xx - 1, lo), p.nx - 1 + q.hi_pad);
+        const int yi = min(max(yy - 1, lo), p.ny - 1 + q.hi_pad);
+        const float *cp = q.base + ((long long)xi * q.sx + (long long)yi * q.sy);
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        float2 *out = p.cols + col * FD;
+        auto load = [&](int z, float (&v)[FD]) {
+            const float *b = cp + (long long)min(max(z, lo), hi) * q.sz;
+#pragma unroll
+            for (int c = 0; c < FD; ++c) v[c] = __ldg(b + (long long)c * q.sc);
+        };
+        if constexpr (CELL > 0) {
+            float2 prev[FD];
+            {
+                float va[FD], vb[FD];
+                load(k0 * CELL - 1, va);
+                load(k0 * CELL, vb);
+#pragma unroll
+                for (int c = 0; c < FD; ++c) prev[c] = range_join(range_of(va[c]), range_of(vb[c]));
+            }
+            for (int k = k0; k < k1; ++k) {
+                const int z0 = k * CELL + 1;
+                float v[CELL][FD];
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) load(z0 + j, v[j]);
+#pragma unroll
+                for (int c = 0; c < FD; ++c) {
+                    float2 core = make_float2(inf, -inf);
+#pragma unroll
+                    for (int j = 0; j < CELL - 2; ++j) core = range_join(core, range_of(v[j][c]));
+                    const float2 next = range_join(range_of(v[CELL - 2][c]), range_of(v[CELL - 1][c]));
+                    out[(long long)k * plane * FD + c] = range_join(range_join(prev[c], core), next);
+                    prev[c] = next;
+                }
+            }
+        } else {
+            const int zs = max(k0 * p.cell - 1, -1), ze = min(k1 * p.cell, p.nz);
+            int ka = k0;
+            int end_a = min((ka + 1) * p.cell, p.nz);
+            int start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;
+            float2 ra[FD], rb[FD];
+#pragma unroll
+            for (int c = 0; c < FD; ++c) ra[c] = rb[c] = make_float2(inf, -inf);
+            for (int zb = zs; zb <= ze; zb += kZ) {
+                float v[kZ][FD];
+#pragma unroll
+                for (int j = 0; j < kZ; ++j) load(zb + j, v[j]);
+#pragma unroll
+                for (int j = 0; j < kZ; ++j) {
+                    const int z = zb + j;
+                    if (z > ze) break;
+                    if (z > end_a) {
+#pragma unroll
+                        for (int c = 0; c < FD; ++c) {
+                            out[(long long)ka * plane * FD + c] = ra[c];
+                            ra[c] = rb[c];
+                            rb[c] = make_float2(inf, -inf);
+                        }
+                        ++ka;
+                        end_a = min((ka + 1) * p.cell, p.nz);
+                        start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;
+                    }
+#pragma unroll
+                    for (int c = 0; c < FD; ++c) {
+                        const float2 r = range_of(v[j][c]);
+                        ra[c] = range_join(ra[c], r);
+                        if (z >= start_b) rb[c] = range_join(rb[c], r);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < FD; ++c) out[(long long)ka * plane * FD + c] = ra[c];
+        }
     }
 }
 
-static __global__ void k_range_decode(unsigned *r, long long n)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        r[i] = __float_as_uint(ord_dec(r[i]));
-}
-
-// Per macro cell (same boxes as the opacity grid) and component of one
-// source, the smallest and largest value read; a NaN widens the component to
-// [-inf, +inf].  Same walk as k_opacity_grid: one block per macro-cell
-// column, one z-walk per (x, y) column with a two-cell window; a warp's
-// minima and maxima are folded into the grid with atomic min / max.
+// Pass 2: one warp per macro cell: per component, the min of the column
+// minima and the max of the column maxima over the cell's apron-extended
+// columns, written as the slot's (min, max).
 template <int FD>
-static __global__ void __launch_bounds__(kGridThreads, 2) k_range_grid(const __grid_constant__ KRange p)
+static __global__ void __launch_bounds__(256) k_range_reduce(const __grid_constant__ KRange p)
 {
-    constexpr int kGridZ = grid_z<FD>();
     const float inf = __int_as_float(0x7f800000);
-    const KSource &q = p.src;
-    const int gi = blockIdx.x % p.gx, gj = blockIdx.x / p.gx;
-    const int x0 = max(gi * p.cell - 1, -1), x1 = min((gi + 1) * p.cell, p.nx);
-    const int y0 = max(gj * p.cell - 1, -1), y1 = min((gj + 1) * p.cell, p.ny);
-    const int wx = x1 - x0 + 1, wy = y1 - y0 + 1;
     const int lane = threadIdx.x & 31;
-    auto flush = [&](int k, const float (&mn)[FD], const float (&mx)[FD]) {
-        const long long base = (((long long)k * p.gy + gj) * p.gx + gi) * p.slots + p.slot0;
+    const long long cells = (long long)p.gx * p.gy * p.gz;
+    const long long plane = (long long)p.W * p.H;
+    for (long long m = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; m < cells;
+         m += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int gi = (int)(m % p.gx), gj = (int)((m / p.gx) % p.gy), k = (int)(m / ((long long)p.gx * p.gy));
+        const int xs = max(gi * p.cell - 1, -1) + 1, xe = min((gi + 1) * p.cell, p.nx) + 1;
+        const int ys = max(gj * p.cell - 1, -1) + 1, ye = min((gj + 1) * p.cell, p.ny) + 1;
+        const int wx = xe - xs + 1, n = wx * (ye - ys + 1);
+        const float2 *base = p.cols + ((long long)k * plane + (long long)ys * p.W + xs) * FD;
+        float2 r[FD];
+#pragma unroll
+        for (int c = 0; c < FD; ++c) r[c] = make_float2(inf, -inf);
+        for (int e = lane; e < n; e += 32) {
+            const int row = e / wx;
+            const float2 *q = base + ((long long)row * p.W + (e - row * wx)) * FD;
+#pragma unroll
+            for (int c = 0; c < FD; ++c) r[c] = range_join(r[c], __ldg(q + c));
+        }
 #pragma unroll
         for (int c = 0; c < FD; ++c) {
-            const unsigned lo = __reduce_min_sync(0xffffffffu, ord_enc(mn[c]));
-            const unsigned hi = __reduce_max_sync(0xffffffffu, ord_enc(mx[c]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r[c].x = fminf(r[c].x, __shfl_xor_sync(0xffffffffu, r[c].x, o));
+                r[c].y = fmaxf(r[c].y, __shfl_xor_sync(0xffffffffu, r[c].y, o));
+            }
             if (lane == 0) {
-                atomicMin(p.r + 2 * (base + c), lo);
-                atomicMax(p.r + 2 * (base + c) + 1, hi);
+                float *dst = p.ranges + 2 * (m * p.slots + p.slot0 + c);
+                dst[0] = r[c].x;
+                dst[1] = r[c].y;
             }
         }
-    };
-    const int passes = (wx * wy + (int)blockDim.x - 1) / (int)blockDim.x;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int col = pass * blockDim.x + threadIdx.x;
-        const bool live = col < wx * wy;
-        const int x = x0 + (live ? col % wx : 0), y = y0 + (live ? col / wx : 0);
-        const int xi = min(max(x, q.lo), p.nx - 1 + q.hi_pad);
-        const int yi = min(max(y, q.lo), p.ny - 1 + q.hi_pad);
-        const float *cp = q.base + ((long long)xi * q.sx + (long long)yi * q.sy);
-        int ka = 0;
-        int end_a = min(p.cell, p.nz);
-        int start_b = p.gz > 1 ? p.cell - 1 : 0x7fffffff;
-        float amn[FD], amx[FD], bmn[FD], bmx[FD];
-#pragma unroll
-        for (int c = 0; c < FD; ++c) {
-            amn[c] = bmn[c] = inf;
-            amx[c] = bmx[c] = -inf;
-        }
-        for (int zb = -1; zb <= p.nz; zb += kGridZ) {
-            float v[kGridZ][FD];
-#pragma unroll
-            for (int j = 0; j < kGridZ; ++j) {
-                const int zi = min(max(min(zb + j, p.nz), q.lo), p.nz - 1 + q.hi_pad);
-                const float *b = cp + (long long)zi * q.sz;
-#pragma unroll
-                for (int c = 0; c < FD; ++c) v[j][c] = __ldg(b + (long long)c * q.sc);
-            }
-#pragma unroll
-            for (int j = 0; j < kGridZ; ++j) {
-                const int z = zb + j;
-                if (z > p.nz) break;
-                if (z > end_a) {
-                    flush(ka, amn, amx);
-                    ++ka;
-#pragma unroll
-                    for (int c = 0; c < FD; ++c) {
-                        amn[c] = bmn[c];
-                        amx[c] = bmx[c];
-                        bmn[c] = inf;
-                        bmx[c] = -inf;
-                    }
-                    end_a = min((ka + 1) * p.cell, p.nz);
-                    start_b = ka + 1 < p.gz ? (ka + 1) * p.cell - 1 : 0x7fffffff;
-                }
-#pragma unroll
-                for (int c = 0; c < FD; ++c) {
-                    const float val = v[j][c];
-                    const bool nan = !(val == val);
-                    const float lo = !live ? inf : (nan ? -inf : val);
-                    const float hi = !live ? -inf : (nan ? inf : val);
-                    amn[c] = fminf(amn[c], lo);
-                    amx[c] = fmaxf(amx[c], hi);
-                    if (z >= start_b) {
-                        bmn[c] = fminf(bmn[c], lo);
-                        bmx[c] = fmaxf(bmx[c], hi);
-                    }
-                }
-            }
-        }
-        flush(ka, amn, amx);
-        if (ka + 1 < p.gz) flush(ka + 1, bmn, bmx);
     }
 }
 
@@ -335,6 +464,19 @@ int launch_empty_flags(const KParams &kp, int nact, const float *ranges, int slo
 
 }  // namespace isaac
 
+namespace isaac {
+static int sm_count_grid()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+    }
+    return n;
+}
+}  // namespace isaac
+
 using namespace isaac;
 
 extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain *chains,
@@ -382,22 +524,44 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
         ++p.nact;
     }
     p.grid = grid;
+    const cudaStream_t st = (cudaStream_t)stream;
     if (p.nact == 0) {
-        if (cudaMemsetAsync(grid, 0, (size_t)cells * sizeof(float), (cudaStream_t)stream) != cudaSuccess)
+        if (cudaMemsetAsync(grid, 0, (size_t)cells * sizeof(float), st) != cudaSuccess)
             return check_cuda("isaac_opacity_grid memset");
         return ISAAC_OK;
     }
-    if (cudaMemsetAsync(grid, 0, (size_t)cells * sizeof(float), (cudaStream_t)stream) != cudaSuccess)
-        return check_cuda("isaac_opacity_grid memset");
-    const dim3 blocks((unsigned)(p.gx * p.gy));
-    const cudaStream_t st = (cudaStream_t)stream;
-    if (p.nact == 1 && p.src[0].fdim == 1 && p.ch[0].n == 0)
-        k_opacity_grid<1, 1><<<blocks, kGridThreads, 0, st>>>(p);
+    // column maxima in the stream's workspace (ordered before any later frame
+    // on the stream that reuses those bytes)
+    p.W = p.nx + 2;
+    p.H = p.ny + 2;
+    p.kchunk = std::max(1, (64 + cell - 1) / cell);
+    p.nchunks = (p.gz + p.kchunk - 1) / p.kchunk;
+    const size_t col_bytes = (size_t)p.gz * (size_t)p.W * (size_t)p.H * sizeof(float);
+    KParams wp;
+    memset(&wp, 0, sizeof wp);
+    void *cols = nullptr;
+    int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
+    if (rc) return rc;
+    p.cols = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
+    const int sms = sm_count_grid();
+    const long long items = (long long)p.W * p.H * p.nchunks;
+    const unsigned b1 = (unsigned)std::max(1LL, std::min((items + 255) / 256, (long long)sms * 4));
+    const bool scalar = p.nact == 1 && p.src[0].fdim == 1 && p.ch[0].n == 0;
+    if (scalar && cell == 16)
+        k_grid_columns_scalar<16><<<b1, 256, 0, st>>>(p);
+    else if (scalar && cell == 8)
+        k_grid_columns_scalar<8><<<b1, 256, 0, st>>>(p);
+    else if (scalar)
+        k_grid_columns<1, 1><<<b1, 256, 0, st>>>(p);
     else if (p.nact == 3)
-        k_opacity_grid<3, 0><<<blocks, kGridThreads, 0, st>>>(p);
+        k_grid_columns<3, 0><<<b1, 256, 0, st>>>(p);
     else
-        k_opacity_grid<0, 0><<<blocks, kGridThreads, 0, st>>>(p);
-    return check_cuda("isaac_opacity_grid launch");
+        k_grid_columns<0, 0><<<b1, 256, 0, st>>>(p);
+    rc = check_cuda("isaac_opacity_grid columns launch");
+    if (rc) return rc;
+    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
+    k_grid_reduce<<<b2, 256, 0, st>>>(p);
+    return check_cuda("isaac_opacity_grid reduce launch");
 }
 
 extern "C" int isaac_range_grid(const isaac_source *sources, int32_t n_sources,
@@ -441,25 +605,51 @@ extern "C" int isaac_range_grid(const isaac_source *sources, int32_t n_sources,
         return fail(ISAAC_ENOMEM, "ranges holds %lld floats, %lld needed", (long long)ranges_len,
                     cells * slots * 2);
     const cudaStream_t st = (cudaStream_t)stream;
-    unsigned *ru = reinterpret_cast<unsigned *>(ranges);
-    const long long pairs = cells * slots;
-    const unsigned eb = (unsigned)std::max(1LL, std::min((pairs + 255) / 256, 148LL * 8));
-    k_range_init<<<eb, 256, 0, st>>>(ru, pairs);
     r.slots = slots;
-    r.r = ru;
+    r.ranges = ranges;
+    r.W = r.nx + 2;
+    r.H = r.ny + 2;
+    r.kchunk = std::max(1, (64 + cell - 1) / cell);
+    r.nchunks = (r.gz + r.kchunk - 1) / r.kchunk;
+    int fmax_src = 1;
+    for (int a = 0; a < nact; ++a) fmax_src = std::max(fmax_src, ks[a].fdim);
+    // per-column (min, max) pairs of one source at a time, in the stream's workspace
+    const size_t col_bytes = (size_t)r.gz * (size_t)r.W * (size_t)r.H * (size_t)fmax_src * sizeof(float2);
+    KParams wp;
+    memset(&wp, 0, sizeof wp);
+    void *cols = nullptr;
+    int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
+    if (rc) return rc;
+    r.cols = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
+    const int sms = sm_count_grid();
+    const long long items = (long long)r.W * r.H * r.nchunks;
+    const unsigned b1 = (unsigned)std::max(1LL, std::min((items + 255) / 256, (long long)sms * 4));
+    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
     int slot = 0;
     for (int a = 0; a < nact; ++a) {
         r.src = ks[a];
         r.slot0 = slot;
-        const dim3 blocks((unsigned)(r.gx * r.gy));
         switch (ks[a].fdim) {
-        case 1: k_range_grid<1><<<blocks, kGridThreads, 0, st>>>(r); break;
-        case 2: k_range_grid<2><<<blocks, kGridThreads, 0, st>>>(r); break;
-        case 3: k_range_grid<3><<<blocks, kGridThreads, 0, st>>>(r); break;
-        default: k_range_grid<4><<<blocks, kGridThreads, 0, st>>>(r); break;
+        case 1:
+            if (cell == 16) k_range_columns<1, 16><<<b1, 256, 0, st>>>(r);
+            else if (cell == 8) k_range_columns<1, 8><<<b1, 256, 0, st>>>(r);
+            else k_range_columns<1, 0><<<b1, 256, 0, st>>>(r);
+            k_range_reduce<1><<<b2, 256, 0, st>>>(r);
+            break;
+        case 2:
+            k_range_columns<2, 0><<<b1, 256, 0, st>>>(r);
+            k_range_reduce<2><<<b2, 256, 0, st>>>(r);
+            break;
+        case 3:
+            k_range_columns<3, 0><<<b1, 256, 0, st>>>(r);
+            k_range_reduce<3><<<b2, 256, 0, st>>>(r);
+            break;
+        default:
+            k_range_columns<4, 0><<<b1, 256, 0, st>>>(r);
+            k_range_reduce<4><<<b2, 256, 0, st>>>(r);
+            break;
         }
         slot += ks[a].fdim;
     }
-    k_range_decode<<<eb, 256, 0, st>>>(ru, 2 * pairs);
     return check_cuda("isaac_range_grid launch");
 }

@@ -35,3 +35,54 @@ def test_grid_bubble_mask_and_empty(cuda_ok):
     z = ds.opacity_grid(8, mask=0)
     torch.cuda.synchronize()
     assert torch.count_nonzero(z) == 0
+
+
+@pytest.mark.parametrize("cell", [2, 5, 40])
+def test_grid_non_cubic_two_sources(cuda_ok, cell):
+    """A 30 x 13 x 19 volume with two scalar sources (the run-time source
+    loop), one with guards and a chain, one without: every macro-cell size
+    from 2 (z chunks of many cells) to one larger than the volume."""
+    import torch
+    from scenes_util import make_scene
+    n = (30, 13, 19)
+    rng = np.random.default_rng(21)
+    f0 = rng.random((n[2] + 2, n[1] + 2, n[0] + 2), np.float32)          # guard 1
+    f1 = rng.random((n[2], n[1], n[0]), np.float32) ** 3                  # no guard
+    cams = synth.random_orbit_camera(n, 16, 16, seed=3)
+    sc = make_scene([f0, f1], [[("mul", (2.0,)), ("add", (-0.5,))], []],
+                    [synth.lut_from_points(31), synth.lut_from_points(32)], [0.7, 0.6], n, cams,
+                    16, 16)
+    sc.sources[0] = synth.source_from_zyx(f0, 1)
+    g = isaac.DeviceScene(sc).opacity_grid(cell)
+    torch.cuda.synchronize()
+    want = oracle.opacity_grid(sc, cell)
+    assert want.shape == tuple((k + cell - 1) // cell for k in n[::-1])
+    np.testing.assert_allclose(g.cpu().numpy(), want, rtol=0, atol=TOL_ALPHA)
+
+
+@pytest.mark.parametrize("guard", [0, 1, 3])
+@pytest.mark.parametrize("cell", [8, 16])
+def test_grid_scalar_identity_ragged(cuda_ok, guard, cell):
+    """The scalar identity-chain walk (its own kernel for 8- and 16-cell macro
+    cells) on volumes that are not multiples of the cell, with and without
+    guard cells, and a negative weight (opacity clamped to 0)."""
+    import torch
+    from scenes_util import make_scene
+    n = (37, 20, 45)
+    rng = np.random.default_rng(40 + guard + cell)
+    S = (n[2] + 2 * guard, n[1] + 2 * guard, n[0] + 2 * guard)
+    # a ramp in z (so each macro cell's maximum depends on exactly which z-cells
+    # it covers, aprons included) plus a little noise
+    ramp = (np.arange(S[0], dtype=np.float32) / S[0])[:, None, None]
+    f = (0.05 + 0.9 * ramp + 0.04 * rng.random(S, np.float32)).astype(np.float32)
+    cams = synth.random_orbit_camera(n, 16, 16, seed=4)
+    for wgt in (0.8, -0.5):
+        sc = make_scene([f], [[]], [synth.lut_from_points(50 + cell)], [wgt], n, cams, 16, 16,
+                        guard=guard)
+        g = isaac.DeviceScene(sc).opacity_grid(cell)
+        torch.cuda.synchronize()
+        want = oracle.opacity_grid(sc, cell)
+        got = g.cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=0, atol=TOL_ALPHA)
+        if wgt < 0:
+            assert np.all(got.view(np.uint32) == 0)       # +0, never -0
