@@ -449,12 +449,16 @@ struct KPropose {
     int *stats;
 };
 
-constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + 4 * 16 * LD_IN;
+// 8 warps per block share one copy of the FP16 weights (~48 KB) and keep a
+// 16-ray input tile each (~7.4 KB): ~106 KB, so two blocks (16 warps) fit on
+// an SM; with 4 warps per block the weights limited it to 8 warps.
+constexpr int kPropWarps = 8;
+constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + kPropWarps * 16 * LD_IN;
 
 // Persistent warps take 16 rays of the frame's ray list at a time: inputs
 // (2 lanes per ray) into the warp's shared tile, the MLP forward pass, then
 // the decision on lanes holding (u0, u1) of rays g and g+8.
-static __global__ void __launch_bounds__(128) k_mlp_propose(const __grid_constant__ KPropose p)
+static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __grid_constant__ KPropose p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __half *sT1 = reinterpret_cast<__half *>(smem_raw);
@@ -546,8 +550,9 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
-    const long long blocks = std::max(1LL, std::min<long long>((rect + 63) / 64, (long long)sms * 2));
-    k_mlp_propose<<<(unsigned)blocks, 128, smem, st>>>(p);
+    const long long blocks = std::max(1LL, std::min<long long>((rect + 16 * kPropWarps - 1) / (16 * kPropWarps),
+                                                              (long long)sms * 2));
+    k_mlp_propose<<<(unsigned)blocks, kPropWarps * 32, smem, st>>>(p);
     return check_cuda("interval proposal launch");
 }
 

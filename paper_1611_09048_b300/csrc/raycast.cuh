@@ -85,14 +85,9 @@ struct WsCounters {
 constexpr int kLongRay = -2;
 // A proposal puts a ray in the long-ray list when it keeps more samples than this.
 constexpr int kLongRaySamples = 96;
-// Lanes per ray and samples per lane and step on the long-ray list: a warp
-// per ray, 128 samples' gathers in flight per step.  Measured at 1080p over
-// the 512^3 bubble (about 4e3 long rays, 3e6 samples): 32 x 4 194 us, 16 x 4
-// 217 us, 16 x 4 with one block per SM 473 us.  Every lane of a group
-// composites every sample in order, so wide groups spend RL/32 warp steps of
-// compositing per sample; the kernel is issue-bound at 32 x 4.
+// Key under which the long-ray kernels are registered (the lanes that shade
+// one ray's samples per instruction); march_long holds kStreamRays rays per warp.
 constexpr int kLongRayLanes = 32;
-constexpr int kLongRaySteps = 4;
 
 // March modes: plain (skipping rays on the long-ray list), footprint bitmap,
 // visible-span labels, the long-ray list alone, plain with empty-space
@@ -367,6 +362,23 @@ __device__ __forceinline__ Geo sample_geo(float x, float y, float z)
 template <typename Idx>
 __device__ __forceinline__ float ld(const float *b, Idx o) { return __ldg(b + o); }
 
+// The 6 floats e[0..5] (two x-adjacent cells of a 3-component AoS source) in
+// four loads: two 8-byte loads at the even-aligned address and two scalars,
+// all inside e[0..5].  q = 1 when e is not 8-byte aligned.
+__device__ __forceinline__ void ld_pair3(const float *e, float (&v)[6])
+{
+    const bool q = ((uintptr_t)e & 4u) != 0;
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(e + (q ? 1 : 0)));
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(e + (q ? 3 : 2)));
+    const float c = __ldg(e + (q ? 0 : 4));
+    v[0] = q ? c : a.x;
+    v[1] = q ? a.x : a.y;
+    v[2] = q ? a.y : b.x;
+    v[3] = q ? b.x : b.y;
+    v[4] = q ? b.y : c;
+    v[5] = __ldg(e + 5);
+}
+
 // Value of source I at the sample: 8-corner gather + trilinear blend per
 // component, or the nearest cell.  Indices are clamped to the readable range
 // the host validated against the source's extent, so no access can leave it.
@@ -390,6 +402,27 @@ __device__ __forceinline__ void fetch_source(const KParams &p, const Geo &g, flo
         const Idx ox0 = Idx(x0) * sx, ox1 = Idx(x1) * sx;
         const Idx o00 = Idx(y0) * sy + Idx(z0) * sz, o10 = Idx(y1) * sy + Idx(z0) * sz;
         const Idx o01 = Idx(y0) * sy + Idx(z1) * sz, o11 = Idx(y1) * sy + Idx(z1) * sz;
+        if constexpr (FD == 3 && AOS) {
+            // cells contiguous in x and both x-corners distinct: each (y, z) row
+            // of the gather is 6 adjacent floats (fewer L1 requests per sample)
+            if (s.sx == 3 && x1 == x0 + 1) {
+                float r00[6], r10[6], r01[6], r11[6];
+                ld_pair3(base + (ox0 + o00), r00);
+                ld_pair3(base + (ox0 + o10), r10);
+                ld_pair3(base + (ox0 + o01), r01);
+                ld_pair3(base + (ox0 + o11), r11);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float c00 = lerp1(r00[c], r00[3 + c], g.fx);
+                    const float c10 = lerp1(r10[c], r10[3 + c], g.fx);
+                    const float c01 = lerp1(r01[c], r01[3 + c], g.fx);
+                    const float c11 = lerp1(r11[c], r11[3 + c], g.fx);
+                    v[c] = lerp1(lerp1(c00, c10, g.fy), lerp1(c01, c11, g.fy), g.fz);
+                }
+                v[3] = 0.0f;
+                return;
+            }
+        }
         const float *p000 = base + (ox0 + o00), *p100 = base + (ox1 + o00);
         const float *p010 = base + (ox0 + o10), *p110 = base + (ox1 + o10);
         const float *p001 = base + (ox0 + o01), *p101 = base + (ox1 + o01);
@@ -777,21 +810,107 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
 }
 
 // The long-ray march: the rays an interval proposal left long (a few among
-// many short ones), kLongRayLanes lanes per ray and kLongRaySteps samples per
-// lane and step, launched before the march of the rest.
+// many short ones), launched before the march of the rest.  A warp holds
+// kStreamRays rays (lanes 0 .. kStreamRays-1 own one each).  Per step every
+// lane shades kStreamU samples -- sample k + j of a held ray, consecutive j on
+// consecutive lanes -- without branches, so the gathers of all of them are in
+// flight together (samples of a dead slot or past a window end read clamped
+// cells and are dropped), into the warp's shared tile; then each owner lane
+// composites its ray's kStreamT samples in order: the same operations in the
+// same order as march_ray, so the pixel is bit-identical to the plain march.
+// A ray that terminates or ends is written and its slot refilled from the
+// list at the next step.  In-order compositing thus costs one lane per ray,
+// not every lane of a group.
+constexpr int kStreamRays = 2, kStreamU = 4, kStreamT = 32 * kStreamU / kStreamRays;
+
 template <class Shader>
 __device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut)
 {
-    constexpr unsigned RAYS = 32 / kLongRayLanes;
+    constexpr int kRow = kStreamT + 1;        // padded row: owners' reads hit distinct banks
+    __shared__ float4 s_tile[4][kStreamRays * kRow];   // 4 warps per block
+    float4 *tile = s_tile[(threadIdx.x >> 5) & 3];
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const bool owner = lane < kStreamRays;
     const unsigned n_long = *(volatile unsigned *)&p.ctr->n_long;
+    RayRec r;
+    r.ex = r.ey = r.ez = r.dx = r.dy = r.dz = 0.0f;
+    r.nsteps = 0;
+    r.pix = 0;
+    int k = 0, ns = 0;
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    bool live = false, exhausted = false;
+    // every list entry is taken once, so the loop ends after n_long takes
     for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(&p.ctr->next_long, RAYS);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if (i >= n_long) break;
-        const unsigned k = i + (unsigned)(lane / kLongRayLanes);
-        if (k < n_long) march_ray<Shader, kLongRayLanes, false, false, false, kLongRaySteps>(p, s_lut, p.longs[k], lane);
+        const unsigned need = exhausted ? 0u : __ballot_sync(full, owner && !live);
+        if (need) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(&p.ctr->next_long, (unsigned)__popc(need));
+            base = __shfl_sync(full, base, 0);
+            if (base + (unsigned)__popc(need) >= n_long) exhausted = true;
+            if (owner && !live) {
+                const unsigned i = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+                if (i < n_long) {
+                    r = p.rays[p.longs[i]];
+                    k = r.kbeg;
+                    ns = 0;
+                    C0 = C1 = C2 = A = 0.0f;
+                    live = k < r.nsteps;
+                    if (!live) write_pixel(p, r.pix, 0.0f, 0.0f, 0.0f, 0.0f, 0);
+                }
+            }
+        }
+        if (!__any_sync(full, live)) {
+            if (exhausted) break;
+            continue;
+        }
+        float4 c[kStreamU];
+        bool valid[kStreamU];
+#pragma unroll
+        for (int u = 0; u < kStreamU; ++u) {
+            const int slot = u * 32 / kStreamT;            // ray of this sample, uniform per u
+            const float ex = __shfl_sync(full, r.ex, slot), ey = __shfl_sync(full, r.ey, slot);
+            const float ez = __shfl_sync(full, r.ez, slot), dx = __shfl_sync(full, r.dx, slot);
+            const float dy = __shfl_sync(full, r.dy, slot), dz = __shfl_sync(full, r.dz, slot);
+            const int ku = __shfl_sync(full, k, slot), nu = __shfl_sync(full, r.nsteps, slot);
+            const bool lu = __shfl_sync(full, (int)live, slot) != 0;
+            const int kk = ku + (u * 32) % kStreamT + lane;
+            valid[u] = lu && kk < nu;
+            const float s = (float)kk * p.step;
+            c[u] = Shader::shade(p, s_lut, fmaf(s, dx, ex), fmaf(s, dy, ey), fmaf(s, dz, ez));
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamU; ++u) {
+            const int slot = u * 32 / kStreamT;
+            tile[slot * kRow + (u * 32) % kStreamT + lane] =
+                valid[u] ? c[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        __syncwarp();
+        if (owner && live) {
+            const int nv = min(kStreamT, r.nsteps - k);
+            const float4 *row = tile + lane * kRow;
+            bool done = false;
+            for (int j = 0; j < nv; ++j) {
+                const float4 cj = row[j];
+                const float a = clamp01(cj.w);
+                const float t = (1.0f - A) * a;
+                C0 = fmaf(t, cj.x, C0);
+                C1 = fmaf(t, cj.y, C1);
+                C2 = fmaf(t, cj.z, C2);
+                A += t;
+                ++ns;
+                if (A >= p.term) {
+                    done = true;
+                    break;
+                }
+            }
+            k += kStreamT;
+            if (done || k >= r.nsteps) {
+                write_pixel(p, r.pix, C0, C1, C2, A, ns);
+                live = false;
+            }
+        }
+        __syncwarp();
     }
 }
 

@@ -164,6 +164,28 @@ def test_proposal_plumbing_closed_forms(cuda_ok, packed):
             assert int(got[0].sum()) == 0
 
 
+@pytest.mark.parametrize("packed", [None, "bf16"])
+def test_long_ray_list_refills(cuda_ok, packed):
+    """'Everything' (full windows, so every ray of > 96 samples goes to the
+    long-ray list) on a frame with many more long rays than the long-ray
+    kernel holds at once (4 per warp): the image is the plain one bit for bit,
+    so slots are refilled in order and no ray is lost or marched twice."""
+    import torch
+    sc = synth.scene_bubble(64, frame=2, seed=5, width=640, height=480, dist_factor=1.1)
+    ds = isaac.DeviceScene(sc)
+    target = ds if packed is None else ds.pack(packed)
+    grid = ds.opacity_grid(8)
+    plain = target.render(want_f32=True, want_nsamp=True)
+    model = _const_model((-30, 30, 30))
+    got = target.render_learned(model.proposal(grid, 8, threshold=0.9, margin=2),
+                                want_f32=True, want_nsamp=True)
+    torch.cuda.synchronize()
+    long_rays = int((plain[2] > 96).sum())
+    assert long_rays > 4 * 4 * 148 * 8 // 2          # well beyond one long-ray slot per warp
+    for a, b in zip(plain, got):
+        assert torch.equal(a, b)
+
+
 def test_trained_proposal_gain_on_bubble(cuda_ok):
     """Train on traced bubble frames, then render an unseen frame: where the
     proposal covered a ray's visible span the pixel is bit-identical to the
