@@ -250,6 +250,7 @@ def run_ours(args, rank, world, local_rank):
     iso = None if args.no_variants else run_iso(args, ds, cams, stream, flush)
     comp = None if args.no_variants else run_composite(args, dev, stream, flush)
     copy = None if args.no_variants else run_source_copy(args, ds, stream, flush)
+    closeup = None if args.no_variants else run_closeup(args, ds, stream, flush)
     learned = None if args.no_learned or rank != 0 else run_learned(args, dev, stream, flush)
     serving = None if args.no_serving or rank != 0 else run_serving(args, ds, dev)
 
@@ -276,6 +277,8 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": dev_ms / args.steps,
+        "ms_per_step_median": statistics.median(step_ms),
+        "ms_per_step_min": min(step_ms),
         "fps": world * args.steps / (dev_ms * 1e-3),
         "higher_is_better": True,
         "scaling": "weak",
@@ -312,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
         "iso": iso,
         "composite": comp,
         "source_copy": copy,
+        "closeup": closeup,
         "learned": learned,
         "serving": serving,
     }
@@ -496,6 +500,42 @@ def run_source_copy(args, ds, stream, flush):
             "peak_kind": kind, "launches": len(srcs)}
 
 
+def run_closeup(args, ds, stream, flush, count=4, dist=0.9):
+    """Stress row: the same volume from cameras at 0.9x the box diagonal, so
+    that the box fills the frame (every ray hits, long chords): per-frame
+    time and composited samples/s, L2 flushed between frames."""
+    import torch
+    from paper_1611_09048_b300 import isaac, synth
+    sc = ds.scene
+    W, H = sc.width, sc.height
+    cams = synth.fibonacci_cameras(tuple(sc.n), W, H, count=count, seed=7, dist_factor=dist)
+    out = torch.empty((H, W, 4), dtype=torch.uint8, device=ds.device)
+    ns = torch.empty((H, W), dtype=torch.int32, device=ds.device)
+    samples, ms, rays = 0, [], 0
+    for mv, proj in cams:
+        with torch.cuda.stream(stream):
+            ds.render(mv, proj, out=out, nsamples=ns, stream=stream)
+        torch.cuda.synchronize()
+        samples += int(ns.sum(dtype=torch.int64).item())
+        rays += int((ns > 0).sum().item())
+        prep = ds.prepare(mv, proj, out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            ds.launch(prep, stream)
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                ds.launch(prep, stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms += [a.elapsed_time(b) for a, b in ev]
+    per_frame = statistics.mean(ms)
+    return {"cameras": count, "camera_distance": f"{dist}x box diagonal",
+            "ms_per_frame": per_frame, "samples_per_frame": samples / count,
+            "hit_rays_per_frame": rays / count,
+            "samples_per_s": (samples / count) / (per_frame * 1e-3)}
+
+
 def run_learned(args, dev, stream, flush):
     """Bubble workload (512^3 scalar: an ellipsoidal shell moving through
     mostly empty space, 1920x1080): train the interval proposal on traced
@@ -537,7 +577,9 @@ def run_learned(args, dev, stream, flush):
     t_train = time.perf_counter() - t1
 
     kinds = ("plain_f32", "skip_f32", "learned_f32", "plain_bf16", "learned_bf16")
-    acc = {k: {"ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0} for k in kinds}
+    acc = {k: {"ms": [], "march_ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0}
+           for k in kinds}
+    grid_ms, range_ms = [], []
     stats = torch.zeros(2, dtype=torch.int32, device=dev)
     for f in (5, 35, 65, 95):
         field = synth.bubble_field(n, f, 0, noise=noise, device=dev)
@@ -585,15 +627,37 @@ def run_learned(args, dev, stream, flush):
                         run(kind)
                     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                           for _ in range(3)]
+                    mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(3)]
+                    for a, b in mev:
+                        a.record(stream)
+                        b.record(stream)
                     torch.cuda.nvtx.range_push(f"timed_{kind}")
-                    for a, b in ev:
+                    for (a, b), (ma, mb) in zip(ev, mev):
                         flush.zero_()
+                        isaac.time_march(ma, mb)
                         a.record(stream)
                         run(kind)
                         b.record(stream)
                     torch.cuda.nvtx.range_pop()
                 torch.cuda.synchronize()
+                isaac.time_march()
                 acc[kind]["ms"] += [a.elapsed_time(b) for a, b in ev]
+                acc[kind]["march_ms"] += [a.elapsed_time(b) for a, b in mev]
+            # the per-frame grids alone (part of the learned / skip frames above)
+            for fn, sink in ((lambda: ds.opacity_grid(cell, out=grid, stream=stream), grid_ms),
+                             (lambda: ds.range_grid(cell, out=ranges, stream=stream), range_ms)):
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(3)]
+                with torch.cuda.stream(stream):
+                    fn()
+                    for a, b in ev:
+                        flush.zero_()
+                        a.record(stream)
+                        fn()
+                        b.record(stream)
+                torch.cuda.synchronize()
+                sink += [a.elapsed_time(b) for a, b in ev]
             del ds, pv
     frames = len(acc["plain_f32"]["ms"]) // 3
     seen, restricted = stats.tolist()
@@ -601,11 +665,13 @@ def run_learned(args, dev, stream, flush):
            "train_steps": args.learned_steps, "train_s": t_train, "data_s": t_data,
            "final_loss": float(loss.item()), "threshold": args.learned_threshold,
            "margin": args.learned_margin, "restricted_frac": restricted / max(1, seen),
-           "test_frames": frames}
+           "test_frames": frames,
+           "opacity_grid_ms": statistics.mean(grid_ms), "range_grid_ms": statistics.mean(range_ms)}
     for kind in kinds:
         a = acc[kind]
         ms = statistics.mean(a["ms"])
         res[kind] = {"ms_per_frame": ms, "fps": 1e3 / ms,
+                     "march_ms": statistics.mean(a["march_ms"]),
                      "samples_per_frame": a["samples"] / frames,
                      "lsb_vs_plain_f32_mean": a["lsb_sum"] / max(1, a["px"]),
                      "lsb_vs_plain_f32_max": a["lsb_max"]}

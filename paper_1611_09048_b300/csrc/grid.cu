@@ -215,12 +215,20 @@ static __global__ void __launch_bounds__(256) k_grid_reduce(const __grid_constan
         const int gi = (int)(m % p.gx), gj = (int)((m / p.gx) % p.gy), k = (int)(m / ((long long)p.gx * p.gy));
         const int xs = max(gi * p.cell - 1, -1) + 1, xe = min((gi + 1) * p.cell, p.nx) + 1;
         const int ys = max(gj * p.cell - 1, -1) + 1, ye = min((gj + 1) * p.cell, p.ny) + 1;
-        const int wx = xe - xs + 1, n = wx * (ye - ys + 1);
-        const float *base = p.cols + (long long)k * plane + (long long)ys * p.W + xs;
+        const float *base = p.cols + (long long)k * plane;
         float mx = 0.0f;
-        for (int e = lane; e < n; e += 32) {
-            const int r = e / wx;
-            mx = fmaxf(mx, __ldg(base + (long long)r * p.W + (e - r * wx)));
+        // lanes along x, 8 rows' loads issued together (the data sits in L2,
+        // so the reduction is bound by load latency, not bytes)
+        for (int x0 = xs; x0 <= xe; x0 += 32) {
+            const int xx = x0 + lane;
+            for (int y0 = ys; y0 <= ye; y0 += 8) {
+                float v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    v[r] = (xx <= xe && y0 + r <= ye) ? __ldg(base + (long long)(y0 + r) * p.W + xx) : 0.0f;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) mx = fmaxf(mx, v[r]);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -362,16 +370,27 @@ static __global__ void __launch_bounds__(256) k_range_reduce(const __grid_consta
         const int gi = (int)(m % p.gx), gj = (int)((m / p.gx) % p.gy), k = (int)(m / ((long long)p.gx * p.gy));
         const int xs = max(gi * p.cell - 1, -1) + 1, xe = min((gi + 1) * p.cell, p.nx) + 1;
         const int ys = max(gj * p.cell - 1, -1) + 1, ye = min((gj + 1) * p.cell, p.ny) + 1;
-        const int wx = xe - xs + 1, n = wx * (ye - ys + 1);
-        const float2 *base = p.cols + ((long long)k * plane + (long long)ys * p.W + xs) * FD;
+        const float2 *base = p.cols + (long long)k * plane * FD;
         float2 r[FD];
 #pragma unroll
         for (int c = 0; c < FD; ++c) r[c] = make_float2(inf, -inf);
-        for (int e = lane; e < n; e += 32) {
-            const int row = e / wx;
-            const float2 *q = base + ((long long)row * p.W + (e - row * wx)) * FD;
+        // lanes along x, 4 rows' loads issued together (L2 latency bound)
+        for (int x0 = xs; x0 <= xe; x0 += 32) {
+            const int xx = x0 + lane;
+            for (int y0 = ys; y0 <= ye; y0 += 4) {
+                float2 v[4][FD];
 #pragma unroll
-            for (int c = 0; c < FD; ++c) r[c] = range_join(r[c], __ldg(q + c));
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < FD; ++c)
+                        v[q][c] = (xx <= xe && y0 + q <= ye)
+                                      ? __ldg(base + ((long long)(y0 + q) * p.W + xx) * FD + c)
+                                      : make_float2(inf, -inf);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int c = 0; c < FD; ++c) r[c] = range_join(r[c], v[q][c]);
+            }
         }
 #pragma unroll
         for (int c = 0; c < FD; ++c) {

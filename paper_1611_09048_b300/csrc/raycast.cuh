@@ -632,6 +632,8 @@ __device__ __forceinline__ void write_pixel(const KParams &p, int pix, float C0,
 }
 
 // Background for every pixel outside the rectangle; resets the counters.
+// Rows are spread over the blocks and a row's pixels over the threads (W*H is
+// at most 2^30, so pixel indices fit an int).
 static __global__ void k_fill_background(const __grid_constant__ KParams p)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.ctr) {
@@ -640,13 +642,14 @@ static __global__ void k_fill_background(const __grid_constant__ KParams p)
         p.ctr->n_long = 0u;
         p.ctr->next_long = 0u;
     }
-    const size_t total = (size_t)p.W * (size_t)p.H;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / (size_t)p.W), x = (int)(i - (size_t)y * p.W);
-        if (x >= p.rx0 && x < p.rx1 && y >= p.ry0 && y < p.ry1) continue;
-        write_pixel(p, (int)i, 0.0f, 0.0f, 0.0f, 0.0f, 0);
-        if (p.depth) p.depth[i] = __int_as_float(0x7f800000);
+    for (int y = blockIdx.x; y < p.H; y += gridDim.x) {
+        const bool row_in = y >= p.ry0 && y < p.ry1;
+        for (int x = threadIdx.x; x < p.W; x += blockDim.x) {
+            if (row_in && x >= p.rx0 && x < p.rx1) continue;
+            const int i = y * p.W + x;
+            write_pixel(p, i, 0.0f, 0.0f, 0.0f, 0.0f, 0);
+            if (p.depth) p.depth[i] = __int_as_float(0x7f800000);
+        }
     }
 }
 

@@ -59,7 +59,7 @@ extern const int k_n_zc_entries = (int)(sizeof(k_entries) / sizeof(k_entries[0])
 // The setup, background and copy kernels are launched from this translation unit.
 void launch_fill(const KParams &p, cudaStream_t st)
 {
-    const int blocks = (int)std::min<long long>(((long long)p.W * p.H + 255) / 256, 148LL * 8);
+    const int blocks = std::max(1, std::min(p.H, 148 * 8));
     k_fill_background<<<blocks, 256, 0, st>>>(p);
 }
 

@@ -86,3 +86,21 @@ def test_grid_scalar_identity_ragged(cuda_ok, guard, cell):
         np.testing.assert_allclose(got, want, rtol=0, atol=TOL_ALPHA)
         if wgt < 0:
             assert np.all(got.view(np.uint32) == 0)       # +0, never -0
+
+
+def test_grid_wide_volume_warp_reduction(cuda_ok):
+    """A very wide, thin volume (5000 x 3 x 4): long rows of column maxima
+    and macro cells clipped to 3 and 4 cells in y and z."""
+    import torch
+    from scenes_util import make_scene
+    n = (5000, 3, 4)
+    rng = np.random.default_rng(77)
+    ramp = (np.arange(n[0], dtype=np.float32) / n[0])[None, None, :]
+    f = (0.1 + 0.8 * ramp + 0.05 * rng.random((n[2], n[1], n[0]), np.float32)).astype(np.float32)
+    cams = synth.random_orbit_camera(n, 16, 16, seed=6)
+    sc = make_scene([f], [[]], [synth.lut_from_points(90)], [0.9], n, cams, 16, 16)
+    for cell in (16, 7):
+        g = isaac.DeviceScene(sc).opacity_grid(cell)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(g.cpu().numpy(), oracle.opacity_grid(sc, cell), rtol=0,
+                                   atol=TOL_ALPHA)

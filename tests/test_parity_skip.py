@@ -126,3 +126,24 @@ def test_range_grid_ragged_with_nan(cuda_ok, guard, cell):
     assert got.shape == want.shape
     assert np.isinf(want).any()                       # some cell reads a NaN
     np.testing.assert_array_equal(got.cpu().numpy(), want)
+
+
+def test_range_grid_wide_vector_volume(cuda_ok):
+    """A very wide, thin 3-component volume (4000 x 3 x 3) with guards and a
+    NaN: bit-exact against the oracle."""
+    import torch
+    from scenes_util import make_scene
+    n = (4000, 3, 3)
+    g = 1
+    rng = np.random.default_rng(78)
+    f = rng.standard_normal((n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g, 3)).astype(np.float32)
+    f[1, 1, 1500, 2] = np.nan
+    cams = synth.random_orbit_camera(n, 16, 16, seed=7)
+    sc = make_scene([f], [[("length",)]], [synth.lut_from_points(91)], [1.0], n, cams, 16, 16,
+                    guard=g)
+    for cell in (16, 5):
+        got = isaac.DeviceScene(sc).range_grid(cell)
+        torch.cuda.synchronize()
+        want = oracle.range_grid(sc, cell)
+        assert np.isinf(want).any()
+        np.testing.assert_array_equal(got.cpu().numpy(), want)

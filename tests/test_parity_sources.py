@@ -146,3 +146,41 @@ def test_update_callback_with_one_scratch_buffer(cuda_ok):
     for a, b in zip(want, shared):
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
     assert not np.array_equal(shared[1], ref[1])
+
+
+def _slab_scene(field, guard, n, width=64, height=48, term=0.99):
+    """One scalar source over an n[0] x n[1] x n[2] box, seen obliquely."""
+    from scenes_util import make_scene
+    cams = synth.random_orbit_camera(n, width, height, seed=17, dist_factor=1.4)
+    return make_scene([field], [[("mul", (1.5,))]], [synth.lut_from_points(88, alpha_max=0.4)],
+                      [1.0], n, cams, width, height, guard=guard, term=term)
+
+
+@pytest.mark.parametrize("guard", [0, 1])
+def test_two_dimensional_source(cuda_ok, guard):
+    """A 2D field (n_z = 1) is a volume one cell thick: its frame equals the
+    oracle's, with guards (the layers above and below are read) and without
+    (z clamps to the one layer)."""
+    n = (40, 28, 1)
+    rng = np.random.default_rng(3 + guard)
+    f = rng.random((1 + 2 * guard, 28 + 2 * guard, 40 + 2 * guard), np.float32)
+    sc = _slab_scene(f, guard, n)
+    g8, g32, gns = _render(isaac.DeviceScene(sc))
+    rep = compare(g32, g8, gns, oracle.render(sc))
+    assert_parity(rep, 1e-3, f"2D source, guard {guard}")
+    assert rep.hit > 100
+
+
+def test_time_series_as_z(cuda_ok):
+    """Time steps of a 2D field stacked along z (time-as-z) form an ordinary
+    source: its frame equals the oracle's."""
+    T, ny, nx = 12, 20, 36
+    t = np.arange(T, dtype=np.float32)[:, None, None]
+    y = np.arange(ny, dtype=np.float32)[None, :, None]
+    x = np.arange(nx, dtype=np.float32)[None, None, :]
+    stack = (0.5 + 0.4 * np.sin(0.3 * x + 0.2 * y - 0.5 * t)).astype(np.float32)
+    sc = _slab_scene(stack, 0, (nx, ny, T))
+    g8, g32, gns = _render(isaac.DeviceScene(sc))
+    rep = compare(g32, g8, gns, oracle.render(sc))
+    assert_parity(rep, 1e-3, "time-as-z stack")
+    assert rep.hit > 200
