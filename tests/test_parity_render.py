@@ -208,3 +208,31 @@ def test_axis_aligned_clip_planes_shrink_the_rectangle(cuda_ok, clip):
         assert rep.hit == 0 and np.all(gns == 0)
     else:
         assert rep.hit > 100
+
+
+@pytest.fixture(scope="module")
+def pic512_device():
+    """The bench's headline workload: 512^3 + 4 guards E/B/rho, 1920x1080."""
+    sc = synth.scene_pic(n=512, guard=4, width=1920, height=1080, seed=0)
+    return sc, isaac.DeviceScene(sc)
+
+
+@pytest.mark.parametrize("cam", [3, 20])
+def test_pic_512_1080p_sampled_bench_cameras(cuda_ok, pic512_device, cam):
+    """Full size, in the launch configuration the bench times (default lanes
+    per ray, one of its 32 Fibonacci cameras): the whole frame on the GPU,
+    the oracle on sampled pixels."""
+    import torch
+    sc, ds = pic512_device
+    mv, proj = synth.fibonacci_cameras((512, 512, 512), 1920, 1080, count=32, seed=0)[cam]
+    out, f32, ns = ds.render(mv, proj, want_f32=True, want_nsamp=True)
+    torch.cuda.synchronize()
+    g8, g32, gns = out.cpu().numpy(), f32.cpu().numpy(), ns.cpu().numpy()
+    rng = np.random.default_rng(cam)
+    hit = np.flatnonzero(gns.reshape(-1) > 0)
+    assert hit.size > 50000
+    pix = np.concatenate([rng.choice(hit, 2500, replace=False),
+                          rng.choice(gns.size, 500, replace=False)])
+    r = oracle.render(sc.with_camera(mv, proj), pixels=pix)
+    rep = compare(g32, g8, gns, r, sel=pix)
+    assert_parity(rep, 2e-3, f"pic 512 1080p camera {cam}")
