@@ -133,7 +133,7 @@ struct RecIO<ISAAC_E4M3, PAD> {
 };
 
 template <int PAD>
-__device__ __forceinline__ void load_scales(const float *s, long long brick, float (&v)[PAD])
+__device__ __forceinline__ void load_scales(const float *s, int brick, float (&v)[PAD])
 {
     const float *p = s + brick * PAD;
     if constexpr (PAD == 1) {
@@ -355,16 +355,20 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
         IO::load(p.rec, ((long long)z * PY + y) * PX + x, v);
         if constexpr (DT == ISAAC_E4M3) {
             float s[PAD];
-            load_scales<PAD>(p.scales, ((long long)(z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
+            load_scales<PAD>(p.scales, ((z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
 #pragma unroll
             for (int c = 0; c < PAD; ++c) v[c] *= s[c];
         }
         return;
     }
-    // corners in packed coordinates (cell -1 -> 0), clamped into the box
+    // corners in packed coordinates (cell -1 -> 0), clamped into the box; the
+    // record of corner 000 in 64 bits, the other corners at 32-bit offsets
+    // from it (a plane of the copy holds at most 4098^2 records)
     const int x0 = min(max(g.ix, -1), p.nx) + 1, x1 = min(max(g.ix + 1, -1), p.nx) + 1;
     const int y0 = min(max(g.iy, -1), p.ny) + 1, y1 = min(max(g.iy + 1, -1), p.ny) + 1;
     const int z0 = min(max(g.iz, -1), p.nz) + 1, z1 = min(max(g.iz + 1, -1), p.nz) + 1;
+    const unsigned char *r000 = p.rec + (((long long)z0 * PY + y0) * PX + x0) * IO::BYTES;
+    const int ox = x1 - x0, oy = (y1 - y0) * (int)PX, oz = (z1 - z0) * (int)(PX * PY);
     if constexpr (DT == ISAAC_E4M3) {
         // each corner may lie in another brick: accumulate weight * scale * code
         // corner by corner (keeps one corner's record live at a time)
@@ -376,8 +380,8 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
             const float w = ((k & 1) ? g.fx : 1.0f - g.fx) * ((k & 2) ? g.fy : 1.0f - g.fy) *
                             ((k & 4) ? g.fz : 1.0f - g.fz);
             float cv[PAD], s[PAD];
-            IO::load(p.rec, ((long long)z * PY + y) * PX + x, cv);
-            load_scales<PAD>(p.scales, ((long long)(z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
+            IO::load(r000, ((k & 1) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 4) ? oz : 0), cv);
+            load_scales<PAD>(p.scales, ((z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
 #pragma unroll
             for (int q = 0; q < PAD; ++q) v[q] = fmaf(w * s[q], cv[q], v[q]);
         }
@@ -386,14 +390,7 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
     float c[8][PAD];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int x = (k & 1) ? x1 : x0, y = (k & 2) ? y1 : y0, z = (k & 4) ? z1 : z0;
-        IO::load(p.rec, ((long long)z * PY + y) * PX + x, c[k]);
-        if constexpr (DT == ISAAC_E4M3) {
-            float s[PAD];
-            load_scales<PAD>(p.scales, ((long long)(z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
-#pragma unroll
-            for (int q = 0; q < PAD; ++q) c[k][q] *= s[q];
-        }
+        IO::load(r000, ((k & 1) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 4) ? oz : 0), c[k]);
     }
 #pragma unroll
     for (int q = 0; q < PAD; ++q) {
