@@ -937,7 +937,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal comparison on the bubble workload")
     ap.add_argument("--learned-n", type=int, default=512)
-    ap.add_argument("--learned-views", type=int, default=10)
+    ap.add_argument("--learned-views", type=int, default=14)
     ap.add_argument("--learned-test-views", type=int, default=2)
     ap.add_argument("--learned-steps", type=int, default=1500)
     ap.add_argument("--learned-threshold", type=float, default=0.9)
