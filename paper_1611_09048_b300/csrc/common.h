@@ -25,6 +25,10 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
                    int elem, KSource &ks, unsigned *nib, bool *wide);
 int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
 int prepare_fb(const isaac_framebuffer *fb, KParams &p);
+// Multiprocessor count of the current device (cached per device; 148 if the
+// query fails).
+int sm_count();
+
 // Calls the calling thread's update hook (isaac_set_update_hook), if any, for
 // every source in order (with its active bit), before an entry point reads the
 // descriptors.

@@ -117,9 +117,7 @@ extern "C" int isaac_composite(const float *const *layers_rgba32, const float *c
     p.npix = (long long)width * height;
     p.out8 = reinterpret_cast<uchar4 *>(rgba8);
     p.out32 = reinterpret_cast<float4 *>(rgba32);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+    const int sms = sm_count();
     const long long blocks = std::max(1LL, std::min((p.npix + 255) / 256, (long long)sms * 8));
     composite_fn(n_layers, std::make_integer_sequence<int, kMaxLayers>{})
         <<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);

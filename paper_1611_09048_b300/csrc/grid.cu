@@ -483,19 +483,6 @@ int launch_empty_flags(const KParams &kp, int nact, const float *ranges, int slo
 
 }  // namespace isaac
 
-namespace isaac {
-static int sm_count_grid()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
-    }
-    return n;
-}
-}  // namespace isaac
-
 using namespace isaac;
 
 extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain *chains,
@@ -562,7 +549,7 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
     int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
     if (rc) return rc;
     p.cols = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
-    const int sms = sm_count_grid();
+    const int sms = sm_count();
     const long long items = (long long)p.W * p.H * p.nchunks;
     const unsigned b1 = (unsigned)std::max(1LL, std::min((items + 255) / 256, (long long)sms * 4));
     const bool scalar = p.nact == 1 && p.src[0].fdim == 1 && p.ch[0].n == 0;
@@ -640,7 +627,7 @@ extern "C" int isaac_range_grid(const isaac_source *sources, int32_t n_sources,
     int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
     if (rc) return rc;
     r.cols = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
-    const int sms = sm_count_grid();
+    const int sms = sm_count();
     const long long items = (long long)r.W * r.H * r.nchunks;
     const unsigned b1 = (unsigned)std::max(1LL, std::min((items + 255) / 256, (long long)sms * 4));
     const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));

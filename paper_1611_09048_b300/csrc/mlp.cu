@@ -546,9 +546,7 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     p.stats = pr->stats;
     const int smem = kPropSmemHalves * 2;
     cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+    const int sms = sm_count();
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
     const long long blocks = std::max(1LL, std::min<long long>((rect + 16 * kPropWarps - 1) / (16 * kPropWarps),
                                                               (long long)sms * 2));

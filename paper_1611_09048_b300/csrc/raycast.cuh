@@ -686,10 +686,7 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
 // group evaluate samples k+0 .. k+RL-1 together; every lane then composites
 // the group's RL samples in order, stopping at the termination sample, so all
 // lanes hold the same C and A.
-// S > 1 (long rays): each lane evaluates S samples per step, k + s*RL + sub
-// for s < S, so that a step has RL*S samples' gathers in flight at once; they
-// are composited in sample order like the rest.
-template <class Shader, int RL, bool LABEL, bool SKIP_LONG = false, bool SKIP_EMPTY = false, int S = 1>
+template <class Shader, int RL, bool LABEL, bool SKIP_LONG = false, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut, unsigned idx,
                                           int lane)
 {
@@ -699,7 +696,7 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     int ns = 0, jf = -1, jl = -1;
     const unsigned gmask = (RL == 32) ? 0xffffffffu : (((1u << RL) - 1u) << (lane & ~(RL - 1)));
-    for (int k = r.kbeg; k < r.nsteps; k += RL * S) {
+    for (int k = r.kbeg; k < r.nsteps; k += RL) {
         if (SKIP_EMPTY) {
             // The macro cell that owns sample k's position: if it is marked
             // empty, jump to the first sample at or past the ray's exit from its
@@ -722,20 +719,14 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
                                : (r.dz < 0.0f ? ((float)mz * cz - z) / r.dz : inf);
                 const float se = fminf(ex, fminf(ey, ez));
                 const int jump = se > 0.0f ? (int)fminf(ceilf(se / p.step), 1.0e9f) : 1;
-                k += max(jump, 1) - RL * S;   // the loop adds RL * S
+                k += max(jump, 1) - RL;   // the loop adds RL
                 continue;
             }
         }
-        float4 cs[S];
-#pragma unroll
-        for (int q = 0; q < S; ++q) {
-            const int kk = k + q * RL + sub;
-            cs[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (kk < r.nsteps) {
-                const float s = (float)kk * p.step;
-                cs[q] = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey),
-                                      fmaf(s, r.dz, r.ez));
-            }
+        float4 cs = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (k + sub < r.nsteps) {
+            const float s = (float)(k + sub) * p.step;
+            cs = Shader::shade(p, s_lut, fmaf(s, r.dx, r.ex), fmaf(s, r.dy, r.ey), fmaf(s, r.dz, r.ez));
         }
         bool done = false;
         auto composite = [&](const float4 &c, int kq, int j) {
@@ -761,15 +752,12 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
                 done = A >= p.term;
             }
         };
+        if constexpr (RL <= 8) {
 #pragma unroll
-        for (int q = 0; q < S; ++q) {
-            if constexpr (RL <= 8) {
-#pragma unroll
-                for (int j = 0; j < RL; ++j) composite(cs[q], k + q * RL, j);
-            } else {   // wide groups: a partly rolled loop keeps the register count down
+            for (int j = 0; j < RL; ++j) composite(cs, k, j);
+        } else {   // wide groups: a partly rolled loop keeps the register count down
 #pragma unroll 4
-                for (int j = 0; j < RL; ++j) composite(cs[q], k + q * RL, j);
-            }
+            for (int j = 0; j < RL; ++j) composite(cs, k, j);
         }
         if (done) break;
     }

@@ -64,7 +64,7 @@ int bind_workspace(KParams &p, cudaStream_t st, size_t extra, void **extra_ptr)
     return ISAAC_OK;
 }
 
-static int sm_count()
+int sm_count()
 {
     static int cached[64] = {0};
     int dev = 0;

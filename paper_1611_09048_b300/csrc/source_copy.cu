@@ -54,17 +54,6 @@ static __global__ void __launch_bounds__(kCopyThreads) k_copy_source(const __gri
     }
 }
 
-static int sm_count_copy()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
-    }
-    return n;
-}
-
 // The update hook (per calling thread).
 static thread_local isaac_update_fn t_update = nullptr;
 static thread_local void *t_update_user = nullptr;
@@ -112,7 +101,7 @@ extern "C" int isaac_copy_source(const isaac_source *src, const int64_t n[3], vo
     p.dst = static_cast<float *>(dst);
     if ((long long)X * p.fdim > 0x7fffffffLL) return fail(ISAAC_ENOTSUP, "a row of the copy is too long");
     const long long rows = Y * Z;
-    const unsigned blocks = (unsigned)std::max(1LL, std::min(rows, (long long)sm_count_copy() * 8));
+    const unsigned blocks = (unsigned)std::max(1LL, std::min(rows, (long long)sm_count() * 8));
     const cudaStream_t st = (cudaStream_t)stream;
     switch (p.fdim) {
     case 1: k_copy_source<1><<<blocks, kCopyThreads, 0, st>>>(p); break;
