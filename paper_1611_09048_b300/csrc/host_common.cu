@@ -179,6 +179,16 @@ int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out)
         }
     }
     out.n = n;
+    const int c0 = n > 0 ? out.op[0].code : 0, c1 = n > 1 ? out.op[1].code : 0;
+    const int c2 = n > 2 ? out.op[2].code : 0;
+    out.shape = CH_GENERIC;
+    if (n == 0) out.shape = CH_IDENTITY;
+    else if (n == 1 && c0 == K_AFFINE) out.shape = CH_AFFINE;
+    else if (n == 1 && c0 == K_LENGTH) out.shape = CH_LENGTH;
+    else if (n == 2 && c0 == K_LENGTH && c1 == K_AFFINE) out.shape = CH_LENGTH_AFFINE;
+    else if (n == 3 && c0 == K_LENGTH && c1 == K_AFFINE && c2 == K_SQRT) out.shape = CH_LENGTH_AFFINE_SQRT;
+    else if (n == 1 && c0 == K_LOG) out.shape = CH_LOG;
+    else if (n == 2 && c0 == K_LOG && c1 == K_AFFINE) out.shape = CH_LOG_AFFINE;
     for (int i = n; i < ISAAC_MAX_FUNCTORS; ++i) {
         out.op[i].code = 0;
         out.op[i].dim = 1;

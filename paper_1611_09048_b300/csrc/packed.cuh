@@ -377,8 +377,7 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int x = (k & 1) ? x1 : x0, y = (k & 2) ? y1 : y0, z = (k & 4) ? z1 : z0;
-            const float w = ((k & 1) ? g.fx : 1.0f - g.fx) * ((k & 2) ? g.fy : 1.0f - g.fy) *
-                            ((k & 4) ? g.fz : 1.0f - g.fz);
+            const float w = g.w[k];
             float cv[PAD], s[PAD];
             IO::load(r000, ((k & 1) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 4) ? oz : 0), cv);
             load_scales<PAD>(p.scales, ((z >> 3) * p.by + (y >> 3)) * p.bx + (x >> 3), s);
@@ -394,9 +393,7 @@ __device__ __forceinline__ void sample_packed(const KParams &p, const Geo &g, fl
     }
 #pragma unroll
     for (int q = 0; q < PAD; ++q) {
-        const float c00 = lerp1(c[0][q], c[1][q], g.fx), c10 = lerp1(c[2][q], c[3][q], g.fx);
-        const float c01 = lerp1(c[4][q], c[5][q], g.fx), c11 = lerp1(c[6][q], c[7][q], g.fx);
-        v[q] = lerp1(lerp1(c00, c10, g.fy), lerp1(c01, c11, g.fy), g.fz);
+        v[q] = tri(g, c[0][q], c[1][q], c[2][q], c[3][q], c[4][q], c[5][q], c[6][q], c[7][q]);
     }
 }
 

@@ -44,8 +44,16 @@ struct KOp {
     float b[4];       // AFFINE: offset
 };
 
+// Folded chain shapes the kernels run as straight-line code on the first
+// component (the only one a chain's result depends on); others are interpreted.
+enum : int {
+    CH_GENERIC = 0, CH_IDENTITY = 1, CH_AFFINE = 2, CH_LENGTH = 3, CH_LENGTH_AFFINE = 4,
+    CH_LENGTH_AFFINE_SQRT = 5, CH_LOG = 6, CH_LOG_AFFINE = 7
+};
+
 struct KChain {
     int n;
+    int shape;        // CH_*: set by compile_chain from the folded op list
     KOp op[ISAAC_MAX_FUNCTORS];
 };
 
@@ -151,10 +159,41 @@ __device__ __forceinline__ unsigned char quant8(float x)
     return (unsigned char)fminf(q, 255.0f);
 }
 
+__device__ __forceinline__ float chain_length(int d, const float v[4])
+{
+    float s = v[0] * v[0];
+    if (d > 1) s = fmaf(v[1], v[1], s);
+    if (d > 2) s = fmaf(v[2], v[2], s);
+    if (d > 3) s = fmaf(v[3], v[3], s);
+    return sqrtf(s);
+}
+
 // Functor chain of one source (Sec. 3.3, Table 1).  The op list is uniform
-// across the launch, so every branch below is uniform across the warp.
+// across the launch, so every branch below is uniform across the warp.  The
+// common folded shapes run as straight-line code on component 0 with the
+// same operations, in the same order, as the op-by-op loop.
 __device__ __forceinline__ float run_chain(const KChain &ch, float v[4])
 {
+    switch (ch.shape) {
+    case CH_IDENTITY:
+        return v[0];
+    case CH_AFFINE:
+        return fmaf(ch.op[0].a[0], v[0], ch.op[0].b[0]);
+    case CH_LENGTH:
+        return chain_length(ch.op[0].dim, v);
+    case CH_LENGTH_AFFINE:
+        return fmaf(ch.op[1].a[0], chain_length(ch.op[0].dim, v), ch.op[1].b[0]);
+    case CH_LENGTH_AFFINE_SQRT: {
+        const float x = fmaf(ch.op[1].a[0], chain_length(ch.op[0].dim, v), ch.op[1].b[0]);
+        return x > 0.0f ? sqrtf(x) : 0.0f;
+    }
+    case CH_LOG:
+        return logf(fmaxf(v[0], 1e-30f));
+    case CH_LOG_AFFINE:
+        return fmaf(ch.op[1].a[0], logf(fmaxf(v[0], 1e-30f)), ch.op[1].b[0]);
+    default:
+        break;
+    }
 #pragma unroll 1
     for (int i = 0; i < ch.n; ++i) {
         const KOp &o = ch.op[i];
@@ -172,13 +211,9 @@ __device__ __forceinline__ float run_chain(const KChain &ch, float v[4])
 #pragma unroll
             for (int c = 0; c < 4; ++c) v[c] *= o.a[c];
             break;
-        case K_LENGTH: {
-            float s = v[0] * v[0];
-            if (d > 1) s = fmaf(v[1], v[1], s);
-            if (d > 2) s = fmaf(v[2], v[2], s);
-            if (d > 3) s = fmaf(v[3], v[3], s);
-            v[0] = sqrtf(s);
-        } break;
+        case K_LENGTH:
+            v[0] = chain_length(d, v);
+            break;
         case K_SUM: {
             float s = v[0];
             if (d > 1) s += v[1];
@@ -334,7 +369,8 @@ __device__ __forceinline__ void blend(float4 &acc, float w, float4 c)
 // Geometry of one sample shared by all sources.
 struct Geo {
     int ix, iy, iz;      // lower corner (trilinear) or the cell (nearest), unclamped
-    float fx, fy, fz;    // trilinear weights
+    float fx, fy, fz;    // fractional position in the corner cell
+    float w[8];          // trilinear weight of corner k (bit 0: x+1, bit 1: y+1, bit 2: z+1)
 };
 
 template <int INTERP>
@@ -350,13 +386,41 @@ __device__ __forceinline__ Geo sample_geo(float x, float y, float z)
         g.fx = qx - flx;
         g.fy = qy - fly;
         g.fz = qz - flz;
+        // the 8 corner weights, once per sample for every source and component
+        const float gx = 1.0f - g.fx, gy = 1.0f - g.fy, gz = 1.0f - g.fz;
+        const float a00 = gy * gz, a10 = g.fy * gz, a01 = gy * g.fz, a11 = g.fy * g.fz;
+        g.w[0] = gx * a00;
+        g.w[1] = g.fx * a00;
+        g.w[2] = gx * a10;
+        g.w[3] = g.fx * a10;
+        g.w[4] = gx * a01;
+        g.w[5] = g.fx * a01;
+        g.w[6] = gx * a11;
+        g.w[7] = g.fx * a11;
     } else {
         g.ix = (int)floorf(x);
         g.iy = (int)floorf(y);
         g.iz = (int)floorf(z);
         g.fx = g.fy = g.fz = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g.w[k] = 0.0f;
     }
     return g;
+}
+
+// Trilinear value from the 8 corner values (corner k as in Geo::w): the
+// weighted sum, one multiply and seven fused multiply-adds per component.
+__device__ __forceinline__ float tri(const Geo &g, float c0, float c1, float c2, float c3, float c4,
+                                     float c5, float c6, float c7)
+{
+    float v = c0 * g.w[0];
+    v = fmaf(g.w[1], c1, v);
+    v = fmaf(g.w[2], c2, v);
+    v = fmaf(g.w[3], c3, v);
+    v = fmaf(g.w[4], c4, v);
+    v = fmaf(g.w[5], c5, v);
+    v = fmaf(g.w[6], c6, v);
+    return fmaf(g.w[7], c7, v);
 }
 
 template <typename Idx>
@@ -412,13 +476,9 @@ __device__ __forceinline__ void fetch_source(const KParams &p, const Geo &g, flo
                 ld_pair3(base + (ox0 + o01), r01);
                 ld_pair3(base + (ox0 + o11), r11);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float c00 = lerp1(r00[c], r00[3 + c], g.fx);
-                    const float c10 = lerp1(r10[c], r10[3 + c], g.fx);
-                    const float c01 = lerp1(r01[c], r01[3 + c], g.fx);
-                    const float c11 = lerp1(r11[c], r11[3 + c], g.fx);
-                    v[c] = lerp1(lerp1(c00, c10, g.fy), lerp1(c01, c11, g.fy), g.fz);
-                }
+                for (int c = 0; c < 3; ++c)
+                    v[c] = tri(g, r00[c], r00[3 + c], r10[c], r10[3 + c], r01[c], r01[3 + c], r11[c],
+                               r11[3 + c]);
                 v[3] = 0.0f;
                 return;
             }
@@ -431,11 +491,8 @@ __device__ __forceinline__ void fetch_source(const KParams &p, const Geo &g, flo
         for (int c = 0; c < 4; ++c) {
             if (c < fd) {
                 const Idx co = Idx(c) * cs;
-                const float c00 = lerp1(ld(p000, co), ld(p100, co), g.fx);
-                const float c10 = lerp1(ld(p010, co), ld(p110, co), g.fx);
-                const float c01 = lerp1(ld(p001, co), ld(p101, co), g.fx);
-                const float c11 = lerp1(ld(p011, co), ld(p111, co), g.fx);
-                v[c] = lerp1(lerp1(c00, c10, g.fy), lerp1(c01, c11, g.fy), g.fz);
+                v[c] = tri(g, ld(p000, co), ld(p100, co), ld(p010, co), ld(p110, co), ld(p001, co),
+                           ld(p101, co), ld(p011, co), ld(p111, co));
             } else {
                 v[c] = 0.0f;
             }
