@@ -279,3 +279,32 @@ def test_pic_512_reduced_precision_error_32_cameras(cuda_ok, pic512_device):
         if fmt != "e4m3":
             assert e.max() <= 2e-3, (fmt, report[fmt])
     print("reduced-precision error vs FP64 oracle, pic512 1080p, 32 cameras:", json.dumps(report))
+
+
+@pytest.mark.parametrize("chains", [
+    [[("length",), ("mul", (0.5,))], [("log",)], [("mul", (2.0,)), ("add", (-0.3,))],
+     [("length",), ("log",), ("mul", (0.1,)), ("add", (0.6,))]],
+    [[], [("length",)], [("log",), ("mul", (0.2,)), ("add", (0.5,))],
+     [("length",), ("mul", (0.4,)), ("add", (0.1,)), ("pow", (0.5,))]],
+])
+def test_every_chain_shape_against_oracle(cuda_ok, chains):
+    """Each folded chain shape the kernels run as straight-line code (identity,
+    affine, length, length+affine, length+affine+sqrt, log, log+affine) and a
+    chain they interpret op by op, on four sources of one frame."""
+    from scenes_util import make_scene
+    n = (22, 18, 20)
+    rng = np.random.default_rng(31)
+    fields = [rng.random((n[2], n[1], n[0], 3), np.float32) * 0.6,
+              rng.random((n[2], n[1], n[0]), np.float32) + 0.05,
+              rng.random((n[2], n[1], n[0]), np.float32),
+              rng.random((n[2], n[1], n[0], 2), np.float32)]
+    if chains[0] == []:
+        fields[0] = fields[0][..., 0].copy()
+        fields[1] = rng.random((n[2], n[1], n[0], 3), np.float32)
+        fields[2] = fields[2] + 0.05
+        fields[3] = rng.random((n[2], n[1], n[0], 3), np.float32)
+    cams = synth.random_orbit_camera(n, 56, 44, seed=12, dist_factor=1.3)
+    luts = [synth.lut_from_points(200 + i, alpha_max=0.15) for i in range(4)]
+    sc = make_scene(fields, chains, luts, [0.3, 0.3, 0.2, 0.2], n, cams, 56, 44)
+    rep, _, _ = _check(sc, f"chains {chains}")
+    assert rep.hit > 300
