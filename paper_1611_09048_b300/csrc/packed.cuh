@@ -416,7 +416,7 @@ struct PackedShader {
 
 // LONG: the long-ray march (MODE_LONG of k_raycast) instead of the march.
 template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL, bool LONG = false>
-__global__ void __launch_bounds__(128, 8) k_raycast_packed(const __grid_constant__ KParams p)
+__global__ void __launch_bounds__(kMarchThreads, kMarchBlocksPerSM) k_raycast_packed(const __grid_constant__ KParams p)
 {
     __shared__ float4 s_lut[NACT * 256];
     load_luts<NACT>(p, s_lut);

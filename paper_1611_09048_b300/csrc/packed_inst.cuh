@@ -8,7 +8,7 @@ namespace isaac {
 template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL, bool LONG>
 static void launch_packed(const KParams &p, dim3 grid, cudaStream_t st)
 {
-    k_raycast_packed<NACT, SIG, DT, PAD, INTERP, RL, LONG><<<grid, 128, 0, st>>>(p);
+    k_raycast_packed<NACT, SIG, DT, PAD, INTERP, RL, LONG><<<grid, kMarchThreads, 0, st>>>(p);
 }
 
 template <int DT, int PAD>

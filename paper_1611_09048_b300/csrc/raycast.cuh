@@ -93,6 +93,15 @@ struct WsCounters {
 constexpr int kLongRay = -2;
 // A proposal puts a ray in the long-ray list when it keeps more samples than this.
 constexpr int kLongRaySamples = 96;
+// Threads per block and blocks per SM of the frame kernels (k_raycast,
+// k_raycast_packed): 32 warps per SM, at most 64 registers per thread.  Each
+// block holds its own shared copy of the LUTs (4 KB per source), and shared
+// memory comes out of the SRAM that also serves the gathers as L1.  Measured
+// at pic512: 256-thread blocks (half the LUT copies) ran at the same speed;
+// LUT copies twice as large (a table of entry differences) halved the frame
+// rate, the L1 being too small for the gathers' working set.
+constexpr int kMarchThreads = 128, kMarchBlocksPerSM = 8;
+
 // Key under which the long-ray kernels are registered (the lanes that shade
 // one ray's samples per instruction); march_long holds kStreamRays rays per warp.
 constexpr int kLongRayLanes = 32;
@@ -875,8 +884,8 @@ template <class Shader>
 __device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut)
 {
     constexpr int kRow = kStreamT + 1;        // padded row: owners' reads hit distinct banks
-    __shared__ float4 s_tile[4][kStreamRays * kRow];   // 4 warps per block
-    float4 *tile = s_tile[(threadIdx.x >> 5) & 3];
+    __shared__ float4 s_tile[kMarchThreads / 32][kStreamRays * kRow];
+    float4 *tile = s_tile[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool owner = lane < kStreamRays;
@@ -1108,7 +1117,7 @@ __device__ __forceinline__ void load_luts(const KParams &p, float4 *s_lut)
 
 // The zero-copy frame kernel (128 threads, at most 64 registers per thread).
 template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, int MODE = MODE_PLAIN>
-__global__ void __launch_bounds__(128, 8) k_raycast(const __grid_constant__ KParams p)
+__global__ void __launch_bounds__(kMarchThreads, kMarchBlocksPerSM) k_raycast(const __grid_constant__ KParams p)
 {
     __shared__ float4 s_lut[NACT * 256];
     load_luts<NACT>(p, s_lut);

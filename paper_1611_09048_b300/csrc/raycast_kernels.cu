@@ -8,7 +8,7 @@ namespace isaac {
 template <int NACT, unsigned SIG, int INTERP, typename Idx, int RL, int MODE>
 static void launch_zc(const KParams &p, dim3 grid, cudaStream_t st)
 {
-    k_raycast<NACT, SIG, INTERP, Idx, RL, MODE><<<grid, 128, 0, st>>>(p);
+    k_raycast<NACT, SIG, INTERP, Idx, RL, MODE><<<grid, kMarchThreads, 0, st>>>(p);
 }
 
 // {nact, sig, interp, rl, wide, mode, launcher}

@@ -133,8 +133,8 @@ int launch_frame_with(KParams &p, FrameLaunch fn, int rl, cudaStream_t st, const
         if (rc) return rc;
     }
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-    const long long want = (rect * rl + 127) / 128;
-    const long long cap = (long long)sm_count() * 8;
+    const long long want = (rect * rl + kMarchThreads - 1) / kMarchThreads;
+    const long long cap = (long long)sm_count() * kMarchBlocksPerSM;
     if (t_march_start) cudaEventRecord(t_march_start, st);
     if (p.longs) fn_long(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
     fn(p, dim3((unsigned)std::max(1LL, std::min(want, cap))), st);
