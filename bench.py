@@ -599,7 +599,7 @@ def run_learned(args, dev, stream, flush):
     kinds = ("plain_f32", "skip_f32", "learned_f32", "plain_bf16", "learned_bf16")
     acc = {k: {"ms": [], "march_ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0}
            for k in kinds}
-    grid_ms, range_ms = [], []
+    grid_ms, grid16_ms, range_ms = [], [], []
     stats = torch.zeros(2, dtype=torch.int32, device=dev)
     for f in (5, 35, 65, 95):
         field = synth.bubble_field(n, f, 0, noise=noise, device=dev)
@@ -617,8 +617,10 @@ def run_learned(args, dev, stream, flush):
             nss = {k: torch.empty((H, W), dtype=torch.int32, device=dev) for k in kinds}
 
             def run(kind, count=None):
-                if kind.startswith("learned"):
+                if kind == "learned_f32":
                     ds.opacity_grid(cell, out=grid, stream=stream)
+                if kind == "learned_bf16":     # the grid of the copy the frame marches
+                    pv.opacity_grid(cell, out=grid, stream=stream)
                 if kind.startswith("skip"):
                     ds.range_grid(cell, out=ranges, stream=stream)
                 tgt = ds if kind.endswith("f32") else pv
@@ -666,6 +668,7 @@ def run_learned(args, dev, stream, flush):
                 acc[kind]["march_ms"] += [a.elapsed_time(b) for a, b in mev]
             # the per-frame grids alone (part of the learned / skip frames above)
             for fn, sink in ((lambda: ds.opacity_grid(cell, out=grid, stream=stream), grid_ms),
+                             (lambda: pv.opacity_grid(cell, out=grid, stream=stream), grid16_ms),
                              (lambda: ds.range_grid(cell, out=ranges, stream=stream), range_ms)):
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(3)]
@@ -686,7 +689,9 @@ def run_learned(args, dev, stream, flush):
            "final_loss": float(loss.item()), "threshold": args.learned_threshold,
            "margin": args.learned_margin, "restricted_frac": restricted / max(1, seen),
            "test_frames": frames,
-           "opacity_grid_ms": statistics.mean(grid_ms), "range_grid_ms": statistics.mean(range_ms)}
+           "opacity_grid_ms": statistics.mean(grid_ms),
+           "opacity_grid_bf16_ms": statistics.mean(grid16_ms),
+           "range_grid_ms": statistics.mean(range_ms)}
     for kind in kinds:
         a = acc[kind]
         ms = statistics.mean(a["ms"])
@@ -699,7 +704,8 @@ def run_learned(args, dev, stream, flush):
         res["learned_bf16"]["ms_per_frame"]
     res["speedup_skip_f32_vs_plain_f32"] = res["plain_f32"]["ms_per_frame"] / \
         res["skip_f32"]["ms_per_frame"]
-    res["note"] = ("learned_* include the per-frame max-opacity grid, skip_f32 the per-frame "
+    res["note"] = ("learned_* include the per-frame max-opacity grid (learned_bf16 computes it "
+                   "from its BF16 copy), skip_f32 the per-frame "
                    "value-range grid (the field changes every frame); skip_f32 is exact "
                    "(bit-identical to plain_f32), learned_* within the stated LSB")
     return res

@@ -556,6 +556,22 @@ int isaac_composite(const float *const *layers_rgba32, const float *const *layer
                     uint8_t *rgba8, float *rgba32, void *stream);
 
 /*
+ * isaac_opacity_grid_packed -- isaac_opacity_grid over a packed copy (built by
+ * isaac_pack): the same macro cells and rule, each cell's values read from
+ * its record of the [-1, n]^3 box (the apron holds the guards, or the
+ * repeated border, exactly the values isaac_opacity_grid reads there) and
+ * dequantised as isaac_render_packed does.  The result is the grid of the
+ * dequantised fields, with half (16-bit) or a quarter (E4M3) of the bytes to
+ * read.  chains, weights (host) and luts (device) are indexed by packed source
+ * as in isaac_render_packed; opts->n must equal vol->n; opts->active_mask
+ * selects packed sources.  Errors as isaac_opacity_grid and
+ * isaac_render_packed.
+ */
+int isaac_opacity_grid_packed(const isaac_packed *vol, const isaac_chain *chains, const float *luts,
+                              const float *weights, const isaac_render_opts *opts, int32_t cell,
+                              float *grid, int64_t grid_len, void *stream);
+
+/*
  * The rest of the source contract (Sec. 3.2): the per-source update callback
  * and sources whose memory is not persistent.
  *

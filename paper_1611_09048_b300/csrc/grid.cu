@@ -10,7 +10,7 @@
 #include <cstring>
 
 #include "common.h"
-#include "raycast.cuh"
+#include "packed.cuh"
 
 namespace isaac {
 
@@ -26,6 +26,12 @@ struct KGrid {
     int kchunk, nchunks;  // macro cells per z chunk, chunks
     float *cols;          // column maxima: (gz, H, W), workspace
     float *grid;
+    // over a packed copy instead of the sources: records of [-1, n]^3, the
+    // active packed sources' first component in the record and f_dim
+    const unsigned char *rec;
+    const float *scales;  // E4M3 brick scales
+    int comp_off[ISAAC_MAX_ACTIVE], fdim[ISAAC_MAX_ACTIVE];
+    int pbx, pby;         // bricks per axis x, y (E4M3)
 };
 
 // z-cells whose loads a thread issues together: 16 on the scalar fast paths
@@ -132,6 +138,151 @@ static __global__ void __launch_bounds__(256, (NS == 1 && FD == 1) ? 4 : 2) k_gr
             }
         }
         out[(long long)ka * plane] = ma;          // ka == k1 - 1: the walk ends in it
+    }
+}
+
+// Pass 1 over a packed copy (isaac_opacity_grid_packed): the walk of
+// k_grid_columns, reading record (x+1, y+1, z+1) of the [-1, n]^3 box -- which
+// already holds the apron trilinear samples read (guards, or the repeated
+// border) -- and decoding it as the packed renderer does (E4M3 times its brick
+// scale).  The grid is then the one of the dequantised copy.
+template <int DT, int PAD>
+static __global__ void __launch_bounds__(256, PAD == 1 ? 3 : 4) k_grid_columns_packed(const __grid_constant__ KGrid p)
+{
+    using IO = RecIO<DT, PAD>;
+    constexpr int kZ = PAD <= 1 ? 16 : 16 / PAD;   // records per batch: all loaded before any use
+    __shared__ float s_alpha[ISAAC_MAX_ACTIVE * 256];
+    for (int i = threadIdx.x; i < p.nact * 256; i += blockDim.x) s_alpha[i] = __ldg(&p.lut[i >> 8][i & 255].w);
+    __syncthreads();
+    const long long plane = (long long)p.W * p.H;
+    const long long items = plane * p.nchunks;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / plane);
+        const long long col = it - (long long)chunk * plane;   // record column (x+1, y+1)
+        const int yy = (int)(col / p.W), xx = (int)(col - (long long)yy * p.W);
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        const int zs = max(k0 * p.cell - 1, -1), ze = min(k1 * p.cell, p.nz);
+        int ka = k0;
+        int end_a = min((ka + 1) * p.cell, p.nz);
+        int start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;
+        float ma = 0.0f, mb = 0.0f;
+        float *out = p.cols + col;
+        for (int zb = zs; zb <= ze; zb += kZ) {
+            float r[kZ][PAD];
+#pragma unroll
+            for (int j = 0; j < kZ; ++j) {
+                const int zr = min(zb + j, p.nz) + 1;           // record z (past ze: a repeat, dropped)
+                IO::load(p.rec, (long long)zr * plane + col, r[j]);
+                if constexpr (DT == ISAAC_E4M3) {
+                    float sc[PAD];
+                    load_scales<PAD>(p.scales, ((zr >> 3) * p.pby + (yy >> 3)) * p.pbx + (xx >> 3), sc);
+#pragma unroll
+                    for (int c = 0; c < PAD; ++c) r[j][c] *= sc[c];
+                }
+            }
+            float a[kZ];
+#pragma unroll
+            for (int j = 0; j < kZ; ++j) {
+                float acc = 0.0f;
+                for (int s = 0; s < p.nact; ++s) {
+                    float w[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float x = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < PAD; ++q)
+                            if (q == p.comp_off[s] + c && c < p.fdim[s]) x = r[j][q];
+                        w[c] = x;
+                    }
+                    const float xv = run_chain(p.ch[s], w);
+                    const float pos = clamp01(xv) * 255.0f;
+                    const int k = min((int)pos, 254);
+                    const float f = pos - (float)k;
+                    acc = fmaf(p.src[s].w, lerp1(s_alpha[s * 256 + k], s_alpha[s * 256 + k + 1], f), acc);
+                }
+                a[j] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < kZ; ++j) {
+                const int z = zb + j;
+                if (z > ze) break;
+                if (z > end_a) {
+                    out[(long long)ka * plane] = ma;
+                    ++ka;
+                    ma = mb;
+                    mb = 0.0f;
+                    end_a = min((ka + 1) * p.cell, p.nz);
+                    start_b = ka + 1 < k1 ? (ka + 1) * p.cell - 1 : 0x7fffffff;
+                }
+                const float al = clamp01(a[j]);
+                ma = fmaxf(ma, al);
+                mb = z >= start_b ? fmaxf(mb, al) : mb;
+            }
+        }
+        out[(long long)ka * plane] = ma;
+    }
+}
+
+// Pass 1 over a packed copy with one scalar record (pad 1) of one active
+// source with the identity chain and CELL-cell macro cells: the branch-free
+// walk of k_grid_columns_scalar over records (x+1, y+1, z+1), z clamped to the
+// box [-1, n] (reads past it repeat the last record, already in the cell).
+template <int DT, int CELL>
+static __global__ void __launch_bounds__(256, 4) k_grid_columns_packed_scalar(const __grid_constant__ KGrid p)
+{
+    using IO = RecIO<DT, 1>;
+    __shared__ float2 s_pair[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float a0 = __ldg(&p.lut[0][i].w);
+        const float a1 = i < 255 ? __ldg(&p.lut[0][i + 1].w) : a0;
+        s_pair[i] = make_float2(a0, a1 - a0);
+    }
+    __syncthreads();
+    const float w = p.src[0].w;
+    auto alpha = [&](float v) {
+        const float pos = clamp01(v) * 255.0f;
+        const int k = min((int)pos, 254);
+        const float2 e = s_pair[k];
+        return clamp01(fmaf(w, fmaf(pos - (float)k, e.y, e.x), 0.0f));
+    };
+    const long long plane = (long long)p.W * p.H;
+    const long long items = plane * p.nchunks;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / plane);
+        const long long col = it - (long long)chunk * plane;
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        auto rec = [&](int z) {                  // value of cell z (clamped to [-1, n]) in this column
+            float r[1];
+            IO::load(p.rec, (long long)(min(max(z, -1), p.nz) + 1) * plane + col, r);
+            return r[0];
+        };
+        float *out = p.cols + col;
+        float prev = fmaxf(alpha(rec(k0 * CELL - 1)), alpha(rec(k0 * CELL)));
+        for (int k = k0; k < k1; ++k) {
+            const int z0 = k * CELL + 1;
+            float v[CELL];
+            if (z0 + CELL - 1 <= p.nz) {          // inside the box: records at a fixed stride
+                const unsigned char *b = p.rec + ((long long)(z0 + 1) * plane + col) * IO::BYTES;
+                const long long step = plane * IO::BYTES;
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) {
+                    float r[1];
+                    IO::load(b + j * step, 0, r);
+                    v[j] = r[0];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) v[j] = rec(z0 + j);
+            }
+            float core = 0.0f;
+#pragma unroll
+            for (int j = 0; j < CELL - 2; ++j) core = fmaxf(core, alpha(v[j]));
+            const float next = fmaxf(alpha(v[CELL - 2]), alpha(v[CELL - 1]));
+            out[(long long)k * plane] = fmaxf(fmaxf(prev, core), next);
+            prev = next;
+        }
     }
 }
 
@@ -568,6 +719,122 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
     const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
     k_grid_reduce<<<b2, 256, 0, st>>>(p);
     return check_cuda("isaac_opacity_grid reduce launch");
+}
+
+extern "C" int isaac_opacity_grid_packed(const isaac_packed *vol, const isaac_chain *chains,
+                                         const float *luts, const float *weights,
+                                         const isaac_render_opts *opts, int32_t cell, float *grid,
+                                         int64_t grid_len, void *stream)
+{
+    clear_error();
+    if (!vol || !chains || !weights || !opts || !grid || !luts)
+        return fail(ISAAC_EINVAL, "vol, chains, luts, weights, opts and grid are required");
+    if (vol->n_src < 1 || vol->n_src > ISAAC_MAX_ACTIVE)
+        return fail(ISAAC_EINVAL, "packed volume has %d sources", vol->n_src);
+    if (vol->dtype < ISAAC_F32 || vol->dtype > ISAAC_E4M3) return fail(ISAAC_EINVAL, "unknown dtype %d", vol->dtype);
+    if (vol->pad != 1 && vol->pad != 2 && vol->pad != 4 && vol->pad != 8)
+        return fail(ISAAC_EINVAL, "pad %d is not 1, 2, 4 or 8", vol->pad);
+    int nc = 0;
+    for (int i = 0; i < vol->n_src; ++i) {
+        if (vol->f_dim[i] < 1 || vol->f_dim[i] > 4)
+            return fail(ISAAC_EINVAL, "packed source %d: f_dim %d", i, vol->f_dim[i]);
+        nc += vol->f_dim[i];
+    }
+    if (nc != vol->n_comp || nc > vol->pad) return fail(ISAAC_EINVAL, "inconsistent packed layout");
+    if (!vol->data || ((uintptr_t)vol->data) % 16) return fail(ISAAC_EINVAL, "vol->data misaligned");
+    if (vol->dtype == ISAAC_E4M3 && (!vol->scales || ((uintptr_t)vol->scales) % 16))
+        return fail(ISAAC_EINVAL, "E4M3 volume needs 16-byte aligned scales");
+    for (int a = 0; a < 3; ++a)
+        if (opts->n[a] != vol->n[a]) return fail(ISAAC_EINVAL, "opts->n differs from the packed volume");
+    if (opts->active_mask >> vol->n_src)
+        return fail(ISAAC_EINVAL, "active_mask 0x%x has bits beyond the %d packed sources",
+                    opts->active_mask, vol->n_src);
+    if (cell < 2 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 2..1024", cell);
+    if (((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+    KGrid p;
+    memset(&p, 0, sizeof p);
+    p.nx = (int)vol->n[0];
+    p.ny = (int)vol->n[1];
+    p.nz = (int)vol->n[2];
+    p.cell = cell;
+    p.gx = (p.nx + cell - 1) / cell;
+    p.gy = (p.ny + cell - 1) / cell;
+    p.gz = (p.nz + cell - 1) / cell;
+    const long long cells = (long long)p.gx * p.gy * p.gz;
+    if (grid_len < cells)
+        return fail(ISAAC_ENOMEM, "grid holds %lld values, %lld needed", (long long)grid_len, cells);
+    int off = 0;
+    for (int s = 0; s < vol->n_src; ++s) {
+        if ((opts->active_mask >> s) & 1u) {
+            if (!std::isfinite(weights[s])) return fail(ISAAC_EINVAL, "weight %d is not finite", s);
+            int rc = compile_chain(chains[s], vol->f_dim[s], s, p.ch[p.nact]);
+            if (rc) return rc;
+            p.comp_off[p.nact] = off;
+            p.fdim[p.nact] = vol->f_dim[s];
+            p.src[p.nact].w = weights[s];
+            p.lut[p.nact] = reinterpret_cast<const float4 *>(luts) + (size_t)s * 256;
+            ++p.nact;
+        }
+        off += vol->f_dim[s];
+    }
+    p.grid = grid;
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (p.nact == 0) {
+        if (cudaMemsetAsync(grid, 0, (size_t)cells * sizeof(float), st) != cudaSuccess)
+            return check_cuda("isaac_opacity_grid_packed memset");
+        return ISAAC_OK;
+    }
+    p.rec = static_cast<const unsigned char *>(vol->data);
+    p.scales = vol->scales;
+    p.pbx = (p.nx + 9) / 8;
+    p.pby = (p.ny + 9) / 8;
+    p.W = p.nx + 2;
+    p.H = p.ny + 2;
+    p.kchunk = std::max(1, (64 + cell - 1) / cell);
+    p.nchunks = (p.gz + p.kchunk - 1) / p.kchunk;
+    const size_t col_bytes = (size_t)p.gz * (size_t)p.W * (size_t)p.H * sizeof(float);
+    KParams wp;
+    memset(&wp, 0, sizeof wp);
+    void *cols = nullptr;
+    int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
+    if (rc) return rc;
+    p.cols = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
+    const int sms = sm_count();
+    const long long items = (long long)p.W * p.H * p.nchunks;
+    const unsigned b1 = (unsigned)std::max(1LL, std::min((items + 255) / 256, (long long)sms * 4));
+#define ISAAC_GP(DT)                                                                              \
+    switch (vol->pad) {                                                                           \
+    case 1: k_grid_columns_packed<DT, 1><<<b1, 256, 0, st>>>(p); break;                           \
+    case 2: k_grid_columns_packed<DT, 2><<<b1, 256, 0, st>>>(p); break;                           \
+    case 4: k_grid_columns_packed<DT, 4><<<b1, 256, 0, st>>>(p); break;                           \
+    default: k_grid_columns_packed<DT, 8><<<b1, 256, 0, st>>>(p); break;                          \
+    }
+    const bool scalar = p.nact == 1 && vol->pad == 1 && p.ch[0].n == 0 && vol->dtype != ISAAC_E4M3 &&
+                        (cell == 8 || cell == 16);
+    if (scalar) {
+#define ISAAC_GPS(DT)                                                                             \
+        if (cell == 16) k_grid_columns_packed_scalar<DT, 16><<<b1, 256, 0, st>>>(p);              \
+        else k_grid_columns_packed_scalar<DT, 8><<<b1, 256, 0, st>>>(p);
+        switch (vol->dtype) {
+        case ISAAC_F32: ISAAC_GPS(ISAAC_F32) break;
+        case ISAAC_BF16: ISAAC_GPS(ISAAC_BF16) break;
+        default: ISAAC_GPS(ISAAC_F16) break;
+        }
+#undef ISAAC_GPS
+    } else {
+        switch (vol->dtype) {
+        case ISAAC_F32: ISAAC_GP(ISAAC_F32) break;
+        case ISAAC_BF16: ISAAC_GP(ISAAC_BF16) break;
+        case ISAAC_F16: ISAAC_GP(ISAAC_F16) break;
+        default: ISAAC_GP(ISAAC_E4M3) break;
+        }
+    }
+#undef ISAAC_GP
+    rc = check_cuda("isaac_opacity_grid_packed columns launch");
+    if (rc) return rc;
+    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
+    k_grid_reduce<<<b2, 256, 0, st>>>(p);
+    return check_cuda("isaac_opacity_grid_packed reduce launch");
 }
 
 extern "C" int isaac_range_grid(const isaac_source *sources, int32_t n_sources,

@@ -33,7 +33,7 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
            "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
            "isaac_render_iso", "isaac_probe_read", "isaac_composite", "isaac_copy_source",
-           "isaac_set_update_hook")
+           "isaac_set_update_hook", "isaac_opacity_grid_packed")
 
 # fn(source, enabled, user) of isaac_set_update_hook
 UPDATE_FN = C.CFUNCTYPE(None, C.c_int32, C.c_int32, C.c_void_p)
@@ -220,6 +220,10 @@ def load(path: Optional[str] = None):
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.isaac_probe_read.restype = C.c_int
         lib.isaac_probe_read.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
+        lib.isaac_opacity_grid_packed.restype = C.c_int
+        lib.isaac_opacity_grid_packed.argtypes = [C.POINTER(Packed), C.POINTER(Chain), C.c_void_p,
+                                                  C.c_void_p, C.POINTER(RenderOpts), C.c_int32,
+                                                  C.c_void_p, C.c_int64, C.c_void_p]
         lib.isaac_copy_source.restype = C.c_int
         lib.isaac_copy_source.argtypes = [C.POINTER(Source), C.POINTER(C.c_int64), C.c_void_p,
                                           C.c_int64, C.POINTER(Source), C.c_void_p]
@@ -626,6 +630,21 @@ class PackedVolume:
                                 C.byref(out), _stream_handle(stream)))
         self.desc = out
         return self
+
+    def opacity_grid(self, cell=16, mask=None, stream=None, out=None):
+        """Max-opacity grid of this copy (isaac_opacity_grid_packed), (Gz, Gy, Gx)
+        float32 on the device: the grid of the dequantised fields."""
+        import torch
+        sc = self.ds.scene
+        G = [(int(k) + cell - 1) // cell for k in sc.n]
+        if out is None:
+            out = torch.empty((G[2], G[1], G[0]), dtype=torch.float32, device=self.ds.device)
+        opts = make_opts(sc, (1 << len(self.src_index)) - 1 if mask is None else mask)
+        check(load().isaac_opacity_grid_packed(C.byref(self.desc), self.chains, self.luts.data_ptr(),
+                                               C.cast(self.weights, C.c_void_p), C.byref(opts),
+                                               int(cell), out.data_ptr(), out.numel(),
+                                               _stream_handle(stream)))
+        return out
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
                 lanes=None):

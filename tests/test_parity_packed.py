@@ -160,3 +160,44 @@ def test_storage_error_against_original_data(cuda_ok, fmt):
     assert lsb.mean() <= 1.0
     if fmt != "e4m3":
         assert e.max() <= TOL_16, e.max(0)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16", "e4m3"])
+@pytest.mark.parametrize("cell", [4, 7])
+def test_opacity_grid_of_packed_copy(cuda_ok, fmt, cell):
+    """isaac_opacity_grid_packed equals the oracle's grid of the dequantised
+    copy; over the float32 copy it equals the zero-copy grid bit for bit (the
+    same values through the same arithmetic)."""
+    import torch
+    sc = _mixed_scene()
+    ds = isaac.DeviceScene(sc)
+    pv = ds.pack(fmt)
+    g = pv.opacity_grid(cell)
+    torch.cuda.synchronize()
+    want = oracle.opacity_grid(_dequantised_scene(sc, fmt), cell)
+    np.testing.assert_allclose(g.cpu().numpy(), want, rtol=0, atol=1e-5)
+    if fmt == "f32":
+        z = ds.opacity_grid(cell)
+        torch.cuda.synchronize()
+        assert torch.equal(g, z)
+    sub = pv.opacity_grid(cell, mask=0b101)
+    torch.cuda.synchronize()
+    want_sub = oracle.opacity_grid(_dequantised_scene(sc, fmt, mask=0b101), cell)
+    np.testing.assert_allclose(sub.cpu().numpy(), want_sub, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16", "e4m3"])
+def test_opacity_grid_of_packed_scalar_bubble(cuda_ok, fmt):
+    """The learned workload's shape (one scalar source, identity chain): its
+    own walk for 8- and 16-cell macro cells (16-bit and float32 records), the
+    general one for other cells and for E4M3."""
+    import torch
+    sc = synth.scene_bubble(64, frame=4, seed=3, width=32, height=32)
+    pv = isaac.DeviceScene(sc).pack(fmt)
+    deq = _dequantised_scene(sc, fmt)
+    for cell in (8, 16, 5):
+        g = pv.opacity_grid(cell)
+        torch.cuda.synchronize()
+        want = oracle.opacity_grid(deq, cell)
+        np.testing.assert_allclose(g.cpu().numpy(), want, rtol=0, atol=1e-5)
+        assert (want > 0).any() and (want == 0).any()
