@@ -269,3 +269,35 @@ def test_composite_validates_before_any_launch():
     assert "misaligned" in lib.isaac_last_error().decode()
     nan = (C.c_float * 4)(float("nan"), 0, 0, 0)
     assert lib.isaac_composite(one, one, 1, 4, 4, nan, FAKE, None, None) == isaac.EINVAL
+
+
+def test_opacity_grid_packed_validates_before_any_launch():
+    lib = isaac.load()
+    a = _valid_call_args(n=8)
+    vol = isaac.Packed()
+    vol.data = FAKE
+    vol.n[0] = vol.n[1] = vol.n[2] = 8
+    vol.dtype = isaac.BF16
+    vol.n_src = 1
+    vol.f_dim[0] = 1
+    vol.n_comp = 1
+    vol.pad = 1
+
+    def call(v, cell=4, grid_len=8, opts=None):
+        return lib.isaac_opacity_grid_packed(C.byref(v) if v is not None else None, a["chains"], FAKE,
+                                             C.cast(a["weights"], C.c_void_p),
+                                             C.byref(opts or a["opts"]), cell, FAKE, grid_len, None)
+    assert call(None) == isaac.EINVAL
+    assert call(vol, cell=1) == isaac.EINVAL
+    rc = call(vol, grid_len=7)
+    assert rc == isaac.ENOMEM and "grid holds 7" in lib.isaac_last_error().decode()
+    bad = isaac.Packed.from_buffer_copy(vol)
+    bad.pad = 3
+    assert call(bad) == isaac.EINVAL
+    other = isaac.RenderOpts.from_buffer_copy(a["opts"])
+    other.n[0] = 9
+    rc = call(vol, opts=other)
+    assert rc == isaac.EINVAL and "differs" in lib.isaac_last_error().decode()
+    e4 = isaac.Packed.from_buffer_copy(vol)
+    e4.dtype = isaac.E4M3
+    assert call(e4) == isaac.EINVAL                       # E4M3 without scales
