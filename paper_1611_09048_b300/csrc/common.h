@@ -60,9 +60,9 @@ int march_grab();
 // Bind the calling stream's workspace (grown as needed) to p.ctr / p.rays /
 // p.longs; `extra` more bytes after them, returned in *extra_ptr.
 int bind_workspace(KParams &p, cudaStream_t st, size_t extra = 0, void **extra_ptr = nullptr);
-// Empty-space flags of the macro cells (one byte each) from a value-range grid.
+// Empty-space bits of the macro cells (32 per word) from a value-range grid.
 int launch_empty_flags(const KParams &p, int nact, const float *ranges, int slots, long long cells,
-                       unsigned char *flags, cudaStream_t st);
+                       unsigned *flags, cudaStream_t st);
 // Background + ray setup + optional hook + march kernel `fn` (null: background
 // only).  fn_long: the long-ray march of the same sources; with a hook and
 // fn_long the hook may fill the long-ray list, which fn_long marches before fn.

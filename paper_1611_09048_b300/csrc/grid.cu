@@ -570,7 +570,7 @@ struct KEmpty {
     float w[ISAAC_MAX_ACTIVE];
     KChain ch[ISAAC_MAX_ACTIVE];
     const float4 *lut[ISAAC_MAX_ACTIVE];
-    unsigned char *flags;
+    unsigned *flags;      // one bit per macro cell, 32 per word
 };
 
 // A macro cell is empty when, for the components' value ranges over its box,
@@ -580,11 +580,14 @@ struct KEmpty {
 // cell interpolates between values of the box, so its opacity is then 0 and
 // compositing it is a no-op.  The interpolation itself may round a few ulps
 // outside the corners' range: the ranges are widened by 10^-6 relative first.
+// One thread per macro cell, a warp per word of 32 bits.
 static __global__ void k_empty_flags(const __grid_constant__ KEmpty p)
 {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < p.cells;
-         g += (long long)gridDim.x * blockDim.x) {
-        bool empty = true;
+    const int lane = threadIdx.x & 31;
+    for (long long gb = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; gb < p.cells;
+         gb += (long long)gridDim.x * blockDim.x) {
+        const long long g = gb + lane;
+        bool empty = g < p.cells;
         int slot = 0;
         for (int s = 0; s < p.nact && empty; ++s) {
             float lo[4] = {0.0f, 0.0f, 0.0f, 0.0f}, hi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -607,12 +610,13 @@ static __global__ void k_empty_flags(const __grid_constant__ KEmpty p)
                 }
             }
         }
-        p.flags[g] = empty ? 1 : 0;
+        const unsigned bits = __ballot_sync(0xffffffffu, empty);
+        if (lane == 0) p.flags[gb >> 5] = bits;
     }
 }
 
 int launch_empty_flags(const KParams &kp, int nact, const float *ranges, int slots, long long cells,
-                       unsigned char *flags, cudaStream_t st)
+                       unsigned *flags, cudaStream_t st)
 {
     KEmpty e;
     memset(&e, 0, sizeof e);

@@ -101,6 +101,8 @@ constexpr int kLongRaySamples = 96;
 // LUT copies twice as large (a table of entry differences) halved the frame
 // rate, the L1 being too small for the gathers' working set.
 constexpr int kMarchThreads = 128, kMarchBlocksPerSM = 8;
+// Words of empty bits a skipping block stages in shared memory (32768 macro cells).
+constexpr int kSkipSharedWords = 1024;
 
 // Key under which the long-ray kernels are registered (the lanes that shade
 // one ray's samples per instruction); march_long holds kStreamRays rays per warp.
@@ -129,9 +131,9 @@ struct KParams {
     int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
     int max_steps;                   // samples on the longest chord of the local box
     int grab;                        // march: most chunks of 32/RL rays a warp takes per atomic
-    // empty-space skipping: one byte per macro cell of skip_cell^3 cells
-    // (1 = every sample whose position lies in it has opacity 0)
-    const unsigned char *empty;
+    // empty-space skipping: one bit per macro cell of skip_cell^3 cells, 32
+    // per word (1 = every sample whose position lies in it has opacity 0)
+    const unsigned *empty;
     int skip_cell, sgx, sgy, sgz;
     float iso[ISAAC_MAX_ACTIVE];     // iso-surface mode: threshold of each active source
     KSource src[ISAAC_MAX_ACTIVE];
@@ -752,9 +754,11 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
 // group evaluate samples k+0 .. k+RL-1 together; every lane then composites
 // the group's RL samples in order, stopping at the termination sample, so all
 // lanes hold the same C and A.
+// s_empty: the block's shared copy of the empty bits (SKIP_EMPTY), or null to
+// read them from p.empty.
 template <class Shader, int RL, bool LABEL, bool SKIP_LONG = false, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut, unsigned idx,
-                                          int lane)
+                                          int lane, const unsigned *s_empty = nullptr)
 {
     const int sub = lane & (RL - 1);
     const RayRec r = p.rays[idx];
@@ -775,7 +779,9 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
             const int mx = min(max((int)floorf(x / cz), 0), p.sgx - 1);
             const int my = min(max((int)floorf(y / cz), 0), p.sgy - 1);
             const int mz = min(max((int)floorf(z / cz), 0), p.sgz - 1);
-            if (p.empty[((long long)mz * p.sgy + my) * p.sgx + mx]) {
+            const long long m = ((long long)mz * p.sgy + my) * p.sgx + mx;
+            const unsigned *bits = s_empty ? s_empty : p.empty;
+            if ((bits[m >> 5] >> (m & 31)) & 1u) {
                 const float inf = __int_as_float(0x7f800000);
                 const float ex = r.dx > 0.0f ? ((float)(mx + 1) * cz - x) / r.dx
                                : (r.dx < 0.0f ? ((float)mx * cz - x) / r.dx : inf);
@@ -843,7 +849,8 @@ __device__ __forceinline__ void march_ray(const KParams &p, const float4 *s_lut,
 // chunks stay small enough to balance the warps.  Rays on the long-ray list
 // are skipped: the long-ray march has taken them.
 template <int NACT, class Shader, int RL, bool LABEL = false, bool SKIP_EMPTY = false>
-__device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
+__device__ __forceinline__ void march(const KParams &p, const float4 *s_lut,
+                                      const unsigned *s_empty = nullptr)
 {
     constexpr unsigned RAYS = 32 / RL;
     const int lane = threadIdx.x & 31;
@@ -861,7 +868,7 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut)
         for (unsigned c = 0; c < grab; ++c) {
             const unsigned idx = first + c * RAYS + (unsigned)(lane / RL);
             if (first + c * RAYS >= n_rays) break;
-            if (idx < n_rays) march_ray<Shader, RL, LABEL, !LABEL, SKIP_EMPTY>(p, s_lut, idx, lane);
+            if (idx < n_rays) march_ray<Shader, RL, LABEL, !LABEL, SKIP_EMPTY>(p, s_lut, idx, lane, s_empty);
         }
     }
 }
@@ -1126,8 +1133,18 @@ __global__ void __launch_bounds__(kMarchThreads, kMarchBlocksPerSM) k_raycast(co
         march_long<Shader>(p, s_lut);
     else if constexpr (MODE == MODE_ISO)
         march_iso<NACT, SIG, INTERP, Idx, RL>(p);
-    else
-        march<NACT, Shader, RL, MODE == MODE_LABEL, MODE == MODE_SKIP>(p, s_lut);
+    else if constexpr (MODE == MODE_SKIP) {
+        // the empty bits in shared memory (a ray tests one per macro cell it
+        // enters), when they fit: 1024 words, 32768 macro cells
+        __shared__ unsigned s_empty[kSkipSharedWords];
+        const long long words = ((long long)p.sgx * p.sgy * p.sgz + 31) / 32;
+        const bool staged = words <= kSkipSharedWords;
+        if (staged)
+            for (int i = threadIdx.x; i < (int)words; i += blockDim.x) s_empty[i] = __ldg(p.empty + i);
+        __syncthreads();
+        march<NACT, Shader, RL, false, true>(p, s_lut, staged ? s_empty : nullptr);
+    } else
+        march<NACT, Shader, RL, MODE == MODE_LABEL, false>(p, s_lut);
 }
 
 // Copy the ray list (at most `cap` records) and its length out of the workspace.

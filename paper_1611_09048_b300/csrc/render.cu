@@ -360,10 +360,11 @@ extern "C" int isaac_render_skip(const isaac_source *sources, const isaac_chain 
                      choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact)), &rl);
         if (!fn) return fail(ISAAC_ENOTSUP, "no empty-space-skipping kernel for %d sources", nact);
         void *flags = nullptr;
-        rc = bind_workspace(p, st, (size_t)cells, &flags);
+        rc = bind_workspace(p, st, (size_t)((cells + 31) / 32) * 4 + 16, &flags);
         if (rc) return rc;
-        p.empty = static_cast<const unsigned char *>(flags);
-        rc = launch_empty_flags(p, nact, ranges, slots, cells, static_cast<unsigned char *>(flags), st);
+        unsigned *bits = reinterpret_cast<unsigned *>((reinterpret_cast<uintptr_t>(flags) + 15) & ~uintptr_t(15));
+        p.empty = bits;
+        rc = launch_empty_flags(p, nact, ranges, slots, cells, bits, st);
         if (rc) return rc;
     }
     return launch_frame_with(p, fn, rl, st, nullptr);
