@@ -245,6 +245,13 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
     return ISAAC_OK;
 }
 
+// A double as the nearest float plus the float nearest to the remainder.
+static ff split_ff(double v)
+{
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+
 // Common validation of everything but the sources; fills the geometric part
 // of KParams.
 int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_clip,
@@ -311,6 +318,35 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
     p.step = opt->step;
     p.step_d = (double)opt->step;
     p.inv_step_d = 1.0 / p.step_d;
+
+    // Float-float copies for the device ray setup.  With X = px + 1/2 - W/2
+    // and Y = py + 1/2 - H/2 the NDC coordinates are xn = X (2/W) and
+    // yn = -Y (2/H); the homogeneous point at depth z is
+    // minv (xn, yn, z, 1), moved to global voxel coordinates by adding
+    // half_g times its w component before the division.
+    p.pix_cx = 0.5f * (float)(cam->width - 1);
+    p.pix_cy = 0.5f * (float)(cam->height - 1);
+    for (int e = 0; e < 2; ++e) {
+        const double z = e == 0 ? -1.0 : 1.0;
+        double c[3][4];
+        for (int i = 0; i < 4; ++i) {
+            c[0][i] = p.minv[8 + i] * z + p.minv[12 + i];
+            c[1][i] = p.minv[i] * p.ndc_sx;
+            c[2][i] = -p.minv[4 + i] * p.ndc_sy;
+        }
+        for (int k = 0; k < 3; ++k) {
+            for (int a = 0; a < 3; ++a) c[k][a] += p.half_g[a] * c[k][3];
+            for (int i = 0; i < 4; ++i) p.ray[e][k][i] = split_ff(c[k][i]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        p.gn_f[a] = split_ff(p.gn[a]);
+        p.llo_f[a] = split_ff(p.llo[a]);
+        p.lhi_f[a] = split_ff(p.lhi[a]);
+    }
+    for (int i = 0; i < n_clip; ++i)
+        for (int j = 0; j < 4; ++j) p.clip_f[i][j] = split_ff(p.clip[i][j]);
+    p.inv_step_f = split_ff(p.inv_step_d);
     // every ray's samples lie on one chord of the local box
     const double diag = std::sqrt((double)opt->n[0] * opt->n[0] + (double)opt->n[1] * opt->n[1] +
                                   (double)opt->n[2] * opt->n[2]);

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include "isaac_b300.h"
+#include "ff.cuh"
 
 namespace isaac {
 
@@ -114,6 +115,7 @@ constexpr int kLongRayLanes = 32;
 enum : int { MODE_PLAIN = 0, MODE_TOUCH = 1, MODE_LABEL = 2, MODE_LONG = 3, MODE_SKIP = 4, MODE_ISO = 5 };
 
 struct KParams {
+    // Host-side geometry in double (the screen rectangle is cut from it).
     double minv[16];                 // inverse of projection * modelview, column-major
     double half_g[3];                // global_n / 2 (world -> global voxel)
     double gn[3];                    // global box [0, gn)
@@ -121,6 +123,15 @@ struct KParams {
     double clip[ISAAC_MAX_CLIP][4];
     double ndc_sx, ndc_sy;           // 2 / W, 2 / H
     double step_d, inv_step_d;
+    // The same geometry as float-float pairs for the device ray setup.  The
+    // homogeneous point of pixel (px, py) at NDC depth -1 (ray[0]) and +1
+    // (ray[1]), in global voxel coordinates, is c[0] + X c[1] + Y c[2] with
+    // X = px - pix_cx, Y = py - pix_cy (both exact in FP32).
+    ff ray[2][3][4];
+    float pix_cx, pix_cy;            // (W - 1) / 2, (H - 1) / 2
+    ff gn_f[3], llo_f[3], lhi_f[3];
+    ff clip_f[ISAAC_MAX_CLIP][4];
+    ff inv_step_f;
     float step;
     float term;
     float bg[4];
@@ -574,24 +585,12 @@ struct ZeroCopyShader {
 
 // ------------------------------------------------------------- ray setup
 
-// Ray setup in FP64 (camera unprojection, box and clip-plane intervals, the
-// sample index range).  The discrete decisions (first/last sample) are taken
-// in double so they match an FP64 reference except at exact ties; the first
-// sample's position and the direction are then rounded to FP32 for the march.
-// FP64 reciprocal from the FP32 one and two Newton steps (error ~1 ulp of
-// double, against some twenty FP64 operations for a division); operands
-// outside the FP32 range take the division.
-template <int NEWTON = 2>
-__device__ __forceinline__ double drcp(double x)
-{
-    const float rf = __frcp_rn((float)x);
-    if (!(fabsf(rf) < 1.0e38f) || !(fabsf(rf) > 1.0e-37f)) return 1.0 / x;
-    double r = (double)rf;
-#pragma unroll
-    for (int i = 0; i < NEWTON; ++i) r = fma(r, fma(-x, r, 1.0), r);
-    return r;
-}
-
+// Ray setup (camera unprojection, box and clip-plane intervals, the sample
+// index range) in float-float arithmetic, ~48 significant bits: the discrete
+// decisions (first and last sample) agree with a double-precision computation
+// except within ~1e-12 of a tie, at a fraction of the cost of FP64 on B300.
+// The first sample's position and the direction are rounded to FP32 for the
+// march.
 __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, float *t_first = nullptr)
 {
     RayRec r;
@@ -602,54 +601,51 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, fl
     r.kbeg = 0;
     r.jf = r.jl = -1;
     r.reserved = 0;
-    const double *m = p.minv;
-    const double xn = ((double)px + 0.5) * p.ndc_sx - 1.0;
-    const double yn = 1.0 - ((double)py + 0.5) * p.ndc_sy;
-    double nb[4], fb[4];
+    const float X = (float)px - p.pix_cx, Y = (float)py - p.pix_cy;
+    ff h[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const double b = fma(m[i], xn, fma(m[4 + i], yn, m[12 + i]));
-        nb[i] = b - m[8 + i];
-        fb[i] = b + m[8 + i];
-    }
-    const double inw = drcp(nb[3]), ifw = drcp(fb[3]);
-    double o[3], d[3];
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            h[e][i] = ff_add(ff_add(p.ray[e][0][i], ff_mulf(p.ray[e][1][i], X)), ff_mulf(p.ray[e][2][i], Y));
+    // near point o and unit direction d towards the far point
+    const ff inw = ff_rcp(h[0][3]), ifw = ff_rcp(h[1][3]);
+    ff o[3], d[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double nv = nb[a] * inw;
-        o[a] = nv + p.half_g[a];
-        d[a] = fb[a] * ifw - nv;
+        o[a] = ff_mul(h[0][a], inw);
+        d[a] = ff_sub(ff_mul(h[1][a], ifw), o[a]);
     }
-    const double il = rsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    d[0] *= il;
-    d[1] *= il;
-    d[2] *= il;
+    const ff il = ff_rsqrt(ff_add(ff_add(ff_mul(d[0], d[0]), ff_mul(d[1], d[1])), ff_mul(d[2], d[2])));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = ff_mul(d[a], il);
     // a degenerate pixel (point at infinity, zero direction) cannot be cast
-    if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]) && isfinite(d[0]) &&
-          isfinite(d[1]) && isfinite(d[2])))
+    if (!(isfinite(o[0].hi) && isfinite(o[1].hi) && isfinite(o[2].hi) && isfinite(d[0].hi) &&
+          isfinite(d[1].hi) && isfinite(d[2].hi)))
         return r;
 
     // Slab intervals of the global box (t0 = its entry: the origin of the
-    // sample grid) and of the local box.  The reciprocals take one Newton step
-    // (relative error ~2^-46, far below the tie margin of the sample decisions);
-    // without a domain split the two boxes coincide and one pass serves both.
-    double t0 = 0.0, tg1 = 1e300, tl0 = 0.0, tout = 1e300;
+    // sample grid) and of the local box.  A direction component below 1e-30
+    // counts as zero (its slab crossings lie beyond any reachable t).  Without
+    // a domain split the two boxes coincide and one pass serves both.
+    const float inf = __int_as_float(0x7f800000);
+    ff t0 = ff_from(0.0f), tg1 = ff_from(inf), tl0 = ff_from(0.0f), tout = ff_from(inf);
     bool miss = false;
     const bool one_box = p.local_is_global != 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (d[a] != 0.0) {
-            const double inv = drcp<1>(d[a]);
-            double ta = (0.0 - o[a]) * inv, tb = (p.gn[a] - o[a]) * inv;
-            t0 = fmax(t0, fmin(ta, tb));
-            tg1 = fmin(tg1, fmax(ta, tb));
+        if (fabsf(d[a].hi) > 1e-30f) {
+            const ff inv = ff_rcp(d[a]);
+            ff ta = ff_mul(ff_neg(o[a]), inv), tb = ff_mul(ff_sub(p.gn_f[a], o[a]), inv);
+            t0 = ff_max(t0, ff_min(ta, tb));
+            tg1 = ff_min(tg1, ff_max(ta, tb));
             if (!one_box) {
-                ta = (p.llo[a] - o[a]) * inv;
-                tb = (p.lhi[a] - o[a]) * inv;
-                tl0 = fmax(tl0, fmin(ta, tb));
-                tout = fmin(tout, fmax(ta, tb));
+                ta = ff_mul(ff_sub(p.llo_f[a], o[a]), inv);
+                tb = ff_mul(ff_sub(p.lhi_f[a], o[a]), inv);
+                tl0 = ff_max(tl0, ff_min(ta, tb));
+                tout = ff_min(tout, ff_max(ta, tb));
             }
-        } else if (o[a] < p.llo[a] || o[a] >= p.lhi[a]) {
+        } else if (ff_lt(o[a], p.llo_f[a]) || !ff_lt(o[a], p.lhi_f[a])) {
             miss = true;
         }
     }
@@ -657,33 +653,35 @@ __device__ __forceinline__ RayRec setup_ray(const KParams &p, int px, int py, fl
         tl0 = t0;
         tout = tg1;
     }
-    if (t0 >= tg1) miss = true;
-    double tin = fmax(t0, tl0);
+    if (!ff_lt(t0, tg1)) miss = true;
+    ff tin = ff_max(t0, tl0);
     for (int i = 0; i < p.n_clip; ++i) {
-        const double *pl = p.clip[i];
-        const double s = fma(pl[0], o[0], fma(pl[1], o[1], fma(pl[2], o[2], pl[3])));
-        const double rr = fma(pl[0], d[0], fma(pl[1], d[1], pl[2] * d[2]));
-        if (rr > 0.0) {
-            tin = fmax(tin, -s * drcp<1>(rr));
-        } else if (rr < 0.0) {
-            tout = fmin(tout, -s * drcp<1>(rr));
-        } else if (s < 0.0) {
+        const ff *pl = p.clip_f[i];
+        const ff s = ff_add(ff_add(ff_add(ff_mul(pl[0], o[0]), ff_mul(pl[1], o[1])), ff_mul(pl[2], o[2])), pl[3]);
+        const ff rr = ff_add(ff_add(ff_mul(pl[0], d[0]), ff_mul(pl[1], d[1])), ff_mul(pl[2], d[2]));
+        if (rr.hi > 0.0f) {
+            tin = ff_max(tin, ff_neg(ff_div(s, rr)));
+        } else if (rr.hi < 0.0f) {
+            tout = ff_min(tout, ff_neg(ff_div(s, rr)));
+        } else if (s.hi < 0.0f) {
             miss = true;
         }
     }
     // the local box is bounded, so a ray inside it has a finite exit
-    if (miss || !(tin < tout) || !(tout < 1e299)) return r;
-    const long long kf = (tin > t0) ? (long long)ceil((tin - t0) * p.inv_step_d) : 0LL;
-    const long long ke = (long long)ceil((tout - t0) * p.inv_step_d);
+    if (miss || !ff_lt(tin, tout) || !(tout.hi < 1e30f)) return r;
+    const long long kf = ff_lt(t0, tin) ? ff_ceil(ff_mul(ff_sub(tin, t0), p.inv_step_f)) : 0LL;
+    const long long ke = ff_ceil(ff_mul(ff_sub(tout, t0), p.inv_step_f));
     if (ke <= kf) return r;
-    const double tf = t0 + (double)kf * p.step_d;
-    if (t_first) *t_first = (float)tf;
-    r.ex = (float)(fma(tf, d[0], o[0]) - p.llo[0]);
-    r.ey = (float)(fma(tf, d[1], o[1]) - p.llo[1]);
-    r.ez = (float)(fma(tf, d[2], o[2]) - p.llo[2]);
-    r.dx = (float)d[0];
-    r.dy = (float)d[1];
-    r.dz = (float)d[2];
+    const float kf_hi = (float)kf;
+    const ff kff = {kf_hi, (float)(kf - (long long)kf_hi)};
+    const ff tf = ff_add(t0, ff_mulf(kff, p.step));
+    if (t_first) *t_first = tf.hi;
+    r.ex = ff_sub(ff_add(o[0], ff_mul(tf, d[0])), p.llo_f[0]).hi;
+    r.ey = ff_sub(ff_add(o[1], ff_mul(tf, d[1])), p.llo_f[1]).hi;
+    r.ez = ff_sub(ff_add(o[2], ff_mul(tf, d[2])), p.llo_f[2]).hi;
+    r.dx = d[0].hi;
+    r.dy = d[1].hi;
+    r.dz = d[2].hi;
     r.nsteps = (int)min(ke - kf, (long long)p.max_steps);
     return r;
 }
