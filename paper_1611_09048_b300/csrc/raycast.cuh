@@ -4,7 +4,7 @@
 //   k_fill_background  background for every pixel outside the screen
 //                      rectangle the box can cover; resets the workspace
 //                      counters;
-//   k_setup_rays       one thread per rectangle pixel: the ray in FP64 (camera
+//   k_setup_rays       one thread per rectangle pixel: the ray in float-float (camera
 //                      unprojection, global/local box and clip-plane interval,
 //                      first and last sample on the global grid); misses write
 //                      the background, hits are appended to a compact ray list
