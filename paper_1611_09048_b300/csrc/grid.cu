@@ -286,6 +286,85 @@ static __global__ void __launch_bounds__(256, 4) k_grid_columns_packed_scalar(co
     }
 }
 
+// The same walk over two adjacent columns (2j, 2j+1) of a 16-bit scalar copy
+// whose padded row length is even: one 4-byte load per cell pair, so each
+// thread keeps twice the bytes in flight of the one-column walk, whose 2-byte
+// loads left it bound by memory latency at half the bandwidth of the float32
+// walk.  Both columns' maxima are written with one 8-byte store.
+template <int DT, int CELL>
+static __global__ void __launch_bounds__(256, 4) k_grid_columns_packed_scalar2(const __grid_constant__ KGrid p)
+{
+    __shared__ float2 s_pair[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        const float a0 = __ldg(&p.lut[0][i].w);
+        const float a1 = i < 255 ? __ldg(&p.lut[0][i + 1].w) : a0;
+        s_pair[i] = make_float2(a0, a1 - a0);
+    }
+    __syncthreads();
+    const float w = p.src[0].w;
+    auto alpha = [&](float v) {
+        const float pos = clamp01(v) * 255.0f;
+        const int k = min((int)pos, 254);
+        const float2 e = s_pair[k];
+        return clamp01(fmaf(w, fmaf(pos - (float)k, e.y, e.x), 0.0f));
+    };
+    const long long plane = (long long)p.W * p.H, half = plane >> 1;
+    const long long items = half * p.nchunks;
+    const unsigned *rec = reinterpret_cast<const unsigned *>(p.rec);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int chunk = (int)(it / half);
+        const long long q = it - (long long)chunk * half;          // word q of a plane: columns 2q, 2q+1
+        const int k0 = chunk * p.kchunk, k1 = min(k0 + p.kchunk, p.gz);
+        auto pair = [&](int z, float &a, float &b) {                // cells z (clamped to [-1, n])
+            unpack2<DT>(__ldg(rec + (long long)(min(max(z, -1), p.nz) + 1) * half + q), a, b);
+        };
+        float2 *out = reinterpret_cast<float2 *>(p.cols) + q;
+        float prev0, prev1;
+        {
+            float a0, a1, b0, b1;
+            pair(k0 * CELL - 1, a0, a1);
+            pair(k0 * CELL, b0, b1);
+            prev0 = fmaxf(alpha(a0), alpha(b0));
+            prev1 = fmaxf(alpha(a1), alpha(b1));
+        }
+        for (int k = k0; k < k1; ++k) {
+            const int z0 = k * CELL + 1;
+            unsigned u[CELL];
+            if (z0 + CELL - 1 <= p.nz) {
+                const unsigned *b = rec + (long long)(z0 + 1) * half + q;
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) u[j] = __ldg(b + j * half);
+            } else {
+#pragma unroll
+                for (int j = 0; j < CELL; ++j) u[j] = __ldg(rec + (long long)(min(z0 + j, p.nz) + 1) * half + q);
+            }
+            float core0 = 0.0f, core1 = 0.0f, next0, next1;
+#pragma unroll
+            for (int j = 0; j < CELL; ++j) {
+                float a, b;
+                unpack2<DT>(u[j], a, b);
+                a = alpha(a);
+                b = alpha(b);
+                if (j < CELL - 2) {
+                    core0 = fmaxf(core0, a);
+                    core1 = fmaxf(core1, b);
+                } else if (j == CELL - 2) {
+                    next0 = a;
+                    next1 = b;
+                } else {
+                    next0 = fmaxf(next0, a);
+                    next1 = fmaxf(next1, b);
+                }
+            }
+            out[(long long)k * half] = make_float2(fmaxf(fmaxf(prev0, core0), next0),
+                                                   fmaxf(fmaxf(prev1, core1), next1));
+            prev0 = next0;
+            prev1 = next1;
+        }
+    }
+}
+
 // Pass 1, one scalar source with the identity chain and macro cells of CELL
 // cells (the learned proposal's configuration).  Macro cell k covers z in
 // [k*CELL - 1, (k+1)*CELL]: the pair {k*CELL - 1, k*CELL} it shares with k-1,
@@ -385,6 +464,72 @@ static __global__ void __launch_bounds__(256) k_grid_reduce(const __grid_constan
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) p.grid[m] = mx;
     }
+}
+
+// Pass 2 for macro cells of CELL = 8 or 16 cells: one block per tile of
+// TM x TM macro cells (TM * CELL = 64) of one z layer k.  The block stages the
+// tile's 66 x 66 column maxima (its 64 x 64 columns and the one-column apron
+// around them, zero outside [-1, n]) in shared memory with row-contiguous
+// loads, takes per row the maximum over each macro cell's CELL + 2 columns,
+// then per macro cell the maximum over its CELL + 2 rows.  Every column
+// maximum is read once (1.06x with the apron), where the warp-per-macro-cell
+// reduction read 18-float row pieces at a time.  Maxima are of values in
+// [0, 1], so the zero fill changes none.
+template <int CELL>
+static __global__ void __launch_bounds__(256) k_grid_reduce_tiled(const __grid_constant__ KGrid p)
+{
+    constexpr int TM = 64 / CELL, R = TM * CELL + 2;
+    __shared__ float s_col[R][R + 1];
+    __shared__ float s_row[R][TM];
+    const int tiles_x = (p.gx + TM - 1) / TM, tiles_y = (p.gy + TM - 1) / TM;
+    const int tx = blockIdx.x % tiles_x, ty = (blockIdx.x / tiles_x) % tiles_y;
+    const int k = blockIdx.x / (tiles_x * tiles_y);
+    const long long plane = (long long)p.W * p.H;
+    const float *base = p.cols + (long long)k * plane;
+    // padded column xx = x + 1: the tile's columns x in [64 tx - 1, 64 tx + 64]
+    const int x0 = tx * TM * CELL, y0 = ty * TM * CELL;
+    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        const int r = i / R, c = i - r * R;
+        const int xx = x0 + c, yy = y0 + r;
+        s_col[r][c] = (xx < p.W && yy < p.H) ? __ldg(base + (long long)yy * p.W + xx) : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R * TM; i += blockDim.x) {
+        const int r = i / TM, mi = i - r * TM;
+        float m = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CELL + 2; ++c) m = fmaxf(m, s_col[r][mi * CELL + c]);
+        s_row[r][mi] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x < TM * TM) {
+        const int mj = threadIdx.x / TM, mi = threadIdx.x - mj * TM;
+        const int gi = tx * TM + mi, gj = ty * TM + mj;
+        if (gi < p.gx && gj < p.gy) {
+            float m = 0.0f;
+#pragma unroll
+            for (int r = 0; r < CELL + 2; ++r) m = fmaxf(m, s_row[mj * CELL + r][mi]);
+            p.grid[((long long)k * p.gy + gj) * p.gx + gi] = m;
+        }
+    }
+}
+
+// Pass 2 launch: the tiled form for 8- and 16-cell macro cells, else one
+// warp per macro cell.
+static int launch_grid_reduce(const KGrid &p, long long cells, int sms, cudaStream_t st)
+{
+    if (p.cell == 8 || p.cell == 16) {
+        const long long tm = 64 / p.cell;
+        const long long blocks = ((p.gx + tm - 1) / tm) * ((p.gy + tm - 1) / tm) * (long long)p.gz;
+        if (blocks <= 0x7fffffffLL) {
+            if (p.cell == 16) k_grid_reduce_tiled<16><<<(unsigned)blocks, 256, 0, st>>>(p);
+            else k_grid_reduce_tiled<8><<<(unsigned)blocks, 256, 0, st>>>(p);
+            return ISAAC_OK;
+        }
+    }
+    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
+    k_grid_reduce<<<b2, 256, 0, st>>>(p);
+    return ISAAC_OK;
 }
 
 // ------------------------------------------------------ value-range grid
@@ -720,8 +865,7 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
         k_grid_columns<0, 0><<<b1, 256, 0, st>>>(p);
     rc = check_cuda("isaac_opacity_grid columns launch");
     if (rc) return rc;
-    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
-    k_grid_reduce<<<b2, 256, 0, st>>>(p);
+    launch_grid_reduce(p, cells, sms, st);
     return check_cuda("isaac_opacity_grid reduce launch");
 }
 
@@ -815,7 +959,19 @@ extern "C" int isaac_opacity_grid_packed(const isaac_packed *vol, const isaac_ch
     }
     const bool scalar = p.nact == 1 && vol->pad == 1 && p.ch[0].n == 0 && vol->dtype != ISAAC_E4M3 &&
                         (cell == 8 || cell == 16);
-    if (scalar) {
+    if (scalar && vol->dtype != ISAAC_F32 && p.W % 2 == 0) {
+        const long long items2 = (long long)p.W / 2 * p.H * p.nchunks;
+        const unsigned b2c = (unsigned)std::max(1LL, std::min((items2 + 255) / 256, (long long)sms * 4));
+#define ISAAC_GPS2(DT)                                                                            \
+        if (cell == 16) k_grid_columns_packed_scalar2<DT, 16><<<b2c, 256, 0, st>>>(p);            \
+        else k_grid_columns_packed_scalar2<DT, 8><<<b2c, 256, 0, st>>>(p);
+        if (vol->dtype == ISAAC_BF16) {
+            ISAAC_GPS2(ISAAC_BF16)
+        } else {
+            ISAAC_GPS2(ISAAC_F16)
+        }
+#undef ISAAC_GPS2
+    } else if (scalar) {
 #define ISAAC_GPS(DT)                                                                             \
         if (cell == 16) k_grid_columns_packed_scalar<DT, 16><<<b1, 256, 0, st>>>(p);              \
         else k_grid_columns_packed_scalar<DT, 8><<<b1, 256, 0, st>>>(p);
@@ -836,8 +992,7 @@ extern "C" int isaac_opacity_grid_packed(const isaac_packed *vol, const isaac_ch
 #undef ISAAC_GP
     rc = check_cuda("isaac_opacity_grid_packed columns launch");
     if (rc) return rc;
-    const unsigned b2 = (unsigned)std::max(1LL, std::min((cells * 32 + 255) / 256, (long long)sms * 8));
-    k_grid_reduce<<<b2, 256, 0, st>>>(p);
+    launch_grid_reduce(p, cells, sms, st);
     return check_cuda("isaac_opacity_grid_packed reduce launch");
 }
 

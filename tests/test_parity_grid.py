@@ -104,3 +104,34 @@ def test_grid_wide_volume_warp_reduction(cuda_ok):
         torch.cuda.synchronize()
         np.testing.assert_allclose(g.cpu().numpy(), oracle.opacity_grid(sc, cell), rtol=0,
                                    atol=TOL_ALPHA)
+
+
+@pytest.mark.parametrize("cell", [8, 16])
+def test_grid_tiled_reductions(cuda_ok, cell):
+    """The tiled opacity-grid reduction (64 x 64 columns per block) over several
+    tiles in x and y with ragged last tiles: the grid of the float32 field and
+    of its BF16 copy (two columns per thread: n_x + 2 even) against the oracle,
+    and the value-range grid of the same field.  The field is BF16-representable,
+    so the copy holds the same values."""
+    import torch
+    from scenes_util import make_scene
+    n = (150, 97, 21)
+    rng = np.random.default_rng(81 + cell)
+    x = np.arange(n[0], dtype=np.float32)[None, None, :]
+    y = np.arange(n[1], dtype=np.float32)[None, :, None]
+    f = 0.5 + 0.3 * np.sin(0.11 * x) * np.cos(0.07 * y) + 0.15 * rng.random((n[2], n[1], n[0]))
+    f = f.astype(np.float32)
+    f = (f.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32)   # BF16 values
+    cams = synth.random_orbit_camera(n, 16, 16, seed=8)
+    sc = make_scene([f], [[]], [synth.lut_from_points(70 + cell)], [0.9], n, cams, 16, 16)
+    ds = isaac.DeviceScene(sc)
+    want = oracle.opacity_grid(sc, cell)
+    assert want.shape == tuple((k + cell - 1) // cell for k in n[::-1])
+    assert len(np.unique(want)) > want.size // 8          # maxima differ from cell to cell
+    g = ds.opacity_grid(cell)
+    gb = ds.pack("bf16").opacity_grid(cell)
+    r = ds.range_grid(cell)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(g.cpu().numpy(), want, rtol=0, atol=TOL_ALPHA)
+    np.testing.assert_allclose(gb.cpu().numpy(), want, rtol=0, atol=TOL_ALPHA)
+    assert np.array_equal(r.cpu().numpy(), oracle.range_grid(sc, cell))

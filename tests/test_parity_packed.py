@@ -187,12 +187,15 @@ def test_opacity_grid_of_packed_copy(cuda_ok, fmt, cell):
 
 
 @pytest.mark.parametrize("fmt", ["f32", "bf16", "f16", "e4m3"])
-def test_opacity_grid_of_packed_scalar_bubble(cuda_ok, fmt):
+@pytest.mark.parametrize("n", [64, 62, 61])
+def test_opacity_grid_of_packed_scalar_bubble(cuda_ok, fmt, n):
     """The learned workload's shape (one scalar source, identity chain): its
-    own walk for 8- and 16-cell macro cells (16-bit and float32 records), the
-    general one for other cells and for E4M3."""
+    own walk for 8- and 16-cell macro cells (float32 records, and 16-bit
+    records one column per thread when the padded row n + 2 is odd, two when
+    it is even; 62 leaves a ragged last macro cell), the general one for other
+    cells and for E4M3."""
     import torch
-    sc = synth.scene_bubble(64, frame=4, seed=3, width=32, height=32)
+    sc = synth.scene_bubble(n, frame=4, seed=3, width=32, height=32)
     pv = isaac.DeviceScene(sc).pack(fmt)
     deq = _dequantised_scene(sc, fmt)
     for cell in (8, 16, 5):
