@@ -941,11 +941,13 @@ __device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut
             const float s = (float)kk * p.step;
             c[u] = Shader::shade(p, s_lut, fmaf(s, dx, ex), fmaf(s, dy, ey), fmaf(s, dz, ez));
         }
+        // alpha is clamped here, on all lanes, rather than in the owner's loop
 #pragma unroll
         for (int u = 0; u < kStreamU; ++u) {
             const int slot = u * 32 / kStreamT;
             tile[slot * kRow + (u * 32) % kStreamT + lane] =
-                valid[u] ? c[u] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                valid[u] ? make_float4(c[u].x, c[u].y, c[u].z, clamp01(c[u].w))
+                         : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         __syncwarp();
         if (owner && live) {
@@ -954,8 +956,7 @@ __device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut
             bool done = false;
             for (int j = 0; j < nv; ++j) {
                 const float4 cj = row[j];
-                const float a = clamp01(cj.w);
-                const float t = (1.0f - A) * a;
+                const float t = (1.0f - A) * cj.w;
                 C0 = fmaf(t, cj.x, C0);
                 C1 = fmaf(t, cj.y, C1);
                 C2 = fmaf(t, cj.z, C2);
