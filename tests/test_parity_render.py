@@ -127,6 +127,35 @@ def test_domain_split_on_gpu(cuda_ok):
     assert np.abs(comp - ref["rgba"]).max() <= 2 * TOL_F32
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_far_camera_deep_domain_split(cuda_ok, seed):
+    """Large coordinates for the float-float ray setup: a 24 x 20 x 16 local box
+    deep inside a 4096 x 3000 x 2048 global volume, seen from ~6000 voxels
+    away through a 0.5-degree field of view, so ray parameters are ~1e4 voxels
+    and the first sample index counts from a global entry thousands of voxels
+    before the local box.  With termination off, every pixel's sample count
+    and colour must match the oracle (near-ties excluded)."""
+    rng = np.random.default_rng(seed)
+    n, g = (24, 20, 16), 1
+    gn, off = (4096, 3000, 2048), (2500, 1200, 900)
+    f = (0.2 + 0.6 * rng.random((n[2] + 2 * g, n[1] + 2 * g, n[0] + 2 * g))).astype(np.float32)
+    centre = np.asarray(off, np.float64) + np.asarray(n) / 2.0 - np.asarray(gn) / 2.0
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    up = (0.0, 1.0, 0.0) if abs(d[1]) < 0.9 else (1.0, 0.0, 0.0)
+    W, H = 64, 48
+    cam = (synth.look_at(centre + 6000.0 * d, centre, up), synth.perspective(0.5, W / H, 5000.0, 7000.0))
+    sc = make_scene([f], [[]], [synth.lut_from_points(30 + seed, alpha_max=0.2)], [1.0], n, cam,
+                    W, H, guard=g)
+    sc.global_n, sc.off, sc.term = gn, off, 2.0
+    g8, g32, gns = _gpu(sc)
+    r = oracle.render(sc)
+    rep = compare(g32, g8, gns, r)
+    assert_parity(rep, 1e-3, f"far camera, seed {seed}")
+    assert rep.hit > 300
+    assert r["kfirst"].max() > 1000             # samples counted from the far global entry
+
+
 def test_edge_cases(cuda_ok):
     base = small_pic_scene(n=16, guard=1, width=37, height=23, dist_factor=1.0)
     # ragged image size, 1x1 image, a single huge step, termination disabled
