@@ -424,9 +424,12 @@ class DeviceScene:
         return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
-                touched=None, lanes=None, depth=None):
+                touched=None, lanes=None, depth=None, luts=None):
         """Marshal one frame's arguments (camera, opts, framebuffer) once; the
-        returned tuple can be launched repeatedly with ``launch``."""
+        returned tuple can be launched repeatedly with ``launch``.  ``luts``: a
+        device float32 tensor shaped like ``self.luts`` to read the transfer
+        functions from instead (e.g. one of two buffers a pipeline uploads into
+        in turn)."""
         sc = self.scene
         cam = make_camera(sc.modelview if mv is None else mv,
                           sc.projection if proj is None else proj, sc.width, sc.height)
@@ -436,8 +439,13 @@ class DeviceScene:
                          touched.data_ptr() if touched is not None else None,
                          depth.data_ptr() if depth is not None else None)
         opts = make_opts(sc, mask, lanes)
-        keep = (cam, planes, fb, opts)
-        return (self.sources, self.chains, len(sc.sources), self.luts.data_ptr(),
+        if luts is None:
+            luts = self.luts
+        elif luts.shape != self.luts.shape or luts.dtype != self.luts.dtype or not luts.is_contiguous() \
+                or luts.device != self.luts.device:
+            raise ValueError("luts must be a contiguous float32 tensor shaped like the scene's, on its device")
+        keep = (cam, planes, fb, opts, luts)
+        return (self.sources, self.chains, len(sc.sources), luts.data_ptr(),
                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
                 C.byref(fb)), keep
 

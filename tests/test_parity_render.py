@@ -337,3 +337,28 @@ def test_every_chain_shape_against_oracle(cuda_ok, chains):
     sc = make_scene(fields, chains, luts, [0.3, 0.3, 0.2, 0.2], n, cams, 56, 44)
     rep, _, _ = _check(sc, f"chains {chains}")
     assert rep.hit > 300
+
+
+def test_prepared_frame_reads_the_given_lut_buffer(cuda_ok):
+    """A frame prepared with another LUT buffer reads that buffer: a copy of the
+    scene's LUTs gives the same image bit for bit, an all-transparent table the
+    background alone (the binding only passes the pointer)."""
+    import torch
+    sc = small_pic_scene()
+    ds = isaac.DeviceScene(sc)
+    out = torch.empty((sc.height, sc.width, 4), dtype=torch.uint8, device="cuda")
+    ds.launch(ds.prepare(out=out))
+    torch.cuda.synchronize()
+    ref = out.clone()
+    assert (ref[..., 3] > 0).sum() > 100
+    same = ds.luts.clone()
+    ds.launch(ds.prepare(out=out, luts=same))
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    clear = torch.zeros_like(ds.luts)
+    ds.launch(ds.prepare(out=out, luts=clear))
+    torch.cuda.synchronize()
+    bg = np.clip(np.floor(255.0 * np.asarray(sc.bg, np.float32) + 0.5), 0, 255).astype(np.uint8)
+    assert np.all(out.cpu().numpy() == bg)
+    with pytest.raises(ValueError):
+        ds.prepare(out=out, luts=torch.zeros(7, device="cuda"))
