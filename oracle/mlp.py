@@ -159,7 +159,12 @@ def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 
 def propose(p, X, ns, margin=2, threshold=0.9):
     """Sample range [kb, ke) per ray where conf >= threshold, else [0, ns)."""
-    u = forward(p, X)["u"]
+    return propose_rule(forward(p, X)["u"], ns, margin, threshold)
+
+
+def propose_rule(u, ns, margin=2, threshold=0.9):
+    """The proposal's decision from the network outputs u (N, 3)."""
+    u = np.asarray(u, np.float64)
     te, tx, conf = sigmoid(u[:, 0]), sigmoid(u[:, 1]), sigmoid(u[:, 2])
     ns = np.asarray(ns, np.int64)
     kb = np.clip(np.floor(te * ns).astype(np.int64) - margin, 0, ns)

@@ -84,3 +84,102 @@ def test_coverage_rule():
     # [8, 52) misses the last sample 52
     np.testing.assert_array_equal(mlp.coverage(te[:1], tx[:1], [8], [52], [100], 2), [0.0])
     np.testing.assert_array_equal(mlp.coverage(te[:1], tx[:1], [7], [51], [100], 2), [0.0])
+
+
+def test_targets_hand_computed():
+    """Labels of three rays with 16 samples each: a span [3, 11], a span that
+    ends on the last sample [0, 15], and a ray with no visible sample."""
+    ye, yx, empty = mlp.targets([3, 0, -1], [11, 15, -1], [16, 16, 16])
+    np.testing.assert_array_equal(ye, [3 / 16, 0.0, 1.0])
+    np.testing.assert_array_equal(yx, [12 / 16, 1.0, 0.0])
+    np.testing.assert_array_equal(empty, [False, False, True])
+
+
+def test_targets_are_the_tightest_covering_window():
+    """Used as a proposal with no margin, a ray's own targets cover its span,
+    and moving either end one sample inwards does not (so the end target is
+    (jl + 1)/ns, not jl/ns, and the start is jf/ns)."""
+    rng = np.random.default_rng(5)
+    ns = rng.choice([16, 32, 64, 128, 256], 200)
+    jf = (rng.uniform(size=200) * (ns - 1)).astype(int)
+    jl = jf + (rng.uniform(size=200) * (ns - jf)).astype(int)
+    ye, yx, _ = mlp.targets(jf, jl, ns)
+    np.testing.assert_array_equal(mlp.coverage(ye, yx, jf, jl, ns, 0), 1.0)
+    np.testing.assert_array_equal(mlp.coverage(ye + 1.0 / ns, yx, jf, jl, ns, 0), 0.0)
+    np.testing.assert_array_equal(mlp.coverage(ye, yx - 1.0 / ns, jf, jl, ns, 0), 0.0)
+
+
+def _hand_params():
+    """A network whose output is known in closed form: layer 1 passes x0,
+    -x1 and 2*x2 - 1 through ReLU on units 0..2 and ignores every other
+    input; layer 2 swaps units 0 and 1 and subtracts 0.25 from unit 0;
+    layer 3 triples; the output is (h0 + 0.5, h1 - h2 - 1, 3)."""
+    p = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    p["W1"][0, 0], p["W1"][1, 1], p["W1"][2, 2] = 1.0, -1.0, 2.0
+    p["b1"][2] = -1.0
+    p["W2"] = np.eye(mlp.WIDTH)
+    p["W2"][[0, 1]] = p["W2"][[1, 0]]
+    p["b2"][0] = -0.25
+    p["W3"] = 3.0 * np.eye(mlp.WIDTH)
+    p["W4"][0, 0], p["W4"][1, 1], p["W4"][2, 1] = 1.0, 1.0, -1.0
+    p["b4"][:] = (0.5, -1.0, 3.0)
+    return p
+
+
+def test_forward_closed_form():
+    X = np.random.default_rng(2).standard_normal((2, mlp.N_IN))   # other inputs must not matter
+    X[0, :3] = (0.8, -0.6, 0.3)
+    X[1, :3] = (-0.5, 0.4, 0.9)
+    f = mlp.forward(_hand_params(), X)
+    # row 0: h1 = (0.8, 0.6, 0) -> h2 = (0.35, 0.8, 0) -> h3 = (1.05, 2.4, 0)
+    # row 1: h1 = (0, 0, 0.8)   -> h2 = (0, 0, 0.8)   -> h3 = (0, 0, 2.4)
+    np.testing.assert_allclose(f["h1"][:, :3], [[0.8, 0.6, 0.0], [0.0, 0.0, 0.8]], atol=1e-15)
+    np.testing.assert_allclose(f["h3"][:, :3], [[1.05, 2.4, 0.0], [0.0, 0.0, 2.4]], atol=1e-14)
+    np.testing.assert_allclose(f["u"], [[1.55, 1.4, 3.0], [0.5, -3.4, 3.0]], atol=1e-14)
+    assert np.all(f["h1"][:, 3:] == 0.0) and np.all(f["h3"][:, 3:] == 0.0)
+
+
+def _const_params(b4):
+    p = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    p["b4"][:] = b4
+    return p
+
+
+def test_propose_constant_network():
+    """A constant network proposes te = sigmoid(b4[0]), tx = sigmoid(b4[1])
+    with confidence sigmoid(b4[2]) for every ray."""
+    X = np.zeros((3, mlp.N_IN))
+    ns = np.array([100, 7, 1])
+    # te = tx = 1/2, sure: [floor(ns/2) - 2, ceil(ns/2) + 2) clipped to [0, ns)
+    kb, ke, use = mlp.propose(_const_params((0.0, 0.0, 5.0)), X, ns, margin=2)
+    np.testing.assert_array_equal(kb, [48, 1, 0])
+    np.testing.assert_array_equal(ke, [52, 6, 1])
+    assert use.all()
+    # unsure (conf 1/2 < 0.9): the whole ray
+    kb, ke, use = mlp.propose(_const_params((0.0, 0.0, 0.0)), X, ns, margin=2)
+    np.testing.assert_array_equal(kb, [0, 0, 0])
+    np.testing.assert_array_equal(ke, ns)
+    assert not use.any()
+    # te > tx: an empty window at kb (te = 0.8808, tx = 0.1192; ns = 100 -> kb = 86)
+    kb, ke, use = mlp.propose(_const_params((2.0, -2.0, 5.0)), X[:1], ns[:1], margin=2)
+    assert (kb[0], ke[0], use[0]) == (86, 86, True)
+    # the threshold is inclusive
+    _, _, use = mlp.propose(_const_params((0.0, 0.0, 0.0)), X[:1], ns[:1], threshold=0.5)
+    assert use[0]
+
+
+def test_propose_agrees_with_coverage():
+    """A confident proposal's window contains a span exactly when the coverage
+    rule counts the ray as covered (the training target of the confidence)."""
+    rng = np.random.default_rng(9)
+    for trial in range(20):
+        b4 = (rng.normal(0, 2), rng.normal(0, 2), 5.0)
+        p = _const_params(b4)
+        ns = rng.integers(1, 400, 64)
+        jf = (rng.uniform(size=64) * ns).astype(int)
+        jl = jf + (rng.uniform(size=64) * (ns - jf)).astype(int)
+        kb, ke, use = mlp.propose(p, np.zeros((64, mlp.N_IN)), ns, margin=3)
+        te, tx = mlp.sigmoid(b4[0]), mlp.sigmoid(b4[1])
+        c = mlp.coverage(np.full(64, te), np.full(64, tx), jf, jl, ns, 3)
+        assert use.all()
+        np.testing.assert_array_equal((kb <= jf) & (ke >= jl + 1), c == 1.0)

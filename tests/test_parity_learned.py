@@ -246,3 +246,42 @@ def test_trained_proposal_gain_on_bubble(cuda_ok):
     assert lsb.mean() <= 1.0
     assert restricted > 0.5 * seen
     assert saved > 0.3
+
+
+@pytest.mark.parametrize("margin", [0, 3])
+def test_proposal_windows_match_oracle_rule(cuda_ok, margin):
+    """The windows the proposal kernel writes into the ray list equal the
+    oracle's proposal rule applied to the network outputs of the same rays
+    (forward pass on the same FP16 inputs); rays whose te*ns or tx*ns lies
+    within 1e-4 of an integer, or whose confidence lies within 1e-5 of the
+    threshold, are decided at a tie and only counted."""
+    import torch
+    sc = synth.scene_bubble(64, frame=4, seed=6, width=160, height=120, dist_factor=1.2)
+    ds = isaac.DeviceScene(sc)
+    grid = ds.opacity_grid(8)
+    rays, count, *_ = ds.trace()
+    k = int(count.item())
+    params = synth.mlp_params(21, bias_scale=0.5)
+    params["b4"] = np.asarray((params["b4"][0], params["b4"][1], 2.2), np.float32)
+    model = isaac.MLPModel(isaac.pack_mlp_params(params), train=False)
+    U = model.forward(isaac.mlp_features(rays[:k], k, sc.n, sc.step, grid, 8)).cpu().numpy()
+    l_rays, l_cnt, *_ = ds.trace(proposal=model.proposal(grid, 8, threshold=0.9, margin=margin))
+    torch.cuda.synchronize()
+    assert int(l_cnt.item()) == k
+    base = rays[:k].cpu().numpy()
+    got = l_rays[:k].cpu().numpy()
+    got = got[np.argsort(got[:, 7])]
+    order = np.argsort(base[:, 7])
+    base, U = base[order], U[order]
+    ns = base[:, 3]
+    kb, ke, use = omlp.propose_rule(U, ns, margin, 0.9)
+    te, tx, conf = (omlp.sigmoid(U[:, i].astype(np.float64)) for i in range(3))
+
+    def near_int(x):
+        return np.abs(x - np.round(x)) < 1e-4
+
+    tie = (np.abs(conf - 0.9) < 1e-5) | (use & (near_int(te * ns) | near_int(tx * ns)))
+    assert 0.2 < use.mean() < 0.95, use.mean()
+    assert tie.mean() < 0.01
+    ok = (got[:, 8] == kb) & (got[:, 3] == ke)
+    assert np.all(ok | tie), np.flatnonzero(~ok & ~tie)[:10]
