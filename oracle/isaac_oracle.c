@@ -173,11 +173,16 @@ static void orc_unproject(const double *Minv, double x, double y, double z, doub
 static int64_t orc_axis_index(int64_t i, int64_t n, int32_t guard)
 {
     /* guard == 0: no neighbour data, clamp to the border cell; otherwise the
-     * guard cells hold the neighbour's values (Sec. 3.1/3.2). */
+     * guard cells hold the neighbour's values (Sec. 3.1/3.2).  Every position
+     * the readings below interpolate at reads inside [-guard, n - 1 + guard];
+     * the clamp to that range only keeps a corner of weight zero at the edge
+     * of the guard layers (an iso-surface gradient position) in the array. */
     if (guard == 0) {
         if (i < 0) return 0;
         if (i > n - 1) return n - 1;
     }
+    if (i < -(int64_t)guard) return -(int64_t)guard;
+    if (i > n - 1 + guard) return n - 1 + guard;
     return i;
 }
 
@@ -526,7 +531,12 @@ static void orc_pixel(const orc_frame *F, int64_t pix, const orc_outputs *out, i
  *   when k is the ray's first sample; the smallest t wins (ties: lower s);
  *   at the hit point q the winning source's gradient is taken by central
  *   differences g_a = (v(q+) - v(q-)) / (q+ - q-)_a with q+- = q +- e_a, each
- *   clamped into the local box [0, n] along a (same interpolation);
+ *   clamped along a into the positions the source's own cells can
+ *   interpolate (same interpolation): [1/2 - g, n + g - 1/2] with g >= 1
+ *   guard cells (Sec. 3.1/3.2: guards carry the neighbour's values so that
+ *   interpolation across a sub-volume face needs no exchange; from g = 2 on
+ *   no hit inside the box is clamped, and a sub-volume's gradients equal the
+ *   whole volume's), [0, n] without guards or with interpolation off;
  *   n = -g/|g| (n = -d if g = 0), turned towards the viewer (n.(-d) >= 0);
  *   headlight Blinn-Phong with light, view and half vector all -d:
  *   rgb = LUT_s(iso[s]).rgb * (1/4 + 3/4 * n.(-d)) + 1/4 * (n.(-d))^32,
@@ -637,10 +647,13 @@ static void orc_pixel_iso(const orc_frame *F, const double *iso, int64_t pix, do
         if (win >= 0) {
             double q[3] = {ol[0] + t_hit * d[0], ol[1] + t_hit * d[1], ol[2] + t_hit * d[2]};
             double g[3];
+            const int32_t gw = p->interp ? F->src[win].guard : 0;
             for (int a = 0; a < 3; ++a) {
                 double qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
-                qp[a] = q[a] + 1.0 < (double)p->n[a] ? q[a] + 1.0 : (double)p->n[a];
-                qm[a] = q[a] - 1.0 > 0.0 ? q[a] - 1.0 : 0.0;
+                const double lo = gw > 0 ? 0.5 - (double)gw : 0.0;
+                const double hi = gw > 0 ? (double)p->n[a] + (double)gw - 0.5 : (double)p->n[a];
+                qp[a] = q[a] + 1.0 < hi ? q[a] + 1.0 : hi;
+                qm[a] = q[a] - 1.0 > lo ? q[a] - 1.0 : lo;
                 double h = qp[a] - qm[a];
                 g[a] = h > 0.0 ? (orc_source_value(F, win, qp) - orc_source_value(F, win, qm)) / h : 0.0;
             }

@@ -78,3 +78,63 @@ def test_nearer_source_wins():
     # a deactivated source is ignored
     r = oracle.render_iso(sc, [4.0, 5.0], mask=0b01)
     assert np.allclose(r["margin"][..., 5], 0.5 + 32 - 16)
+
+
+def _iso_split(n, g, declared_guard, iso, seed=5):
+    """Whole-volume iso frame and the two halves along x (each reading its
+    neighbour's cells through guards; `declared_guard` is the guard width the
+    halves declare), composited: the nearest hit of the halves wins."""
+    from paper_1611_09048_b300 import synth
+    fields = synth.pic_fields(n, g, seed=seed)
+    whole = synth.scene_pic(n=n, guard=g, width=48, height=40, seed=seed, fields=fields,
+                            dist_factor=1.0)
+    whole.bg = (0.0, 0.0, 0.0, 0.0)
+    ref = oracle.render_iso(whole, iso)
+    parts = []
+    for lo in (0, n // 2):
+        part = synth.scene_pic(n=n, guard=g, width=48, height=40, seed=seed, fields=fields,
+                               dist_factor=1.0)
+        part.bg = (0.0, 0.0, 0.0, 0.0)
+        part.global_n = (n, n, n)
+        part.off = (lo, 0, 0)
+        part.n = (n // 2, n, n)
+        for s in part.sources:
+            s.offset = s.offset + lo * s.strides[0]
+            s.guard = declared_guard
+        parts.append(oracle.render_iso(part, iso))
+    t = np.stack([np.where(r["margin"][..., 5] >= 0, r["margin"][..., 5], np.inf) for r in parts])
+    first = np.argmin(t, axis=0)
+    pick = lambda key: np.where((first == 0)[..., None], parts[0][key], parts[1][key])  # noqa: E731
+    return ref, pick("rgba"), pick("margin"), np.isfinite(t).any(axis=0)
+
+
+def test_domain_split_iso_equals_whole_with_two_guard_layers():
+    """Sec. 3.1/3.2: with two guard layers a sub-volume interpolates every
+    gradient position of its hits from its own cells, so the halves of a split
+    volume, composited by nearest hit, reproduce the whole volume's iso frame
+    -- except where a half's hit is its first sample, which has no previous
+    sample in the half for the secant step (the whole refines it)."""
+    iso = [0.6, 0.55, 0.5]
+    ref, rgba, m, hit = _iso_split(20, 2, 2, iso)
+    whole_hit = ref["margin"][..., 5] >= 0
+    np.testing.assert_array_equal(hit, whole_hit)
+    tie = ref["margin"][..., 2] < 1e-9
+    no_secant = (m[..., 3] >= oracle.INF) & (ref["margin"][..., 3] < oracle.INF)
+    keep = whole_hit & ~tie & ~no_secant
+    assert keep.sum() > 300 and no_secant.sum() < 0.1 * whole_hit.sum()
+    np.testing.assert_allclose(rgba[keep], ref["rgba"][keep], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(m[keep, 5], ref["margin"][keep, 5], rtol=0, atol=1e-9)
+
+
+def test_domain_split_iso_with_one_guard_layer_clamps_at_the_face():
+    """The same split with one declared guard layer: gradient positions are
+    clamped to half a voxel beyond the face, so hits within a voxel of the
+    split face shade differently from the whole volume (the data the halves
+    could read is the same; only the declared guard width differs)."""
+    iso = [0.6, 0.55, 0.5]
+    ref, rgba, m, hit = _iso_split(20, 2, 1, iso)
+    whole_hit = ref["margin"][..., 5] >= 0
+    keep = whole_hit & (ref["margin"][..., 2] >= 1e-9) & (m[..., 3] < oracle.INF)
+    diff = np.abs(rgba - ref["rgba"]).max(-1)
+    assert (diff[keep] > 1e-6).sum() > 0
+    np.testing.assert_allclose(m[keep, 5], ref["margin"][keep, 5], rtol=0, atol=1e-9)

@@ -90,3 +90,48 @@ def test_iso_rejects_nonfinite_threshold(cuda_ok):
     with pytest.raises(isaac.IsaacError) as e:
         isaac.DeviceScene(sc).render_iso([float("nan")])
     assert e.value.code == isaac.EINVAL
+
+
+def test_domain_split_iso_composites_to_whole(cuda_ok):
+    """Two halves along x with two guard layers, each an iso frame on the GPU
+    with a zero background and the depth output, composited by isaac_composite
+    (the nearest layer with a hit wins, alpha 1): the oracle's whole-volume
+    iso frame, except where a half's hit is its own first sample (no previous
+    sample in the half for the secant step) and at decision ties."""
+    import torch
+    n, g = 20, 2
+    iso = [0.6, 0.55, 0.5]
+    fields = synth.pic_fields(n, g, seed=5)
+    whole = synth.scene_pic(n=n, guard=g, width=48, height=40, seed=5, fields=fields,
+                            dist_factor=1.0)
+    whole.bg = (0.0, 0.0, 0.0, 0.0)
+    ref = oracle.render_iso(whole, iso)
+    layers, no_secant = [], np.zeros((40, 48), bool)
+    for lo in (0, n // 2):
+        part = synth.scene_pic(n=n, guard=g, width=48, height=40, seed=5, fields=fields,
+                               dist_factor=1.0)
+        part.bg = (0.0, 0.0, 0.0, 0.0)
+        part.global_n = (n, n, n)
+        part.off = (lo, 0, 0)
+        part.n = (n // 2, n, n)
+        for s in part.sources:
+            s.offset = s.offset + lo * s.strides[0]
+        pm = oracle.render_iso(part, iso)["margin"]
+        no_secant |= (pm[..., 5] >= 0) & (pm[..., 3] >= oracle.INF)
+        f32 = torch.empty((40, 48, 4), dtype=torch.float32, device="cuda")
+        dep = torch.empty((40, 48), dtype=torch.float32, device="cuda")
+        isaac.DeviceScene(part).render_iso(iso, rgba32=f32, depth=dep)
+        layers.append((f32, dep))
+    out8 = torch.empty((40, 48, 4), dtype=torch.uint8, device="cuda")
+    out32 = torch.empty((40, 48, 4), dtype=torch.float32, device="cuda")
+    isaac.composite(layers, bg=(0.0, 0.0, 0.0, 0.0), out=out8, rgba32=out32)
+    torch.cuda.synchronize()
+    m = ref["margin"]
+    hit = m[..., 5] >= 0
+    excl = (m[..., 0] < 1e-6) | (m[..., 1] < 1e-6) | (m[..., 2] < 1e-4 * 1.6)
+    excl |= hit & ((m[..., 3] < 1e-4) | (m[..., 4] < 1e-2))
+    keep = ~excl & ~(no_secant & (m[..., 3] < oracle.INF))
+    got = out32.cpu().numpy().astype(np.float64)
+    assert hit.sum() > 300 and keep.mean() > 0.9
+    assert np.abs(got - ref["rgba"])[keep].max() <= TOL_ISO
+    assert np.abs(out8.cpu().numpy().astype(int) - ref["rgba8"].astype(int))[keep].max() <= 1
