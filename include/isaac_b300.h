@@ -26,7 +26,7 @@
 extern "C" {
 #endif
 
-#define ISAAC_ABI_VERSION 2
+#define ISAAC_ABI_VERSION 3
 #define ISAAC_MAX_SOURCES 8   /* sources described per call */
 #define ISAAC_MAX_ACTIVE 4    /* sources rendered per call (active_mask bits) */
 #define ISAAC_MAX_FUNCTORS 8  /* functors per chain */
@@ -119,7 +119,16 @@ typedef struct {
     int32_t lanes_per_ray;   /* 0 = automatic, else 1, 2, 4, 8 or 16 threads cooperating on one
                                 ray; a hint (the nearest compiled variant is used) that
                                 never changes the image, only the speed */
+    uint32_t flags;          /* ISAAC_LUTS_HOST or 0; other bits are rejected (ISAAC_EINVAL) */
 } isaac_render_opts;
+
+/* opts.flags: `luts` is a HOST array (any host memory).  The call copies the
+ * active sources' LUTs before it returns (so the caller may reuse the array
+ * at once) into a library-owned pinned staging slot, and from there, on the
+ * call's stream, into the stream's workspace.  A stream has 8 such slots; a
+ * call waits only when the copy issued 8 calls earlier on that stream has not
+ * run yet.  Without the flag `luts` is device memory, read by the kernels. */
+#define ISAAC_LUTS_HOST 1u
 
 /* Output buffers (device, owned by the caller), row-major, row 0 at the top. */
 typedef struct {
@@ -154,8 +163,9 @@ typedef struct {
  *   (C, A) + (1-A) bg, quantised to round(255 * clamp(x, 0, 1)).
  *
  * sources, chains, weights: host arrays of n_sources (1..ISAAC_MAX_SOURCES).
- * luts: DEVICE array of n_sources * 256 * 4 floats (RGBA, source-major),
- *       16-byte aligned, owned by the caller.
+ * luts: n_sources * 256 * 4 floats (RGBA, source-major), owned by the
+ *       caller: a DEVICE array, 16-byte aligned, or with opts->flags &
+ *       ISAAC_LUTS_HOST a host array (copied before the call returns).
  * camera, clip (n_clip <= ISAAC_MAX_CLIP, may be NULL if 0), opts, fb: host
  *       structs, read before the call returns; the caller may reuse them.
  * stream: cudaStream_t to order the work on (NULL = legacy default stream).
@@ -286,8 +296,11 @@ int isaac_render_skip(const isaac_source *sources, const isaac_chain *chains, in
  *   crossing by one secant step towards the previous sample (none at the
  *   ray's first sample), the nearest crossing wins (ties: lower source);
  *   the normal is that source's central-difference gradient (one voxel,
- *   the two positions clamped into the local box [0, n], same
- *   interpolation), turned towards the viewer; with a headlight,
+ *   same interpolation; the two positions are clamped to what the source's
+ *   cells can interpolate: [1/2 - g, n + g - 1/2] with g = min(guard, 2)
+ *   guard layers, [0, n] without guards or with interpolation off, so that
+ *   with two guard layers a sub-volume shades its hits as the whole volume
+ *   does), turned towards the viewer; with a headlight,
  *   rgb = LUT_s(iso_values[s]).rgb * (1/4 + 3/4 * n.v) + 1/4 * (n.v)^32,
  *   clamped to [0, 1], alpha 1.  Rays without a crossing show the background.
  * iso_values: host, n_sources floats (finite for active sources).  The
@@ -378,6 +391,44 @@ typedef struct {
 /* Refresh the FP16 kernel copy from the float32 parameters. */
 int isaac_mlp_sync(const isaac_mlp *model, void *stream);
 
+/* isaac_mlp_create -- allocate a model's device buffers in one block
+ * (params, and with `train` grads, adam_m, adam_v; then half_w), fill the
+ * weights He-uniform, U(-sqrt(6/fan_in), sqrt(6/fan_in)), from the SplitMix64
+ * stream of `seed`, biases, gradients and moments with 0, step 0, and the
+ * FP16 copy.  Synchronises `stream`.  ISAAC_ENOMEM if allocation fails.
+ * isaac_mlp_destroy frees a model made by isaac_mlp_create (and zeroes the
+ * struct); a model whose buffers the caller owns is rejected (ISAAC_EINVAL). */
+int isaac_mlp_create(isaac_mlp *model, int32_t train, uint64_t seed, void *stream);
+int isaac_mlp_destroy(isaac_mlp *model);
+
+/*
+ * Checkpoint / resume of the proposal network.  Image layout (host memory,
+ * little-endian): a 64-byte header {char magic[8] = "ISAACMLP"; uint32
+ * version = 1; uint32 count = ISAAC_MLP_PARAMS; int32 step; uint32 flags
+ * (bit 0: Adam moments present); uint64 tag; uint32 crc; zero padding} then
+ * float32 params[count] and, with bit 0, adam_m[count] and adam_v[count].
+ * crc is the CRC-32 (zlib's) of everything after the header; tag is the
+ * caller's (e.g. the position of its training-data sampler).
+ * isaac_mlp_checkpoint_bytes: the image size with or without Adam moments.
+ * isaac_mlp_save writes the image of `model` (Adam moments when the model
+ * has them) after the work already queued on `stream`; it synchronises the
+ * stream and returns with the image complete.  ISAAC_ENOMEM if `bytes` is
+ * too small.
+ * isaac_mlp_load checks magic, version, count, size and CRC on the host
+ * before touching the device (ISAAC_EINVAL on any mismatch), then copies the
+ * parameters (and, for a model with Adam buffers, the moments and step; an
+ * image without moments gives such a model zero moments and step 0) and
+ * refreshes the FP16 copy; it synchronises the stream.  *tag (optional)
+ * receives the header's tag.
+ * Training is bitwise reproducible (the batch gradient is reduced in a fixed
+ * order), so a run resumed from a checkpoint equals the uninterrupted run
+ * when it is given the same batches.
+ */
+#define ISAAC_MLP_CKPT_HEADER 64
+int64_t isaac_mlp_checkpoint_bytes(int32_t with_adam);
+int isaac_mlp_save(const isaac_mlp *model, uint64_t tag, void *image, int64_t bytes, void *stream);
+int isaac_mlp_load(isaac_mlp *model, const void *image, int64_t bytes, uint64_t *tag, void *stream);
+
 /* Inputs of n_rays records into X (device, n_rays * 224 FP16, row-major);
  * grid as written by isaac_opacity_grid for the same volume size and cell. */
 int isaac_mlp_features(const isaac_ray *rays, int64_t n_rays, const int64_t vol_n[3], float step,
@@ -393,7 +444,10 @@ int isaac_mlp_forward(const isaac_mlp *model, const uint16_t *X, int64_t n_rays,
  * with no visible sample), c = 1 when the proposed range with `margin`
  * covers [jf, jl] (always for an empty ray).  rays supply jf, jl, nsteps.
  * model->grads holds the batch gradient afterwards; loss_sum (device,
- * optional) accumulates the batch's mean loss. */
+ * optional) accumulates the batch's mean loss.  The gradient is summed per
+ * 64-ray tile, per block over its tiles in order, then over at most 148
+ * blocks in block order (partial sums in the stream's workspace): the same
+ * inputs give the same bits on any run and any device. */
 int isaac_mlp_train_step(isaac_mlp *model, const uint16_t *X, const isaac_ray *rays,
                          int64_t n_rays, float lr, int32_t margin, float *loss_sum, void *stream);
 

@@ -21,8 +21,10 @@ int check_cuda(const char *what);
 
 int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_clip,
                   const isaac_render_opts *opt, KParams &p);
+// reach: guard layers the kernel may read (1; 2 for iso-surface gradients),
+// capped by the source's own guard width.
 int prepare_source(const isaac_source &src, int s, const int64_t n[3], int interp, float weight,
-                   int elem, KSource &ks, unsigned *nib, bool *wide);
+                   int elem, KSource &ks, unsigned *nib, bool *wide, int reach = 1);
 int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out);
 int prepare_fb(const isaac_framebuffer *fb, KParams &p);
 // Multiprocessor count of the current device (cached per device; 148 if the
@@ -37,7 +39,7 @@ void update_sources(int32_t n_sources, uint32_t active_mask);
 // Validate the sources of isaac_render and fill their part of KParams.
 int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
                     const float *luts, const float *weights, const isaac_render_opts *opts,
-                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out);
+                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out, int reach = 1);
 // Zero-copy frame kernel for a source signature and march mode (nullptr if none).
 FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, int mode, int rl,
                     int *rl_used);
@@ -52,6 +54,9 @@ int proposal_hook(const isaac_proposal *proposal, const isaac_render_opts *opts,
 // Lanes per ray for a rectangle of `rect_pixels` (hint 0 = automatic) when a
 // sample gathers `corner_bytes` per trilinear corner (0: unknown).
 int choose_lanes(long long rect_pixels, int hint, int corner_bytes = 0);
+// Bytes a trilinear corner gathers over the first `nact` sources of p (4 per
+// component), the corner_bytes of choose_lanes for a zero-copy frame.
+int zc_corner_bytes(const KParams &p, int nact);
 // Most march chunks a warp takes per atomic (KParams::grab, guided
 // self-scheduling): 16; the environment variable ISAAC_MARCH_GRAB (1..64)
 // overrides it, 1 = one chunk per atomic.  Scheduling only: the image does not

@@ -797,7 +797,9 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
         return fail(ISAAC_EINVAL, "n_sources %d outside 1..%d", n_sources, ISAAC_MAX_SOURCES);
     if (cell < 2 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 2..1024", cell);
     if (opts->active_mask >> n_sources) return fail(ISAAC_EINVAL, "active_mask beyond n_sources");
-    if (((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+    if (opts->flags & ~ISAAC_LUTS_HOST) return fail(ISAAC_EINVAL, "unknown opts.flags bits");
+    if (!(opts->flags & ISAAC_LUTS_HOST) && ((uintptr_t)luts) % 16)
+        return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
     KGrid p;
     memset(&p, 0, sizeof p);
     for (int a = 0; a < 3; ++a)
@@ -845,9 +847,15 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
     const size_t col_bytes = (size_t)p.gz * (size_t)p.W * (size_t)p.H * sizeof(float);
     KParams wp;
     memset(&wp, 0, sizeof wp);
+    if (opts->flags & ISAAC_LUTS_HOST) {   // staged into the workspace by bind_workspace
+        for (int a = 0; a < p.nact; ++a) wp.lut[a] = p.lut[a];
+        wp.luts_host = 1;
+    }
     void *cols = nullptr;
     int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
     if (rc) return rc;
+    if (opts->flags & ISAAC_LUTS_HOST)   // the staged device copies
+        for (int a = 0; a < p.nact; ++a) p.lut[a] = wp.lut[a];
     p.cols = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
     const int sms = sm_count();
     const long long items = (long long)p.W * p.H * p.nchunks;
@@ -943,9 +951,15 @@ extern "C" int isaac_opacity_grid_packed(const isaac_packed *vol, const isaac_ch
     const size_t col_bytes = (size_t)p.gz * (size_t)p.W * (size_t)p.H * sizeof(float);
     KParams wp;
     memset(&wp, 0, sizeof wp);
+    if (opts->flags & ISAAC_LUTS_HOST) {   // staged into the workspace by bind_workspace
+        for (int a = 0; a < p.nact; ++a) wp.lut[a] = p.lut[a];
+        wp.luts_host = 1;
+    }
     void *cols = nullptr;
     int rc = bind_workspace(wp, st, col_bytes + 16, &cols);
     if (rc) return rc;
+    if (opts->flags & ISAAC_LUTS_HOST)   // the staged device copies
+        for (int a = 0; a < p.nact; ++a) p.lut[a] = wp.lut[a];
     p.cols = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(cols) + 15) & ~uintptr_t(15));
     const int sms = sm_count();
     const long long items = (long long)p.W * p.H * p.nchunks;

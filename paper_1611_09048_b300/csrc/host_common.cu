@@ -201,7 +201,7 @@ int compile_chain(const isaac_chain &in, int fdim, int s, KChain &out)
 // kernel descriptor.  elem = bytes per element.  Returns the signature
 // nibble via *nib and whether 64-bit offsets are needed via *wide.
 int prepare_source(const isaac_source &src, int s, const int64_t n[3], int interp, float weight,
-                   int elem, KSource &ks, unsigned *nib, bool *wide)
+                   int elem, KSource &ks, unsigned *nib, bool *wide, int reach)
 {
     if (!src.ptr) return fail(ISAAC_EINVAL, "source %d: NULL pointer for an active source", s);
     if (src.f_dim < 1 || src.f_dim > 4)
@@ -212,7 +212,9 @@ int prepare_source(const isaac_source &src, int s, const int64_t n[3], int inter
                     (long long)src.offset);
     if (((uintptr_t)src.ptr) % (uintptr_t)elem != 0)
         return fail(ISAAC_EINVAL, "source %d: pointer not aligned to its element size", s);
-    const int g1 = (interp && src.guard >= 1) ? 1 : 0;
+    // guard layers read: one for the samples (positions in [0, n)), up to
+    // `reach` for positions beyond the box (iso-surface gradients)
+    const int g1 = interp ? std::min(src.guard, std::max(reach, 1)) : 0;
     // smallest and largest element index any sample can read
     long double lo = (long double)src.offset, hi = lo, span = 0.0L;
     for (int a = 0; a < 3; ++a) {
@@ -274,6 +276,7 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
                         (long long)opt->offset[a], (long long)(opt->offset[a] + opt->n[a]),
                         (long long)gn[a], a);
     }
+    if (opt->flags & ~ISAAC_LUTS_HOST) return fail(ISAAC_EINVAL, "unknown opts.flags bits 0x%x", opt->flags);
     if (!(opt->step > 0.0f) || !std::isfinite(opt->step))
         return fail(ISAAC_EINVAL, "step must be positive and finite");
     if (opt->interp != 0 && opt->interp != 1) return fail(ISAAC_EINVAL, "interp must be 0 or 1");

@@ -3,7 +3,10 @@
 // training pass with gradient accumulation, Adam.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "common.h"
 #include "mlp.cuh"
@@ -111,20 +114,28 @@ static __global__ void __launch_bounds__(128) k_mlp_forward(const __grid_constan
 struct KTrain {
     const __half *hw;
     const float *params;
-    float *grads;
+    float *part;              // per block: kPartStride floats (gradient partial sums, then the loss)
     const __half *X;
     const RayRec *rays;       // jf, jl, nsteps of every training ray
     long long n;
     float inv_n;
     int margin;
-    float *loss_sum;          // optional
 };
+
+// The batch gradient is reduced in a fixed order, so a training run is
+// bitwise reproducible (and a resumed run equals an uninterrupted one): block
+// b of at most kTrainBlocks takes the 64-ray tiles b, b + G, ... and sums
+// their gradients, in that order, into its own slot of kPartStride floats
+// (no atomics); k_mlp_reduce then adds the G slots in block order.  The grid
+// size depends on the batch size only, not on the device.
+constexpr int kTrainBlocks = 148;
+constexpr int kPartStride = ((N_PARAMS + 1 + 3) / 4) * 4;   // + the loss, 16-byte rows
 
 constexpr int kTrainSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W   // forward weights
                                  + 2 * MLP_W * LD_W + MLP_W * LD_B4             // backward weights
                                  + 64 * LD_IN + MLP_IN * LD_R                   // X, X^T
                                  + 6 * MLP_W * LD_R + 8 * LD_R;                 // h^T, dA^T tiles
-constexpr int kTrainSmemBytes = kTrainSmemHalves * 2 + 3 * 64 * 4;
+constexpr int kTrainSmemBytes = kTrainSmemHalves * 2 + 4 * 64 * 4;
 
 __device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + __expf(-x)); }
 
@@ -200,111 +211,145 @@ static __global__ void __launch_bounds__(128) k_mlp_train(const __grid_constant_
     __half *d1t = h3t + MLP_W * LD_R, *d2t = d1t + MLP_W * LD_R, *d3t = d2t + MLP_W * LD_R;
     __half *d4t = d3t + MLP_W * LD_R;
     int *s_jf = reinterpret_cast<int *>(d4t + 8 * LD_R), *s_jl = s_jf + 64, *s_ns = s_jl + 64;
+    float *s_loss = reinterpret_cast<float *>(s_ns + 64);
 
     load_weights_smem(p.hw, sT1, sT2, sT3, sT4, sB2, sB3, sB4);
-    const long long base = blockIdx.x * 64LL;
-    for (int i = threadIdx.x; i < 64 * MLP_IN; i += blockDim.x) {
-        const int rr = i / MLP_IN, k = i % MLP_IN;
-        const long long r = base + rr;
-        const __half v = r < p.n ? p.X[r * MLP_IN + k] : __float2half_rn(0.0f);
-        xs[rr * LD_IN + k] = v;
-        xt[k * LD_R + rr] = v;
-    }
-    for (int i = threadIdx.x; i < 8 * LD_R; i += blockDim.x) d4t[i] = __float2half_rn(0.0f);
-    if (threadIdx.x < 64) {
-        const long long r = base + threadIdx.x;
-        const bool ok = r < p.n;
-        s_jf[threadIdx.x] = ok ? p.rays[r].jf : -1;
-        s_jl[threadIdx.x] = ok ? p.rays[r].jl : -1;
-        s_ns[threadIdx.x] = ok ? p.rays[r].nsteps : 0;
-    }
-    __syncthreads();
-
+    float *part = p.part + (size_t)blockIdx.x * kPartStride;
+    const long long tiles = (p.n + 63) / 64;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     const int col0 = warp * 16;
-    Hidden hid;
-    float u[4];
-    mlp_forward_warp(xs, col0, sT1, sT2, sT3, sT4, p.params, u, &hid, h1t, h2t, h3t, col0);
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const bool first = tile == blockIdx.x;   // the block's first tile stores, later ones add
+        const long long base = tile * 64;
+        for (int i = threadIdx.x; i < 64 * MLP_IN; i += blockDim.x) {
+            const int rr = i / MLP_IN, k = i % MLP_IN;
+            const long long r = base + rr;
+            const __half v = r < p.n ? p.X[r * MLP_IN + k] : __float2half_rn(0.0f);
+            xs[rr * LD_IN + k] = v;
+            xt[k * LD_R + rr] = v;
+        }
+        for (int i = threadIdx.x; i < 8 * LD_R; i += blockDim.x) d4t[i] = __float2half_rn(0.0f);
+        if (threadIdx.x < 64) {
+            const long long r = base + threadIdx.x;
+            const bool ok = r < p.n;
+            s_jf[threadIdx.x] = ok ? p.rays[r].jf : -1;
+            s_jl[threadIdx.x] = ok ? p.rays[r].jl : -1;
+            s_ns[threadIdx.x] = ok ? p.rays[r].nsteps : 0;
+        }
+        __syncthreads();
 
-    // output gradient of rays col0+g and col0+g+8 (computed on lanes t == 0)
-    const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1), u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
-    float da[3] = {0, 0, 0}, db[3] = {0, 0, 0}, la = 0.0f, lb = 0.0f;
-    if (t == 0) {
-        const int ra = col0 + g, rb = ra + 8;
-        ray_grad(u[0], u[1], u2a, s_jf[ra], s_jl[ra], s_ns[ra], p.margin, base + ra < p.n, da[0],
-                 da[1], da[2], la);
-        ray_grad(u[2], u[3], u2b, s_jf[rb], s_jl[rb], s_ns[rb], p.margin, base + rb < p.n, db[0],
-                 db[1], db[2], lb);
-        for (int o = 0; o < 3; ++o) {
-            d4t[o * LD_R + ra] = __float2half_rn(da[o]);
-            d4t[o * LD_R + rb] = __float2half_rn(db[o]);
-        }
-        if (p.loss_sum) atomicAdd(p.loss_sum, (la + lb) * p.inv_n);
-    }
-    const float da2 = __shfl_up_sync(0xffffffffu, da[2], 1), db2 = __shfl_up_sync(0xffffffffu, db[2], 1);
-    unsigned A4[4][4];
-    for (int j = 0; j < 4; ++j)
-        for (int q = 0; q < 4; ++q) A4[j][q] = 0u;
-    if (t == 0) {
-        A4[0][0] = pack_h2(da[0], da[1]);
-        A4[0][1] = pack_h2(db[0], db[1]);
-    } else if (t == 1) {
-        A4[0][0] = pack_h2(da2, 0.0f);
-        A4[0][1] = pack_h2(db2, 0.0f);
-    }
-    float c[8][4];
-    unsigned A[4][4];
-    backward_layer(A4, 1, sB4, LD_B4, hid.m3, c, d3t, col0);        // dA3
-    for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
-    backward_layer(A, 4, sB3, LD_W, hid.m2, c, d2t, col0);          // dA2
-    for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
-    backward_layer(A, 4, sB2, LD_W, hid.m1, c, d1t, col0);          // dA1
-    __syncthreads();
+        Hidden hid;
+        float u[4];
+        mlp_forward_warp(xs, col0, sT1, sT2, sT3, sT4, p.params, u, &hid, h1t, h2t, h3t, col0);
 
-    // weight gradients over the block's 64 rays: dW = H^T . dA (jobs = m-tiles)
-    // layer 4: 4 m-tiles x 1 n-tile, layers 3, 2: 4 x 8, layer 1: 14 x 8
-    for (int job = warp; job < 26; job += 4) {
-        const __half *at, *bt;
-        int mt, nts, wo, out_dim;
-        if (job < 4) {
-            at = h3t; bt = d4t; mt = job; nts = 1; wo = P_W4; out_dim = MLP_OUT;
-        } else if (job < 8) {
-            at = h2t; bt = d3t; mt = job - 4; nts = 8; wo = P_W3; out_dim = MLP_W;
-        } else if (job < 12) {
-            at = h1t; bt = d2t; mt = job - 8; nts = 8; wo = P_W2; out_dim = MLP_W;
-        } else {
-            at = xt; bt = d1t; mt = job - 12; nts = 8; wo = P_W1; out_dim = MLP_W;
-        }
-        float acc[8][4];
-        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-        for (int ks = 0; ks < 4; ++ks) {
-            unsigned a[4];
-            frag_a(at, LD_R, mt * 16, ks * 16, a);
-            for (int nt = 0; nt < nts; ++nt) {
-                unsigned b[2];
-                frag_b(bt, LD_R, nt * 8, ks * 16, b);
-                mma16816(acc[nt], a, b);
+        // output gradient of rays col0+g and col0+g+8 (computed on lanes t == 0)
+        const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1), u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
+        float da[3] = {0, 0, 0}, db[3] = {0, 0, 0}, la = 0.0f, lb = 0.0f;
+        if (t == 0) {
+            const int ra = col0 + g, rb = ra + 8;
+            ray_grad(u[0], u[1], u2a, s_jf[ra], s_jl[ra], s_ns[ra], p.margin, base + ra < p.n, da[0],
+                     da[1], da[2], la);
+            ray_grad(u[2], u[3], u2b, s_jf[rb], s_jl[rb], s_ns[rb], p.margin, base + rb < p.n, db[0],
+                     db[1], db[2], lb);
+            for (int o = 0; o < 3; ++o) {
+                d4t[o * LD_R + ra] = __float2half_rn(da[o]);
+                d4t[o * LD_R + rb] = __float2half_rn(db[o]);
             }
+            s_loss[ra] = la;
+            s_loss[rb] = lb;
         }
-        for (int nt = 0; nt < nts; ++nt)
-            for (int j = 0; j < 4; ++j) {
-                const int in = mt * 16 + g + (j >= 2 ? 8 : 0);
-                const int out = nt * 8 + 2 * t + (j & 1);
-                if (out < out_dim) atomicAdd(p.grads + wo + in * out_dim + out, acc[nt][j] * p.inv_n);
+        const float da2 = __shfl_up_sync(0xffffffffu, da[2], 1), db2 = __shfl_up_sync(0xffffffffu, db[2], 1);
+        unsigned A4[4][4];
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) A4[j][q] = 0u;
+        if (t == 0) {
+            A4[0][0] = pack_h2(da[0], da[1]);
+            A4[0][1] = pack_h2(db[0], db[1]);
+        } else if (t == 1) {
+            A4[0][0] = pack_h2(da2, 0.0f);
+            A4[0][1] = pack_h2(db2, 0.0f);
+        }
+        float c[8][4];
+        unsigned A[4][4];
+        backward_layer(A4, 1, sB4, LD_B4, hid.m3, c, d3t, col0);        // dA3
+        for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
+        backward_layer(A, 4, sB3, LD_W, hid.m2, c, d2t, col0);          // dA2
+        for (int j = 0; j < 4; ++j) acc_to_a(c[2 * j], c[2 * j + 1], A[j]);
+        backward_layer(A, 4, sB2, LD_W, hid.m1, c, d1t, col0);          // dA1
+        __syncthreads();
+
+        // weight gradients over the tile's 64 rays: dW = H^T . dA (jobs = m-tiles)
+        // layer 4: 4 m-tiles x 1 n-tile, layers 3, 2: 4 x 8, layer 1: 14 x 8;
+        // every element of the block's slot has one owner thread, the same for
+        // every tile, so the slot is updated without atomics
+        for (int job = warp; job < 26; job += 4) {
+            const __half *at, *bt;
+            int mt, nts, wo, out_dim;
+            if (job < 4) {
+                at = h3t; bt = d4t; mt = job; nts = 1; wo = P_W4; out_dim = MLP_OUT;
+            } else if (job < 8) {
+                at = h2t; bt = d3t; mt = job - 4; nts = 8; wo = P_W3; out_dim = MLP_W;
+            } else if (job < 12) {
+                at = h1t; bt = d2t; mt = job - 8; nts = 8; wo = P_W2; out_dim = MLP_W;
+            } else {
+                at = xt; bt = d1t; mt = job - 12; nts = 8; wo = P_W1; out_dim = MLP_W;
             }
+            float acc[8][4];
+            for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+            for (int ks = 0; ks < 4; ++ks) {
+                unsigned a[4];
+                frag_a(at, LD_R, mt * 16, ks * 16, a);
+                for (int nt = 0; nt < nts; ++nt) {
+                    unsigned b[2];
+                    frag_b(bt, LD_R, nt * 8, ks * 16, b);
+                    mma16816(acc[nt], a, b);
+                }
+            }
+            for (int nt = 0; nt < nts; ++nt)
+                for (int j = 0; j < 4; ++j) {
+                    const int in = mt * 16 + g + (j >= 2 ? 8 : 0);
+                    const int out = nt * 8 + 2 * t + (j & 1);
+                    if (out < out_dim) {
+                        float *dst = part + wo + in * out_dim + out;
+                        const float v = acc[nt][j] * p.inv_n;
+                        *dst = first ? v : *dst + v;
+                    }
+                }
+        }
+        // bias gradients: sum of dA over the tile's rays, in ray order
+        for (int o = threadIdx.x; o < 3 * MLP_W + MLP_OUT; o += blockDim.x) {
+            const __half *row;
+            int bo;
+            if (o < MLP_W) { row = d1t + o * LD_R; bo = P_B1 + o; }
+            else if (o < 2 * MLP_W) { row = d2t + (o - MLP_W) * LD_R; bo = P_B2 + o - MLP_W; }
+            else if (o < 3 * MLP_W) { row = d3t + (o - 2 * MLP_W) * LD_R; bo = P_B3 + o - 2 * MLP_W; }
+            else { row = d4t + (o - 3 * MLP_W) * LD_R; bo = P_B4 + o - 3 * MLP_W; }
+            float sum = 0.0f;
+            for (int r = 0; r < 64; ++r) sum += __half2float(row[r]);
+            const float v = sum * p.inv_n;
+            part[bo] = first ? v : part[bo] + v;
+        }
+        // the tile's loss, in ray order
+        if (threadIdx.x == blockDim.x - 1) {
+            float sum = 0.0f;
+            for (int r = 0; r < 64; ++r) sum += s_loss[r];
+            const float v = sum * p.inv_n;
+            part[N_PARAMS] = first ? v : part[N_PARAMS] + v;
+        }
+        __syncthreads();   // the next tile overwrites the shared tiles
     }
-    // bias gradients: sum of dA over the block's rays
-    for (int o = threadIdx.x; o < 3 * MLP_W + MLP_OUT; o += blockDim.x) {
-        const __half *row;
-        int bo;
-        if (o < MLP_W) { row = d1t + o * LD_R; bo = P_B1 + o; }
-        else if (o < 2 * MLP_W) { row = d2t + (o - MLP_W) * LD_R; bo = P_B2 + o - MLP_W; }
-        else if (o < 3 * MLP_W) { row = d3t + (o - 2 * MLP_W) * LD_R; bo = P_B3 + o - 2 * MLP_W; }
-        else { row = d4t + (o - 3 * MLP_W) * LD_R; bo = P_B4 + o - 3 * MLP_W; }
+}
+
+// Batch gradient (and loss) = the blocks' slots added in block order.
+static __global__ void k_mlp_reduce(const float *__restrict__ part, int blocks, float *grads,
+                                    float *loss_sum)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= N_PARAMS; i += gridDim.x * blockDim.x) {
         float s = 0.0f;
-        for (int r = 0; r < 64; ++r) s += __half2float(row[r]);
-        atomicAdd(p.grads + bo, s * p.inv_n);
+        for (int b = 0; b < blocks; ++b) s += part[(size_t)b * kPartStride + i];
+        if (i < N_PARAMS) grads[i] = s;
+        else if (loss_sum) *loss_sum += s;
     }
 }
 
@@ -335,6 +380,215 @@ static int check_model(const isaac_mlp *m, bool train)
     if (((uintptr_t)m->half_w) % 16 || ((uintptr_t)m->params) % 16)
         return fail(ISAAC_EINVAL, "model buffers must be 16-byte aligned");
     return ISAAC_OK;
+}
+
+// ------------------------------------------------- create, checkpoint, destroy
+
+namespace {
+
+// Base pointers of the blocks isaac_mlp_create allocated (isaac_mlp_destroy
+// frees only those).
+std::mutex g_created_mu;
+std::vector<void *> g_created;
+
+constexpr size_t kParamFloats = ((N_PARAMS + 3) / 4) * 4;   // 16-byte aligned arrays
+
+// CRC-32 (reflected, polynomial 0xEDB88320, initial and final XOR ~0: the
+// checksum of zlib and PNG), table-driven.
+uint32_t crc32_bytes(const unsigned char *b, size_t n)
+{
+    static uint32_t table[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+    });
+    uint32_t c = 0xFFFFFFFFu;
+    for (size_t i = 0; i < n; ++i) c = table[(c ^ b[i]) & 0xFFu] ^ (c >> 8);
+    return c ^ 0xFFFFFFFFu;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): the seeded stream of the initial weights.
+uint64_t splitmix64(uint64_t &state)
+{
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct CkptHeader {
+    char magic[8];        // "ISAACMLP"
+    uint32_t version;     // 1
+    uint32_t count;       // ISAAC_MLP_PARAMS
+    int32_t step;
+    uint32_t flags;       // bit 0: Adam moments follow the parameters
+    uint64_t tag;
+    uint32_t crc;         // CRC-32 of everything after the header
+    unsigned char pad[ISAAC_MLP_CKPT_HEADER - 36];
+};
+static_assert(sizeof(CkptHeader) == ISAAC_MLP_CKPT_HEADER, "checkpoint header layout");
+
+}  // namespace
+
+extern "C" int64_t isaac_mlp_checkpoint_bytes(int32_t with_adam)
+{
+    return (int64_t)ISAAC_MLP_CKPT_HEADER + (int64_t)(with_adam ? 3 : 1) * N_PARAMS * 4;
+}
+
+extern "C" int isaac_mlp_create(isaac_mlp *m, int32_t train, uint64_t seed, void *stream)
+{
+    clear_error();
+    if (!m) return fail(ISAAC_EINVAL, "model is required");
+    const size_t floats = kParamFloats * (train ? 4 : 1);
+    const size_t bytes = floats * sizeof(float) + (size_t)N_HALF * sizeof(__half);
+    void *base = nullptr;
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ISAAC_ENOMEM, "cannot allocate %zu bytes for the model", bytes);
+    }
+    // He-uniform weights U(-sqrt(6/fan_in), +sqrt(6/fan_in)), zero biases
+    std::vector<float> init(N_PARAMS, 0.0f);
+    uint64_t state = seed;
+    const int layers[4][3] = {{P_W1, MLP_IN, MLP_W}, {P_W2, MLP_W, MLP_W}, {P_W3, MLP_W, MLP_W},
+                              {P_W4, MLP_W, MLP_OUT}};
+    for (const auto &L : layers) {
+        const double lim = std::sqrt(6.0 / (double)L[1]);
+        for (int i = 0; i < L[1] * L[2]; ++i) {
+            const double u = (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+            init[L[0] + i] = (float)((2.0 * u - 1.0) * lim);
+        }
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    float *f = static_cast<float *>(base);
+    isaac_mlp out;
+    out.params = f;
+    out.grads = train ? f + kParamFloats : nullptr;
+    out.adam_m = train ? f + 2 * kParamFloats : nullptr;
+    out.adam_v = train ? f + 3 * kParamFloats : nullptr;
+    out.half_w = reinterpret_cast<uint16_t *>(f + floats);
+    out.step = 0;
+    if (cudaMemsetAsync(base, 0, floats * sizeof(float), st) != cudaSuccess ||
+        cudaMemcpyAsync(out.params, init.data(), N_PARAMS * sizeof(float), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {   // `init` is a pageable host vector
+        const int rc = check_cuda("isaac_mlp_create (initial weights)");
+        cudaFree(base);
+        return rc;
+    }
+    k_mlp_half<<<64, 256, 0, st>>>(out.params, reinterpret_cast<__half *>(out.half_w));
+    const int rc = check_cuda("isaac_mlp_create");
+    if (rc) {
+        cudaFree(base);
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_created_mu);
+        g_created.push_back(base);
+    }
+    *m = out;
+    return ISAAC_OK;
+}
+
+extern "C" int isaac_mlp_destroy(isaac_mlp *m)
+{
+    clear_error();
+    if (!m) return fail(ISAAC_EINVAL, "model is required");
+    {
+        std::lock_guard<std::mutex> lock(g_created_mu);
+        auto it = std::find(g_created.begin(), g_created.end(), static_cast<void *>(m->params));
+        if (it == g_created.end())
+            return fail(ISAAC_EINVAL, "the model's buffers were not allocated by isaac_mlp_create");
+        g_created.erase(it);
+    }
+    cudaFree(m->params);
+    memset(m, 0, sizeof *m);
+    return check_cuda("isaac_mlp_destroy");
+}
+
+extern "C" int isaac_mlp_save(const isaac_mlp *m, uint64_t tag, void *image, int64_t bytes,
+                              void *stream)
+{
+    clear_error();
+    if (!m || !m->params || !image) return fail(ISAAC_EINVAL, "model params and image are required");
+    const bool adam = m->adam_m && m->adam_v;
+    const int64_t need = isaac_mlp_checkpoint_bytes(adam ? 1 : 0);
+    if (bytes < need)
+        return fail(ISAAC_ENOMEM, "the image holds %lld bytes, the checkpoint needs %lld",
+                    (long long)bytes, (long long)need);
+    unsigned char *out = static_cast<unsigned char *>(image);
+    float *payload = reinterpret_cast<float *>(out + ISAAC_MLP_CKPT_HEADER);
+    const cudaStream_t st = (cudaStream_t)stream;
+    // stream-ordered after the caller's training steps; the image is complete
+    // when the call returns
+    const float *src[3] = {m->params, m->adam_m, m->adam_v};
+    for (int k = 0; k < (adam ? 3 : 1); ++k)
+        if (cudaMemcpyAsync(payload + (size_t)k * N_PARAMS, src[k], N_PARAMS * sizeof(float),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return check_cuda("isaac_mlp_save (copy)");
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda("isaac_mlp_save (sync)");
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "ISAACMLP", 8);
+    h.version = 1;
+    h.count = N_PARAMS;
+    h.step = m->step;
+    h.flags = adam ? 1u : 0u;
+    h.tag = tag;
+    h.crc = crc32_bytes(out + ISAAC_MLP_CKPT_HEADER, (size_t)(need - ISAAC_MLP_CKPT_HEADER));
+    memcpy(out, &h, sizeof h);
+    return ISAAC_OK;
+}
+
+extern "C" int isaac_mlp_load(isaac_mlp *m, const void *image, int64_t bytes, uint64_t *tag,
+                              void *stream)
+{
+    clear_error();
+    if (!m || !image) return fail(ISAAC_EINVAL, "model and image are required");
+    if (bytes < ISAAC_MLP_CKPT_HEADER) return fail(ISAAC_EINVAL, "image shorter than the header");
+    CkptHeader h;
+    memcpy(&h, image, sizeof h);
+    if (memcmp(h.magic, "ISAACMLP", 8) != 0) return fail(ISAAC_EINVAL, "not a proposal-network checkpoint");
+    if (h.version != 1) return fail(ISAAC_EINVAL, "checkpoint version %u (1 expected)", h.version);
+    if (h.count != (uint32_t)N_PARAMS)
+        return fail(ISAAC_EINVAL, "checkpoint holds %u parameters (%d expected)", h.count, N_PARAMS);
+    const bool adam = (h.flags & 1u) != 0;
+    if (h.flags & ~1u) return fail(ISAAC_EINVAL, "unknown checkpoint flags 0x%x", h.flags);
+    const int64_t need = isaac_mlp_checkpoint_bytes(adam ? 1 : 0);
+    if (bytes < need)
+        return fail(ISAAC_EINVAL, "checkpoint truncated: %lld of %lld bytes", (long long)bytes,
+                    (long long)need);
+    const unsigned char *in = static_cast<const unsigned char *>(image);
+    if (crc32_bytes(in + ISAAC_MLP_CKPT_HEADER, (size_t)(need - ISAAC_MLP_CKPT_HEADER)) != h.crc)
+        return fail(ISAAC_EINVAL, "checkpoint checksum mismatch (corrupt image)");
+    int rc = check_model(m, false);
+    if (rc) return rc;
+    const float *payload = reinterpret_cast<const float *>(in + ISAAC_MLP_CKPT_HEADER);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const bool model_adam = m->adam_m && m->adam_v;
+    if (cudaMemcpyAsync(m->params, payload, N_PARAMS * sizeof(float), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return check_cuda("isaac_mlp_load (parameters)");
+    if (model_adam) {
+        // Adam state from the image, or a fresh optimiser (zero moments, step 0)
+        for (int k = 0; k < 2; ++k) {
+            float *dst = k ? m->adam_v : m->adam_m;
+            const cudaError_t e = adam
+                ? cudaMemcpyAsync(dst, payload + (size_t)(k + 1) * N_PARAMS, N_PARAMS * sizeof(float),
+                                  cudaMemcpyHostToDevice, st)
+                : cudaMemsetAsync(dst, 0, N_PARAMS * sizeof(float), st);
+            if (e != cudaSuccess) return check_cuda("isaac_mlp_load (Adam state)");
+        }
+    }
+    k_mlp_half<<<64, 256, 0, st>>>(m->params, reinterpret_cast<__half *>(m->half_w));
+    // the image may be pageable memory the caller frees after the call
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_cuda("isaac_mlp_load (sync)");
+    m->step = model_adam && adam ? h.step : 0;
+    if (tag) *tag = h.tag;
+    return check_cuda("isaac_mlp_load");
 }
 
 extern "C" int isaac_mlp_sync(const isaac_mlp *m, void *stream)
@@ -406,20 +660,26 @@ extern "C" int isaac_mlp_train_step(isaac_mlp *m, const uint16_t *X, const isaac
     if (((uintptr_t)X) % 4) return fail(ISAAC_EINVAL, "X must be 4-byte aligned");
     if (!std::isfinite(lr) || lr < 0.0f) return fail(ISAAC_EINVAL, "lr must be finite and >= 0");
     const cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemsetAsync(m->grads, 0, N_PARAMS * sizeof(float), st) != cudaSuccess)
-        return check_cuda("grad reset");
+    const long long tiles = (n_rays + 63) / 64;
+    const int blocks = (int)std::min<long long>(tiles, kTrainBlocks);
+    // the blocks' partial sums live in the stream's workspace
+    KParams wp;
+    memset(&wp, 0, sizeof wp);
+    void *part = nullptr;
+    rc = bind_workspace(wp, st, (size_t)blocks * kPartStride * sizeof(float) + 16, &part);
+    if (rc) return rc;
     KTrain p;
     p.hw = reinterpret_cast<const __half *>(m->half_w);
     p.params = m->params;
-    p.grads = m->grads;
+    p.part = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(part) + 15) & ~uintptr_t(15));
     p.X = reinterpret_cast<const __half *>(X);
     p.rays = reinterpret_cast<const RayRec *>(rays);
     p.n = n_rays;
     p.inv_n = 1.0f / (float)n_rays;
     p.margin = margin;
-    p.loss_sum = loss_sum;
     cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmemBytes);
-    k_mlp_train<<<(unsigned)((n_rays + 63) / 64), 128, kTrainSmemBytes, st>>>(p);
+    k_mlp_train<<<(unsigned)blocks, 128, kTrainSmemBytes, st>>>(p);
+    k_mlp_reduce<<<(N_PARAMS + 256) / 256, 256, 0, st>>>(p.part, blocks, m->grads, loss_sum);
     rc = check_cuda("isaac_mlp_train_step (gradients)");
     if (rc) return rc;
     m->step += 1;

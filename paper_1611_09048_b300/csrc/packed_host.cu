@@ -189,7 +189,9 @@ static int render_packed_impl(const isaac_packed *vol, const isaac_chain *chains
     if (rc) return rc;
     rc = prepare_fb(fb, p);
     if (rc) return rc;
-    if (!luts || ((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+    if (!luts || (!(opts->flags & ISAAC_LUTS_HOST) && ((uintptr_t)luts) % 16))
+        return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+    if (opts->flags & ISAAC_LUTS_HOST) p.luts_host = 1;   // staged when the workspace is bound
     // Every packed source is evaluated (its components share the record); an
     // inactive one gets an identity chain and weight 0, which adds exactly +0.
     int off = 0;

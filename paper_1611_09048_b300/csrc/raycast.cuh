@@ -142,6 +142,8 @@ struct KParams {
     int rx0, ry0, rx1, ry1;          // rectangle of pixels that can hit the box
     int max_steps;                   // samples on the longest chord of the local box
     int grab;                        // march: most chunks of 32/RL rays a warp takes per atomic
+    int luts_host;                   // host only: 1 = lut[] are host addresses still to be
+                                     // staged into the workspace, 2 = staged
     // empty-space skipping: one bit per macro cell of skip_cell^3 cells, 32
     // per word (1 = every sample whose position lies in it has opacity 0)
     const unsigned *empty;
@@ -1010,8 +1012,9 @@ __device__ __forceinline__ float value_of(const KParams &p, int which, float x, 
 // source's chain value reaches its threshold; each crossing source refines
 // the crossing by one secant step towards the previous sample, the nearest
 // wins (ties: lower source); the normal is the winning source's central-
-// difference gradient (one voxel, positions clamped into the box), turned
-// towards the viewer; headlight
+// difference gradient (one voxel, positions clamped to what the source's
+// cells can interpolate: [1/2 - g, n + g - 1/2] with g >= 1 guard layers
+// read, [0, n] without), turned towards the viewer; headlight
 // Blinn-Phong: rgb = LUT(iso).rgb * (1/4 + 3/4 n.v) + 1/4 (n.v)^32, alpha 1).
 // The RL lanes of a group evaluate consecutive samples; a ballot finds the
 // first one that crosses.
@@ -1072,10 +1075,14 @@ __device__ __forceinline__ void iso_ray(const KParams &p, unsigned idx, int lane
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     if (win >= 0) {
         const float qx = fmaf(s_hit, r.dx, r.ex), qy = fmaf(s_hit, r.dy, r.ey), qz = fmaf(s_hit, r.dz, r.ez);
-        // central differences over one voxel, positions clamped into the box
-        const float xp = fminf(qx + 1.0f, (float)p.nx), xm = fmaxf(qx - 1.0f, 0.0f);
-        const float yp = fminf(qy + 1.0f, (float)p.ny), ym = fmaxf(qy - 1.0f, 0.0f);
-        const float zp = fminf(qz + 1.0f, (float)p.nz), zm = fmaxf(qz - 1.0f, 0.0f);
+        // central differences over one voxel, positions clamped to the range
+        // the winning source's readable cells interpolate (guard layers read:
+        // -lo, two at most in this mode; none with interpolation off)
+        const int gw = INTERP ? -p.src[win].lo : 0;
+        const float plo = gw > 0 ? 0.5f - (float)gw : 0.0f, pad = gw > 0 ? (float)gw - 0.5f : 0.0f;
+        const float xp = fminf(qx + 1.0f, (float)p.nx + pad), xm = fmaxf(qx - 1.0f, plo);
+        const float yp = fminf(qy + 1.0f, (float)p.ny + pad), ym = fmaxf(qy - 1.0f, plo);
+        const float zp = fminf(qz + 1.0f, (float)p.nz + pad), zm = fmaxf(qz - 1.0f, plo);
         const float gx = xp > xm ? (value_of<NACT, SIG, INTERP, Idx>(p, win, xp, qy, qz) -
                                     value_of<NACT, SIG, INTERP, Idx>(p, win, xm, qy, qz)) / (xp - xm) : 0.0f;
         const float gy = yp > ym ? (value_of<NACT, SIG, INTERP, Idx>(p, win, qx, yp, qz) -

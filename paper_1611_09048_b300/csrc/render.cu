@@ -27,11 +27,66 @@ struct Workspace {
 static std::mutex g_ws_mu;
 static std::vector<Workspace> g_ws;
 
+// Device copies of host LUTs (ISAAC_LUTS_HOST) sit at the end of the workspace.
+constexpr size_t kWsLutBytes = (size_t)ISAAC_MAX_ACTIVE * 256 * sizeof(float4);
+
+// Host LUTs go through a ring of pinned slots per (device, stream): the call
+// copies them into the next slot on the host, then the slot to the workspace
+// on the stream; an event per slot tells when the slot may be refilled.
+constexpr int kLutSlots = 8;
+struct LutStage {
+    int device;
+    cudaStream_t stream;
+    float4 *host;                 // kLutSlots * ISAAC_MAX_ACTIVE * 256 pinned entries
+    cudaEvent_t done[kLutSlots];
+    bool used[kLutSlots];
+    int next;
+};
+static std::vector<LutStage> g_lut_stage;   // guarded by g_ws_mu
+
+static int stage_host_luts(KParams &p, float4 *dev_luts, int nact, int dev, cudaStream_t st)
+{
+    LutStage *g = nullptr;
+    for (LutStage &e : g_lut_stage)
+        if (e.device == dev && e.stream == st) g = &e;
+    if (!g) {
+        LutStage e{};
+        e.device = dev;
+        e.stream = st;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&e.host), kLutSlots * kWsLutBytes,
+                          cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ISAAC_ENOMEM, "cannot allocate pinned LUT staging (%zu bytes)",
+                        kLutSlots * kWsLutBytes);
+        }
+        for (int i = 0; i < kLutSlots; ++i) {
+            if (cudaEventCreateWithFlags(&e.done[i], cudaEventDisableTiming) != cudaSuccess)
+                return check_cuda("LUT staging event");
+        }
+        g_lut_stage.push_back(e);
+        g = &g_lut_stage.back();
+    }
+    const int slot = g->next;
+    g->next = (g->next + 1) % kLutSlots;
+    if (g->used[slot] && cudaEventSynchronize(g->done[slot]) != cudaSuccess)
+        return check_cuda("LUT staging slot wait");
+    float4 *h = g->host + (size_t)slot * ISAAC_MAX_ACTIVE * 256;
+    for (int a = 0; a < nact; ++a) memcpy(h + (size_t)a * 256, p.lut[a], 256 * sizeof(float4));
+    if (cudaMemcpyAsync(dev_luts, h, (size_t)nact * 256 * sizeof(float4), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return check_cuda("LUT upload");
+    if (cudaEventRecord(g->done[slot], st) != cudaSuccess) return check_cuda("LUT staging event");
+    g->used[slot] = true;
+    for (int a = 0; a < nact; ++a) p.lut[a] = dev_luts + (size_t)a * 256;
+    p.luts_host = 2;
+    return ISAAC_OK;
+}
+
 int bind_workspace(KParams &p, cudaStream_t st, size_t extra, void **extra_ptr)
 {
     const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
     const size_t lists = (size_t)kWsHeader + (size_t)std::max(1LL, rect) * (sizeof(RayRec) + sizeof(unsigned));
-    const size_t need = lists + extra;
+    const size_t need = lists + ((extra + 15) & ~(size_t)15) + kWsLutBytes + 256;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("cudaGetDevice");
     std::lock_guard<std::mutex> lock(g_ws_mu);
@@ -61,6 +116,14 @@ int bind_workspace(KParams &p, cudaStream_t st, size_t extra, void **extra_ptr)
     p.rays = reinterpret_cast<RayRec *>(static_cast<char *>(w->ptr) + kWsHeader);
     p.longs = reinterpret_cast<unsigned *>(p.rays + std::max(1LL, rect));
     if (extra_ptr) *extra_ptr = static_cast<char *>(w->ptr) + lists;
+    if (p.luts_host == 1) {
+        // the last kWsLutBytes of the block, 256-byte aligned (need reserves the slack)
+        const uintptr_t end = reinterpret_cast<uintptr_t>(w->ptr) + w->bytes - kWsLutBytes;
+        float4 *dev_luts = reinterpret_cast<float4 *>(end & ~uintptr_t(255));
+        int nact = 0;
+        while (nact < ISAAC_MAX_ACTIVE && p.lut[nact]) ++nact;
+        return stage_host_luts(p, dev_luts, nact, dev, st);
+    }
     return ISAAC_OK;
 }
 
@@ -93,7 +156,7 @@ int choose_lanes(long long rect_pixels, int hint, int corner_bytes)
     return corner_bytes >= 24 ? 8 : 4;
 }
 
-static int zc_corner_bytes(const KParams &p, int nact)
+int zc_corner_bytes(const KParams &p, int nact)
 {
     int b = 0;
     for (int a = 0; a < nact; ++a) b += 4 * p.src[a].fdim;
@@ -166,7 +229,7 @@ FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, int mode, int
 
 int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int32_t n_sources,
                     const float *luts, const float *weights, const isaac_render_opts *opts,
-                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out)
+                    KParams &p, int *nact_out, unsigned *sig_out, bool *wide_out, int reach)
 {
     if (!sources || !chains || !weights)
         return fail(ISAAC_EINVAL, "sources, chains and weights are required");
@@ -186,17 +249,19 @@ int prepare_sources(const isaac_source *sources, const isaac_chain *chains, int3
         unsigned nib = 0;
         bool w = false;
         int rc = prepare_source(sources[s], s, opts->n, opts->interp, weights[s], 4, p.src[nact],
-                                &nib, &w);
+                                &nib, &w, reach);
         if (rc) return rc;
         rc = compile_chain(chains[s], sources[s].f_dim, s, p.ch[nact]);
         if (rc) return rc;
         if (!luts) return fail(ISAAC_EINVAL, "luts is NULL");
-        if (((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+        if (!(opts->flags & ISAAC_LUTS_HOST) && ((uintptr_t)luts) % 16)
+            return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
         p.lut[nact] = reinterpret_cast<const float4 *>(luts) + (size_t)s * 256;
         sig |= nib << (4 * nact);
         wide |= w;
         ++nact;
     }
+    if (opts->flags & ISAAC_LUTS_HOST) p.luts_host = 1;   // staged when the workspace is bound
     *nact_out = nact;
     *sig_out = sig;
     *wide_out = wide;
@@ -390,7 +455,9 @@ extern "C" int isaac_render_iso(const isaac_source *sources, const isaac_chain *
     unsigned sig = 0;
     bool wide = false;
     update_sources(n_sources, opts->active_mask);
-    rc = prepare_sources(sources, chains, n_sources, luts, ones, opts, p, &nact, &sig, &wide);
+    // two guard layers where the sources have them: the gradient stencil of a
+    // hit reaches one voxel beyond the box
+    rc = prepare_sources(sources, chains, n_sources, luts, ones, opts, p, &nact, &sig, &wide, 2);
     if (rc) return rc;
     rc = prepare_fb(fb, p);
     if (rc) return rc;
@@ -426,6 +493,16 @@ extern "C" int isaac_release_workspaces(void)
         }
     }
     g_ws.swap(keep);
+    std::vector<LutStage> keep_stage;
+    for (LutStage &e : g_lut_stage) {
+        if (e.device == dev) {
+            for (int i = 0; i < kLutSlots; ++i) cudaEventDestroy(e.done[i]);
+            cudaFreeHost(e.host);
+        } else {
+            keep_stage.push_back(e);
+        }
+    }
+    g_lut_stage.swap(keep_stage);
     return check_cuda("isaac_release_workspaces");
 }
 

@@ -79,6 +79,9 @@ extern "C" int isaac_render_noalloc(const isaac_source *sources, const isaac_cha
     memset(&p, 0, sizeof p);
     int rc = prepare_frame(camera, clip, n_clip, opts, p);
     if (rc) return rc;
+    if (opts->flags & ISAAC_LUTS_HOST)
+        return fail(ISAAC_EINVAL, "isaac_render_noalloc reads device LUTs only (host LUTs need "
+                                  "the pinned staging isaac_render allocates)");
     int nact = 0;
     unsigned sig = 0;
     bool wide = false;
@@ -101,8 +104,8 @@ extern "C" int isaac_render_noalloc(const isaac_source *sources, const isaac_cha
                     "isaac_render_noalloc holds at most %lld rays -- use isaac_render or a "
                     "smaller image", p.rx1 - p.rx0, p.ry1 - p.ry0, rect, kNoAllocMaxRays);
     int rl = 1;
-    FrameLaunch fn = find_zc(nact, sig, opts->interp, wide, false,
-                             choose_lanes(rect, opts->lanes_per_ray), &rl);
+    FrameLaunch fn = find_zc(nact, sig, opts->interp, wide, MODE_PLAIN,
+                             choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact)), &rl);
     if (!fn) return fail(ISAAC_ENOTSUP, "no kernel for %d sources", nact);
     void *scratch = nullptr;
     int sms = 0;
@@ -110,9 +113,10 @@ extern "C" int isaac_render_noalloc(const isaac_source *sources, const isaac_cha
     if (rc) return rc;
     p.ctr = static_cast<WsCounters *>(scratch);
     p.rays = reinterpret_cast<RayRec *>(static_cast<char *>(scratch) + kWsHeader);
+    p.grab = march_grab();
     launch_fill(p, st);     // also resets the counters left by the previous call
     launch_setup(p, st);
-    const long long want = (rect * rl + 127) / 128;
-    fn(p, dim3((unsigned)std::max(1LL, std::min(want, (long long)sms * 8))), st);
+    const long long want = (rect * rl + kMarchThreads - 1) / kMarchThreads;
+    fn(p, dim3((unsigned)std::max(1LL, std::min(want, (long long)sms * kMarchBlocksPerSM))), st);
     return check_cuda("isaac_render_noalloc launch");
 }

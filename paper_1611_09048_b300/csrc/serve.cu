@@ -443,6 +443,8 @@ extern "C" int isaac_server_create(const isaac_source *sources, const isaac_chai
         return fail(ISAAC_EINVAL, "max_batch must be 1..%d", ISAAC_SERVER_MAX_BATCH);
     if (cfg->budget_bytes < (1 << 20)) return fail(ISAAC_EINVAL, "budget below 1 MiB");
     if (((uintptr_t)luts) % 16) return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
+    if (opts->flags & ISAAC_LUTS_HOST)
+        return fail(ISAAC_EINVAL, "the server's LUTs are device memory (requests carry host LUTs)");
     if (n_clip < 0 || n_clip > ISAAC_MAX_CLIP || (n_clip > 0 && !clip))
         return fail(ISAAC_EINVAL, "n_clip %d outside 0..%d (or clip is NULL)", n_clip, ISAAC_MAX_CLIP);
     std::unique_ptr<isaac_server> s(new isaac_server());

@@ -22,6 +22,7 @@ MAX_CLIP = 6
 
 OK, EINVAL, EGUARD, ENOMEM, ECUDA, ENOTSUP = 0, -1, -2, -3, -4, -5
 F32, BF16, F16, E4M3 = 0, 1, 2, 3
+LUTS_HOST = 1   # isaac_render_opts.flags: `luts` is a host array
 OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 
 # every C symbol declared in include/isaac_b300.h
@@ -33,7 +34,8 @@ EXPORTS = ("isaac_render", "isaac_last_error", "isaac_abi_version", "isaac_pack_
            "isaac_server_submit", "isaac_server_poll", "isaac_server_outstanding",
            "isaac_server_destroy", "isaac_time_march", "isaac_range_grid", "isaac_render_skip",
            "isaac_render_iso", "isaac_probe_read", "isaac_composite", "isaac_copy_source",
-           "isaac_set_update_hook", "isaac_opacity_grid_packed")
+           "isaac_set_update_hook", "isaac_opacity_grid_packed", "isaac_mlp_create",
+           "isaac_mlp_destroy", "isaac_mlp_checkpoint_bytes", "isaac_mlp_save", "isaac_mlp_load")
 
 # fn(source, enabled, user) of isaac_set_update_hook
 UPDATE_FN = C.CFUNCTYPE(None, C.c_int32, C.c_int32, C.c_void_p)
@@ -68,7 +70,8 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("n", C.c_int64 * 3), ("global_n", C.c_int64 * 3), ("offset", C.c_int64 * 3),
                 ("step", C.c_float), ("interp", C.c_int32), ("term_alpha", C.c_float),
-                ("bg", C.c_float * 4), ("active_mask", C.c_uint32), ("lanes_per_ray", C.c_int32)]
+                ("bg", C.c_float * 4), ("active_mask", C.c_uint32), ("lanes_per_ray", C.c_int32),
+                ("flags", C.c_uint32)]
 
 
 class Framebuffer(C.Structure):
@@ -183,6 +186,17 @@ def load(path: Optional[str] = None):
             [C.POINTER(Proposal), C.c_void_p]
         lib.isaac_mlp_sync.restype = C.c_int
         lib.isaac_mlp_sync.argtypes = [C.POINTER(Mlp), C.c_void_p]
+        lib.isaac_mlp_create.restype = C.c_int
+        lib.isaac_mlp_create.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_uint64, C.c_void_p]
+        lib.isaac_mlp_destroy.restype = C.c_int
+        lib.isaac_mlp_destroy.argtypes = [C.POINTER(Mlp)]
+        lib.isaac_mlp_checkpoint_bytes.restype = C.c_int64
+        lib.isaac_mlp_checkpoint_bytes.argtypes = [C.c_int32]
+        lib.isaac_mlp_save.restype = C.c_int
+        lib.isaac_mlp_save.argtypes = [C.POINTER(Mlp), C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]
+        lib.isaac_mlp_load.restype = C.c_int
+        lib.isaac_mlp_load.argtypes = [C.POINTER(Mlp), C.c_void_p, C.c_int64, C.POINTER(C.c_uint64),
+                                       C.c_void_p]
         lib.isaac_mlp_features.restype = C.c_int
         lib.isaac_mlp_features.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_float, C.c_void_p,
                                            C.c_int32, C.c_void_p, C.c_void_p]
@@ -441,11 +455,19 @@ class DeviceScene:
         opts = make_opts(sc, mask, lanes)
         if luts is None:
             luts = self.luts
+            lut_ptr = luts.data_ptr()
+        elif isinstance(luts, np.ndarray):     # host LUTs: copied by the call
+            if luts.dtype != np.float32 or luts.size != self.luts.numel() or not luts.flags.c_contiguous:
+                raise ValueError("host luts must be a contiguous float32 array of the scene's LUT size")
+            opts.flags = LUTS_HOST
+            lut_ptr = luts.ctypes.data
         elif luts.shape != self.luts.shape or luts.dtype != self.luts.dtype or not luts.is_contiguous() \
                 or luts.device != self.luts.device:
             raise ValueError("luts must be a contiguous float32 tensor shaped like the scene's, on its device")
+        else:
+            lut_ptr = luts.data_ptr()
         keep = (cam, planes, fb, opts, luts)
-        return (self.sources, self.chains, len(sc.sources), luts.data_ptr(),
+        return (self.sources, self.chains, len(sc.sources), lut_ptr,
                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
                 C.byref(fb)), keep
 
@@ -456,9 +478,10 @@ class DeviceScene:
 
     def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
                mask=None, want_f32=False, want_nsamp=False, touched=None, lanes=None,
-               depth=None):
+               depth=None, luts=None):
         """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
-        as device tensors (``depth``: optional (H, W) float32 output)."""
+        as device tensors (``depth``: optional (H, W) float32 output; ``luts``:
+        a device tensor, or a host float32 array copied by the call)."""
         import torch
         W, H = self.scene.width, self.scene.height
         if out is None:
@@ -467,20 +490,26 @@ class DeviceScene:
             rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         if nsamples is None and want_nsamp:
             nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
-        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes, depth), stream)
+        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes, depth, luts),
+                    stream)
         return out, rgba32, nsamples
 
 
-    def opacity_grid(self, cell=16, mask=None, stream=None, out=None):
-        """Max-opacity grid (Gz, Gy, Gx) float32 on the device."""
+    def opacity_grid(self, cell=16, mask=None, stream=None, out=None, host_luts=None):
+        """Max-opacity grid (Gz, Gy, Gx) float32 on the device (``host_luts``:
+        a host float32 array to read the transfer functions from instead)."""
         import torch
         sc = self.scene
         G = [(int(k) + cell - 1) // cell for k in sc.n]
         if out is None:
             out = torch.empty((G[2], G[1], G[0]), dtype=torch.float32, device=self.device)
         opts = make_opts(sc, mask)
+        lut_ptr = self.luts.data_ptr()
+        if host_luts is not None:
+            opts.flags = LUTS_HOST
+            lut_ptr = np.ascontiguousarray(host_luts, np.float32).ctypes.data
         check(load().isaac_opacity_grid(self.sources, self.chains, len(sc.sources),
-                                        self.luts.data_ptr(), C.cast(self.weights, C.c_void_p),
+                                        lut_ptr, C.cast(self.weights, C.c_void_p),
                                         C.byref(opts), int(cell), out.data_ptr(), out.numel(),
                                         _stream_handle(stream)))
         return out
@@ -521,14 +550,16 @@ class DeviceScene:
         self.launch_skip(self.prepare_skip(ranges, cell, mv, proj, out, f32, ns, mask, lanes), stream)
         return out, f32, ns
 
-    def prepare_iso(self, iso, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None):
+    def prepare_iso(self, iso, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
+                    depth=None):
         """Marshal one iso-surface frame (``iso``: one threshold per source)."""
         sc = self.scene
         cam = make_camera(sc.modelview if mv is None else mv,
                           sc.projection if proj is None else proj, sc.width, sc.height)
         planes, n_clip = make_planes(sc.clip)
         fb = Framebuffer(out.data_ptr(), rgba32.data_ptr() if rgba32 is not None else None,
-                         nsamples.data_ptr() if nsamples is not None else None, None)
+                         nsamples.data_ptr() if nsamples is not None else None, None,
+                         depth.data_ptr() if depth is not None else None)
         opts = make_opts(sc, mask)
         iso_arr = (C.c_float * len(sc.sources))(*[float(v) for v in iso])
         keep = (cam, planes, fb, opts, iso_arr)
@@ -542,14 +573,16 @@ class DeviceScene:
         check(load().isaac_render_iso(*args, _stream_handle(stream)))
 
     def render_iso(self, iso, mv=None, proj=None, out=None, stream=None, mask=None,
-                   want_f32=False, want_nsamp=False):
+                   want_f32=False, want_nsamp=False, rgba32=None, depth=None):
         import torch
         W, H = self.scene.width, self.scene.height
         if out is None:
             out = torch.empty((H, W, 4), dtype=torch.uint8, device=self.device)
-        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device) if want_f32 else None
+        f32 = rgba32
+        if f32 is None and want_f32:
+            f32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         ns = torch.empty((H, W), dtype=torch.int32, device=self.device) if want_nsamp else None
-        self.launch_iso(self.prepare_iso(iso, mv, proj, out, f32, ns, mask), stream)
+        self.launch_iso(self.prepare_iso(iso, mv, proj, out, f32, ns, mask, depth), stream)
         return out, f32, ns
 
     def trace(self, mv=None, proj=None, out=None, proposal=None, capacity=None, stream=None,
@@ -847,6 +880,15 @@ class MLPModel:
     def named(self):
         return unpack_mlp_params(self.params.cpu().numpy())
 
+    def save(self, tag=0, stream=None) -> bytes:
+        """Checkpoint image (header, parameters, Adam moments when training)."""
+        return checkpoint_save(self.desc, tag, stream)
+
+    def load(self, image, stream=None) -> int:
+        """Restore from a checkpoint image; returns its tag."""
+        return checkpoint_load(self.desc, image, stream)
+
+
     def forward(self, X, stream=None):
         import torch
         U = torch.empty((X.shape[0], 3), dtype=torch.float32, device=self.device)
@@ -865,6 +907,56 @@ class MLPModel:
                      stats.data_ptr() if stats is not None else None)
         p._keep = (grid, stats)
         return p
+
+
+def checkpoint_save(desc, tag=0, stream=None) -> bytes:
+    lib = load()
+    n = lib.isaac_mlp_checkpoint_bytes(1 if desc.adam_m and desc.adam_v else 0)
+    buf = (C.c_ubyte * n)()
+    check(lib.isaac_mlp_save(C.byref(desc), int(tag), buf, n, _stream_handle(stream)))
+    return bytes(buf)
+
+
+def checkpoint_load(desc, image, stream=None) -> int:
+    tag = C.c_uint64(0)
+    data = bytes(image)
+    check(load().isaac_mlp_load(C.byref(desc), data, len(data), C.byref(tag), _stream_handle(stream)))
+    return int(tag.value)
+
+
+class LibraryMLP:
+    """A proposal network whose buffers the library allocates
+    (isaac_mlp_create) and frees (close / isaac_mlp_destroy)."""
+
+    def __init__(self, train=True, seed=0, stream=None):
+        self.desc = Mlp()
+        check(load().isaac_mlp_create(C.byref(self.desc), 1 if train else 0, int(seed),
+                                      _stream_handle(stream)))
+
+    @property
+    def step(self):
+        return self.desc.step
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        C.memmove(out.ctypes.data, self.save()[64:64 + 4 * MLP_PARAMS], 4 * MLP_PARAMS)
+        return out
+
+    def train_step(self, X, rays, lr=1e-3, margin=2, loss_sum=None, stream=None):
+        check(load().isaac_mlp_train_step(C.byref(self.desc), X.data_ptr(), rays.data_ptr(),
+                                          X.shape[0], float(lr), int(margin),
+                                          loss_sum.data_ptr() if loss_sum is not None else None,
+                                          _stream_handle(stream)))
+
+    def save(self, tag=0, stream=None) -> bytes:
+        return checkpoint_save(self.desc, tag, stream)
+
+    def load(self, image, stream=None) -> int:
+        return checkpoint_load(self.desc, image, stream)
+
+    def close(self):
+        if self.desc.params:
+            check(load().isaac_mlp_destroy(C.byref(self.desc)))
 
 
 def mlp_features(rays, n_rays, vol_n, step, grid, cell, stream=None):

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version():
-    assert isaac.load().isaac_abi_version() == 2
+    assert isaac.load().isaac_abi_version() == 3
 
 
 def test_struct_sizes_match_header_layout():
@@ -44,8 +44,9 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(isaac.Chain) == 4 + 24 * isaac.MAX_FUNCTORS
     assert C.sizeof(isaac.Camera) == 256 + 8
     assert C.sizeof(isaac.Framebuffer) == 5 * 8
-    # 9 int64, step, interp, term_alpha, bg[4], active_mask, lanes_per_ray -> 108, 8-aligned
+    # 9 int64, step, interp, term_alpha, bg[4], active_mask, lanes_per_ray, flags -> 112
     assert C.sizeof(isaac.RenderOpts) == 112
+    assert isaac.RenderOpts.flags.offset == 108
 
 
 FAKE = 0x7F0000000000  # never dereferenced: every call below fails validation first
@@ -187,6 +188,12 @@ def test_rejects_misaligned_lut():
     a = _valid_call_args()
     a["luts"] = FAKE + 4
     _expect(a, isaac.EINVAL, "16-byte")
+
+
+def test_rejects_unknown_opts_flags():
+    a = _valid_call_args()
+    a["opts"].flags = 0x6
+    _expect(a, isaac.EINVAL, "flags")
 
 
 # ------------------------------------------------------------ serving loop
