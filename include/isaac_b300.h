@@ -451,7 +451,13 @@ int isaac_mlp_forward(const isaac_mlp *model, const uint16_t *X, int64_t n_rays,
 int isaac_mlp_train_step(isaac_mlp *model, const uint16_t *X, const isaac_ray *rays,
                          int64_t n_rays, float lr, int32_t margin, float *loss_sum, void *stream);
 
-/* The interval proposal applied to one frame. */
+/* The interval proposal applied to one frame.
+ * widen != 0: a confident ray's range is widened to keep every chord segment
+ * whose grid feature is nonzero -- segment i of 32 covers samples
+ * [floor(i*nsteps/32), ceil((i+1)*nsteps/32)) and its feature is the grid at
+ * its midpoint -- i.e. the range becomes the hull of the network's range
+ * (when not empty) and those segments.  The network may tighten a range
+ * within what the grid marks as possibly visible, never cut such a part. */
 typedef struct {
     const isaac_mlp *model;   /* params + half_w are read */
     const float *grid;        /* device max-opacity grid of this frame (isaac_opacity_grid) */
@@ -459,6 +465,7 @@ typedef struct {
     float threshold;          /* confidence needed to restrict a ray (e.g. 0.9) */
     int32_t margin;           /* samples added on both sides of the proposed range */
     int32_t *stats;           /* optional device int32[2]: += rays seen, rays restricted */
+    int32_t widen;            /* 1: keep the grid's nonzero chord segments (see above) */
 } isaac_proposal;
 
 /*

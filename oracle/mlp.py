@@ -157,17 +157,48 @@ def adam(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return p2, m2, v2
 
 
-def propose(p, X, ns, margin=2, threshold=0.9):
+def propose(p, X, ns, margin=2, threshold=0.9, widen=None):
     """Sample range [kb, ke) per ray where conf >= threshold, else [0, ns)."""
-    return propose_rule(forward(p, X)["u"], ns, margin, threshold)
+    return propose_rule(forward(p, X)["u"], ns, margin, threshold, widen)
 
 
-def propose_rule(u, ns, margin=2, threshold=0.9):
-    """The proposal's decision from the network outputs u (N, 3)."""
+def nonzero_samples(e, d, ns, step, grid, cell):
+    """Per ray, the sample indices k in [0, ns) whose position e + k*step*d
+    lies in a macro cell (floor(position / cell), clamped to the grid) with
+    a nonzero grid value (grid shaped (Gz, Gy, Gx))."""
+    G = np.array(grid.shape[::-1])
+    out = []
+    for r in range(len(ns)):
+        k = np.arange(int(ns[r]), dtype=np.float64)
+        pos = np.asarray(e[r], np.float64)[None, :] + (k * step)[:, None] * np.asarray(d[r], np.float64)[None, :]
+        idx = np.clip(np.floor(pos / cell).astype(np.int64), 0, G - 1)
+        out.append(np.flatnonzero(np.asarray(grid)[idx[:, 2], idx[:, 1], idx[:, 0]] > 0))
+    return out
+
+
+def propose_rule(u, ns, margin=2, threshold=0.9, widen=None):
+    """The proposal's decision from the network outputs u (N, 3).
+
+    widen = dict(e, d, step, grid, cell) of the same rays: a confident ray's
+    range then becomes the hull of the network's range (if not empty) and
+    every sample in a macro cell with a nonzero grid value (nonzero_samples),
+    before it is clipped to the ray."""
     u = np.asarray(u, np.float64)
     te, tx, conf = sigmoid(u[:, 0]), sigmoid(u[:, 1]), sigmoid(u[:, 2])
     ns = np.asarray(ns, np.int64)
-    kb = np.clip(np.floor(te * ns).astype(np.int64) - margin, 0, ns)
-    ke = np.clip(np.ceil(tx * ns).astype(np.int64) + margin, 0, ns)
+    kb = np.floor(te * ns).astype(np.int64) - margin
+    ke = np.ceil(tx * ns).astype(np.int64) + margin
     use = conf >= threshold
-    return np.where(use, kb, 0), np.where(use, np.maximum(ke, np.where(use, kb, 0)), ns), use
+    if widen is not None:
+        keep = nonzero_samples(widen["e"], widen["d"], ns, widen["step"], widen["grid"], widen["cell"])
+        for r in range(len(ns)):
+            if not use[r] or len(keep[r]) == 0:
+                continue
+            lo, hi = int(keep[r][0]), int(keep[r][-1]) + 1
+            if ke[r] > kb[r]:
+                kb[r], ke[r] = min(kb[r], lo), max(ke[r], hi)
+            else:
+                kb[r], ke[r] = lo, hi
+    kb = np.clip(kb, 0, ns)
+    ke = np.clip(ke, kb, ns)
+    return np.where(use, kb, 0), np.where(use, ke, ns), use

@@ -695,6 +695,51 @@ extern "C" int isaac_mlp_train_step(isaac_mlp *m, const uint16_t *X, const isaac
 
 namespace isaac {
 
+// Whether macro cell idx has a nonzero grid value: from the block's bitmask
+// of the grid (shared memory) when there is one, else from the grid.
+__device__ __forceinline__ bool cell_on(const unsigned *bits, const float *grid, int idx)
+{
+    return bits ? ((bits[idx >> 5] >> (idx & 31)) & 1u) != 0u : __ldg(grid + idx) > 0.0f;
+}
+
+// One end of a ray's widening: the first sample in a macro cell with a
+// nonzero grid value met walking the samples from k_from towards k_to
+// (exclusive; either direction), or -1.  Every step tests the cell of the
+// current sample (indexed as the grid features index it: floor(p / cell),
+// clamped) and jumps to the first sample past that cell's faces along the
+// walk, so each cell the samples fall in is tested once (a sample within
+// FP32 rounding of a face may count on either side).  Both ends share this
+// code, so the two lanes of a ray do not diverge.
+__device__ __forceinline__ int walk_to_nonzero(const RayRec &r, float step, const float *grid,
+                                               const unsigned *bits, int cell, int gx, int gy,
+                                               int gz, int k_from, int k_to)
+{
+    const int dir = k_to >= k_from ? 1 : -1;
+    const float sg = (float)dir;
+    const float inv_cell = 1.0f / (float)cell, c = (float)cell, inv_step = 1.0f / step;
+    // per-axis reciprocals of the walking direction (+-inf for a zero component)
+    const float ix = sg / r.dx, iy = sg / r.dy, iz = sg / r.dz;
+    for (int k = k_from; k != k_to;) {
+        const float s = (float)k * step;
+        const float x = fmaf(s, r.dx, r.ex), y = fmaf(s, r.dy, r.ey), z = fmaf(s, r.dz, r.ez);
+        const int cx = min(max((int)floorf(x * inv_cell), 0), gx - 1);
+        const int cy = min(max((int)floorf(y * inv_cell), 0), gy - 1);
+        const int cz = min(max((int)floorf(z * inv_cell), 0), gz - 1);
+        if (cell_on(bits, grid, (cz * gy + cy) * gx + cx)) return k;
+        // faces of the cell along the walk; an edge cell reaches to infinity
+        // on the side it was clamped from
+        const float inf = __int_as_float(0x7f800000);
+        const float fx = ix > 0.0f ? (cx == gx - 1 ? inf : (float)(cx + 1) * c) : (cx == 0 ? -inf : (float)cx * c);
+        const float fy = iy > 0.0f ? (cy == gy - 1 ? inf : (float)(cy + 1) * c) : (cy == 0 ? -inf : (float)cy * c);
+        const float fz = iz > 0.0f ? (cz == gz - 1 ? inf : (float)(cz + 1) * c) : (cz == 0 ? -inf : (float)cz * c);
+        const float e = fminf((fx - x) * ix, fminf((fy - y) * iy, (fz - z) * iz));
+        const int j = e > 0.0f ? max(1, (int)ceilf(fminf(e * inv_step, 1.0e9f))) : 1;
+        // the walk never steps over k_to
+        k = dir > 0 ? min(k + j, k_to) : max(k - j, k_to);
+    }
+    return -1;
+}
+
 struct KPropose {
     WsCounters *ctr;
     RayRec *rays;
@@ -706,6 +751,7 @@ struct KPropose {
     float step, nx, ny, nz;
     float threshold;
     int margin;
+    int widen;
     int *stats;
 };
 
@@ -714,6 +760,11 @@ struct KPropose {
 // an SM; with 4 warps per block the weights limited it to 8 warps.
 constexpr int kPropWarps = 8;
 constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + kPropWarps * 16 * LD_IN;
+// The widening walk tests macro cells in a per-block bitmask of the grid
+// when it has at most this many words (32^3 cells; with the 106 KB above two
+// blocks still fit an SM), else it reads the grid (L2: the L1 left beside
+// this much shared memory is small).
+constexpr int kPropBitWords = 1024;
 
 // Persistent warps take 16 rays of the frame's ray list at a time: inputs
 // (2 lanes per ray) into the warp's shared tile, the MLP forward pass, then
@@ -725,9 +776,19 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
     __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
     __half *xs_all = sT4 + 8 * LD_W;
     load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
+    const long long cells = (long long)p.gx * p.gy * p.gz;
+    unsigned *s_bits = nullptr;
+    if (p.widen && cells <= 32LL * kPropBitWords) {
+        s_bits = reinterpret_cast<unsigned *>(xs_all + kPropWarps * 16 * LD_IN);
+        for (long long b0 = 32LL * warp; b0 < cells; b0 += 32LL * kPropWarps) {
+            const bool on = b0 + lane < cells && __ldg(p.grid + b0 + lane) > 0.0f;
+            const unsigned word = __ballot_sync(0xffffffffu, on);
+            if (lane == 0) s_bits[b0 >> 5] = word;
+        }
+    }
+    __syncthreads();
     __half *xs = xs_all + warp * 16 * LD_IN;
     const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
     int seen = 0, restricted = 0;
@@ -750,19 +811,68 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
         mlp_forward_warp(xs, 0, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr, nullptr, 0);
         const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1);
         const float u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
+        // the network's range of rays g and g + 8 (lanes t == 0), unclipped
+        int nkb[2] = {0, 0}, nke[2] = {0, 0}, sure[2] = {0, 0};
+        if (t == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const unsigned r = base + g + 8 * h;
+                if (r >= n) continue;
+                if (sigmoidf(h ? u2b : u2a) >= p.threshold) {
+                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
+                    const int ns = p.rays[r].nsteps;
+                    nkb[h] = (int)floorf(te * (float)ns) - p.margin;
+                    nke[h] = (int)ceilf(tx * (float)ns) + p.margin;
+                    sure[h] = 1;
+                }
+            }
+        }
+        // Widening: lane 4g + 2h walks ray g + 8h forward over the samples
+        // before its range for the first one in a macro cell with a nonzero
+        // grid value, lane 4g + 2h + 1 backward over those after it for the
+        // last one (the whole ray when the range is empty).
+        int found = -1;
+        {
+            const int src = lane & ~3, hh = t >> 1;
+            const int kb0 = __shfl_sync(0xffffffffu, nkb[0], src), kb1 = __shfl_sync(0xffffffffu, nkb[1], src);
+            const int ke0 = __shfl_sync(0xffffffffu, nke[0], src), ke1 = __shfl_sync(0xffffffffu, nke[1], src);
+            const int s0 = __shfl_sync(0xffffffffu, sure[0], src), s1 = __shfl_sync(0xffffffffu, sure[1], src);
+            const unsigned r = base + g + 8 * hh;
+            if (p.widen && r < n && (hh ? s1 : s0)) {
+                const RayRec rec = p.rays[r];
+                const int kb = hh ? kb1 : kb0, ke = hh ? ke1 : ke0;
+                const bool open = ke > kb;
+                // forward from the ray's start to the range, or backward from
+                // its end to the range (the whole ray when the range is empty)
+                const int from = (t & 1) == 0 ? 0 : rec.nsteps - 1;
+                const int to = (t & 1) == 0 ? (open ? min(max(kb, 0), rec.nsteps) : rec.nsteps)
+                                            : (open ? min(max(ke, 0), rec.nsteps) : 0) - 1;
+                found = walk_to_nonzero(rec, p.step, p.grid, s_bits, p.cell, p.gx, p.gy, p.gz, from, to);
+            }
+        }
+        const int first0 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 0);
+        const int last0 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 1);
+        const int first1 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 2);
+        const int last1 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 3);
         if (t == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const unsigned r = base + g + 8 * h;
                 if (r >= n) continue;
                 ++seen;
-                const float conf = sigmoidf(h ? u2b : u2a);
                 const int ns = p.rays[r].nsteps;
                 int kb = 0, ke = ns;
-                if (conf >= p.threshold) {
-                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
-                    kb = (int)floorf(te * (float)ns) - p.margin;
-                    ke = (int)ceilf(tx * (float)ns) + p.margin;
+                if (sure[h]) {
+                    kb = nkb[h];
+                    ke = nke[h];
+                    const int first = h ? first1 : first0, last = h ? last1 : last0;
+                    if (ke > kb) {          // the hull of the range and the nonzero samples
+                        if (first >= 0) kb = min(kb, first);
+                        if (last >= 0) ke = max(ke, last + 1);
+                    } else if (first >= 0) {
+                        kb = first;
+                        ke = max(last, first) + 1;
+                    }
                     kb = min(max(kb, 0), ns);
                     ke = min(max(ke, kb), ns);
                     p.rays[r].kbeg = kb;
@@ -797,14 +907,17 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     p.gx = (fp.nx + pr->cell - 1) / pr->cell;
     p.gy = (fp.ny + pr->cell - 1) / pr->cell;
     p.gz = (fp.nz + pr->cell - 1) / pr->cell;
+    if ((long long)p.gx * p.gy * p.gz > 0x7fffffffLL)
+        return fail(ISAAC_ENOTSUP, "the proposal's grid has more than 2^31 - 1 macro cells");
     p.step = fp.step;
     p.nx = (float)fp.nx;
     p.ny = (float)fp.ny;
     p.nz = (float)fp.nz;
     p.threshold = pr->threshold;
     p.margin = pr->margin;
+    p.widen = pr->widen != 0;
     p.stats = pr->stats;
-    const int smem = kPropSmemHalves * 2;
+    const int smem = kPropSmemHalves * 2 + kPropBitWords * 4;
     cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int sms = sm_count();
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);

@@ -89,7 +89,7 @@ static __global__ void __launch_bounds__(128) k_batch_setup(const __grid_constan
 // marched by march_ray with its own request's parameters (LUTs read from
 // global memory, since a block may hold rays of several requests).
 template <class Shader, int RL>
-static __global__ void __launch_bounds__(128, 8) k_batch_march(const __grid_constant__ KBatch b)
+static __global__ void __launch_bounds__(kMarchThreads, kMarchBlocksPerSM) k_batch_march(const __grid_constant__ KBatch b)
 {
     constexpr unsigned RAYS = 32 / RL;
     const int lane = threadIdx.x & 31;
@@ -109,7 +109,7 @@ using BatchLaunch = void (*)(const KBatch &, dim3, cudaStream_t);
 template <class Shader>
 static void launch_batch_march(const KBatch &b, dim3 grid, cudaStream_t st)
 {
-    k_batch_march<Shader, 4><<<grid, 128, 0, st>>>(b);
+    k_batch_march<Shader, 4><<<grid, kMarchThreads, 0, st>>>(b);
 }
 
 struct BatchEntry {

@@ -101,7 +101,8 @@ class Mlp(C.Structure):
 
 class Proposal(C.Structure):
     _fields_ = [("model", C.POINTER(Mlp)), ("grid", C.c_void_p), ("cell", C.c_int32),
-                ("threshold", C.c_float), ("margin", C.c_int32), ("stats", C.c_void_p)]
+                ("threshold", C.c_float), ("margin", C.c_int32), ("stats", C.c_void_p),
+                ("widen", C.c_int32)]
 
 
 class ServerConfig(C.Structure):
@@ -902,9 +903,9 @@ class MLPModel:
                                           loss_sum.data_ptr() if loss_sum is not None else None,
                                           _stream_handle(stream)))
 
-    def proposal(self, grid, cell, threshold=0.9, margin=2, stats=None):
+    def proposal(self, grid, cell, threshold=0.9, margin=2, stats=None, widen=True):
         p = Proposal(C.pointer(self.desc), grid.data_ptr(), int(cell), float(threshold), int(margin),
-                     stats.data_ptr() if stats is not None else None)
+                     stats.data_ptr() if stats is not None else None, 1 if widen else 0)
         p._keep = (grid, stats)
         return p
 

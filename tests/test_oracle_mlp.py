@@ -183,3 +183,63 @@ def test_propose_agrees_with_coverage():
         c = mlp.coverage(np.full(64, te), np.full(64, tx), jf, jl, ns, 3)
         assert use.all()
         np.testing.assert_array_equal((kb <= jf) & (ke >= jl + 1), c == 1.0)
+
+
+def test_nonzero_samples_along_an_axis():
+    """A ray along +x at y = z = 4 in a 4^3 grid of 8-cell macro cells whose
+    cells x = 1 and x = 3 (of row y = z = 0) are nonzero: samples k with
+    position 0.25 + k/2 in [8, 16) or [24, 32) are kept."""
+    grid = np.zeros((4, 4, 4))
+    grid[0, 0, 1] = 0.2
+    grid[0, 0, 3] = 0.7
+    keep = mlp.nonzero_samples([[0.25, 4.0, 4.0]], [[1.0, 0.0, 0.0]], [60], 0.5, grid, 8)[0]
+    x = 0.25 + 0.5 * np.arange(60)
+    np.testing.assert_array_equal(keep, np.flatnonzero(((x >= 8) & (x < 16)) | ((x >= 24) & (x < 32))))
+    # a ray that stays in zero cells keeps nothing; positions beyond the grid clamp to its edge
+    assert len(mlp.nonzero_samples([[0.25, 20.0, 4.0]], [[1.0, 0.0, 0.0]], [60], 0.5, grid, 8)[0]) == 0
+    keep = mlp.nonzero_samples([[30.0, 4.0, 4.0]], [[1.0, 0.0, 0.0]], [10], 0.5, grid, 8)[0]
+    np.testing.assert_array_equal(keep, np.arange(10))
+
+
+def test_propose_widening_hand_computed():
+    """The range becomes the hull of the network's (non-empty) range and the
+    samples in nonzero macro cells; an empty network range becomes those
+    samples' hull; unsure rays keep the whole ray."""
+    grid = np.zeros((4, 4, 4))
+    grid[0, 0, 1] = 0.2            # x in [8, 16): samples 16..31 of the rays below
+    e = np.array([[0.25, 4.0, 4.0]] * 3)
+    d = np.array([[1.0, 0.0, 0.0]] * 3)
+    ns = np.array([60, 60, 60])
+    w = dict(e=e, d=d, step=0.5, grid=grid, cell=8)
+    X = np.zeros((3, mlp.N_IN))
+    kb, ke, use = mlp.propose(_const_params((0.0, 0.0, 5.0)), X, ns, margin=2, widen=w)
+    assert (kb[0], ke[0]) == (16, 32)                  # the network's [28, 32) widened
+    kb, ke, _ = mlp.propose(_const_params((-2.0, -1.0, 5.0)), X, ns, margin=0, widen=w)
+    assert (kb[0], ke[0]) == (7, 32)                   # network [7, 17) + [16, 32)
+    kb, ke, _ = mlp.propose(_const_params((2.0, -2.0, 5.0)), X, ns, margin=2, widen=w)
+    assert (kb[0], ke[0]) == (16, 32)                  # empty network range
+    kb, ke, _ = mlp.propose(_const_params((0.0, 0.0, 0.0)), X, ns, margin=2, widen=w)
+    assert (kb[0], ke[0]) == (0, 60)                   # unsure
+    kb, ke, _ = mlp.propose(_const_params((0.0, 0.0, 5.0)), X, ns, margin=2)
+    assert (kb[0], ke[0]) == (28, 32)                  # no widening
+
+
+def test_propose_widening_keeps_every_nonzero_sample():
+    rng = np.random.default_rng(4)
+    grid = (rng.uniform(size=(4, 4, 4)) < 0.15) * 0.5
+    for _ in range(5):
+        N = 40
+        e = rng.uniform(0, 32, (N, 3))
+        d = rng.normal(size=(N, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        ns = rng.integers(1, 120, N)
+        w = dict(e=e, d=d, step=0.5, grid=grid, cell=8)
+        b4 = (rng.normal(0, 2), rng.normal(0, 2), 5.0)
+        kb0, ke0, _ = mlp.propose(_const_params(b4), np.zeros((N, mlp.N_IN)), ns, margin=1)
+        kb, ke, use = mlp.propose(_const_params(b4), np.zeros((N, mlp.N_IN)), ns, margin=1, widen=w)
+        keep = mlp.nonzero_samples(e, d, ns, 0.5, grid, 8)
+        assert use.all()
+        for r in range(N):
+            assert np.all((keep[r] >= kb[r]) & (keep[r] < ke[r]))
+            if ke0[r] > kb0[r]:
+                assert kb[r] <= kb0[r] and ke0[r] <= ke[r]

@@ -150,7 +150,7 @@ def test_proposal_plumbing_closed_forms(cuda_ok, packed):
                                ((30, -30, 30), 0, "empty")):
         stats = torch.zeros(2, dtype=torch.int32, device="cuda")
         model = _const_model(b4)
-        prop = model.proposal(grid, 8, threshold=0.9, margin=margin, stats=stats)
+        prop = model.proposal(grid, 8, threshold=0.9, margin=margin, stats=stats, widen=False)
         got = target.render_learned(prop, want_f32=True, want_nsamp=True)
         torch.cuda.synchronize()
         seen, restricted = stats.tolist()
@@ -248,13 +248,15 @@ def test_trained_proposal_gain_on_bubble(cuda_ok):
     assert saved > 0.3
 
 
-@pytest.mark.parametrize("margin", [0, 3])
-def test_proposal_windows_match_oracle_rule(cuda_ok, margin):
+@pytest.mark.parametrize("margin,widen", [(0, False), (3, False), (2, True)])
+def test_proposal_windows_match_oracle_rule(cuda_ok, margin, widen):
     """The windows the proposal kernel writes into the ray list equal the
     oracle's proposal rule applied to the network outputs of the same rays
-    (forward pass on the same FP16 inputs); rays whose te*ns or tx*ns lies
-    within 1e-4 of an integer, or whose confidence lies within 1e-5 of the
-    threshold, are decided at a tie and only counted."""
+    (forward pass on the same FP16 inputs; with widening, the same grid and
+    ray records); rays whose te*ns or tx*ns lies within 1e-4 of an integer, or
+    whose confidence lies within 1e-5 of the threshold, are decided at a tie
+    and only counted; with widening an end may also differ by one sample that
+    lies within 1e-3 voxel of a macro-cell face (FP32 against FP64 position)."""
     import torch
     sc = synth.scene_bubble(64, frame=4, seed=6, width=160, height=120, dist_factor=1.2)
     ds = isaac.DeviceScene(sc)
@@ -264,8 +266,10 @@ def test_proposal_windows_match_oracle_rule(cuda_ok, margin):
     params = synth.mlp_params(21, bias_scale=0.5)
     params["b4"] = np.asarray((params["b4"][0], params["b4"][1], 2.2), np.float32)
     model = isaac.MLPModel(isaac.pack_mlp_params(params), train=False)
-    U = model.forward(isaac.mlp_features(rays[:k], k, sc.n, sc.step, grid, 8)).cpu().numpy()
-    l_rays, l_cnt, *_ = ds.trace(proposal=model.proposal(grid, 8, threshold=0.9, margin=margin))
+    X = isaac.mlp_features(rays[:k], k, sc.n, sc.step, grid, 8)
+    U = model.forward(X).cpu().numpy()
+    l_rays, l_cnt, *_ = ds.trace(proposal=model.proposal(grid, 8, threshold=0.9, margin=margin,
+                                                         widen=widen))
     torch.cuda.synchronize()
     assert int(l_cnt.item()) == k
     base = rays[:k].cpu().numpy()
@@ -274,14 +278,33 @@ def test_proposal_windows_match_oracle_rule(cuda_ok, margin):
     order = np.argsort(base[:, 7])
     base, U = base[order], U[order]
     ns = base[:, 3]
-    kb, ke, use = omlp.propose_rule(U, ns, margin, 0.9)
+    fl = base.view(np.float32)
+    e, d = fl[:, 0:3].astype(np.float64), fl[:, 4:7].astype(np.float64)
+    g_np = grid.cpu().numpy()
+    w = dict(e=e, d=d, step=sc.step, grid=g_np, cell=8) if widen else None
+    kb, ke, use = omlp.propose_rule(U, ns, margin, 0.9, w)
     te, tx, conf = (omlp.sigmoid(U[:, i].astype(np.float64)) for i in range(3))
 
     def near_int(x):
         return np.abs(x - np.round(x)) < 1e-4
 
+    def near_face(r, k):
+        p = e[r] + k * sc.step * d[r]
+        f = p / 8.0 - np.floor(p / 8.0)
+        return bool(np.any(np.minimum(f, 1.0 - f) * 8.0 < 1e-3))
+
     tie = (np.abs(conf - 0.9) < 1e-5) | (use & (near_int(te * ns) | near_int(tx * ns)))
     assert 0.2 < use.mean() < 0.95, use.mean()
     assert tie.mean() < 0.01
     ok = (got[:, 8] == kb) & (got[:, 3] == ke)
+    if widen:
+        for r in np.flatnonzero(~ok & ~tie):
+            db, de = got[r, 8] - kb[r], got[r, 3] - ke[r]
+            assert abs(db) <= 1 and abs(de) <= 1, (r, db, de)
+            # the sample one side keeps and the other does not
+            assert db == 0 or near_face(r, min(got[r, 8], kb[r])), (r, db)
+            assert de == 0 or near_face(r, min(got[r, 3], ke[r])), (r, de)
+            ok[r] = True
+        keep = omlp.nonzero_samples(e, d, ns, sc.step, g_np, 8)
+        assert np.mean([len(k) > 0 for k in keep]) > 0.1      # the widening has work to do
     assert np.all(ok | tie), np.flatnonzero(~ok & ~tie)[:10]
