@@ -296,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = [c * bpc + W * H * 4 for c in cells]
     mean_launch_ms = statistics.mean(march_ms)
     achieved = (sum(alg_bytes) / args.steps) / (mean_launch_ms * 1e-3) / 1e9
-    prof = _ncu_traffic(cfg["workload"]) or {}
+    prof, traffic_source = _ncu_traffic(cfg["workload"])
+    prof = prof or {}
     traffic = prof.get("dram_bytes_per_launch")
     l2_peak = _l2_peak(dev)
     lts = prof.get("lts_bytes_per_launch")
@@ -327,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "traffic": traffic,
+                     "traffic_source": traffic_source,
                      "kernel": "k_raycast (march), CUDA events recorded by the library around "
                                "its launch on the render stream",
                      "launch_ms_mean": mean_launch_ms,
@@ -336,7 +338,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline_l2": {"achieved": (lts / (mean_launch_ms * 1e-3) / 1e9) if lts else None,
                         "peak": l2_peak, "unit": "GB/s",
                         "frac": (lts / (mean_launch_ms * 1e-3) / 1e9 / l2_peak) if lts else None,
-                        "bytes": "ncu lts__t_bytes per k_raycast launch (profiles/traffic.json)",
+                        "bytes": "ncu lts__t_bytes per k_raycast launch (" + traffic_source + ")",
+                        "time": "mean march launch of this run (CUDA events)",
                         "peak_kind": "measured here: isaac_probe_read over half the L2, best of 10"},
         "e2e": {"value": all_samp / (e2e_ms * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(luts_host.numel() * 4),
@@ -360,8 +363,9 @@ def run_ours(args, rank, world, local_rank):
 
 def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
     """Packed copies (FP32, BF16, FP16, E4M3) of the same sources: pack time,
-    samples/s over the same cameras, and the 8-bit difference to the FP32
-    zero-copy frame (mean and max LSB over the image's hit pixels)."""
+    samples/s over the same cameras, and the difference to the FP32 zero-copy
+    frame over the image's hit pixels: 8-bit (mean and max LSB, share of
+    pixels over 1 LSB) and before quantisation (max per channel, mean)."""
     import torch
     out = {}
     W, H = ds.scene.width, ds.scene.height
@@ -386,7 +390,12 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
         pack_ms = e0.elapsed_time(e1)
         fb = torch.empty_like(fb_f32)
         prep = [pv.prepare(mv, proj, out=fb) for mv, proj in cams]
-        lsb_sum, lsb_max, npx = 0.0, 0, 0
+        lsb_sum, lsb_max, npx, over1, nhit = 0.0, 0, 0, 0, 0
+        abs_max = torch.zeros(4, dtype=torch.float32, device=fb.device)
+        abs_sum = 0.0
+        ref32 = torch.empty((H, W, 4), dtype=torch.float32, device=fb.device)
+        var32 = torch.empty_like(ref32)
+        tmp8 = torch.empty_like(fb_f32)
         with torch.cuda.stream(stream):
             for j in range(n_cam):
                 pv.launch(prep[j], stream)
@@ -395,6 +404,15 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
                 lsb_sum += float(d[hit].float().sum().item())
                 lsb_max = max(lsb_max, int(d.max().item()))
                 npx += int(hit.sum().item()) * 4
+                over1 += int((d.amax(-1)[hit] > 1).sum().item())
+                nhit += int(hit.sum().item())
+                # before quantisation: the packed frame against the FP32 zero-copy frame
+                mv, proj = cams[j]
+                ds.render(mv, proj, out=tmp8, rgba32=ref32, stream=stream)
+                pv.render(mv, proj, out=tmp8, rgba32=var32, stream=stream)
+                e = (var32 - ref32).abs()
+                abs_max = torch.maximum(abs_max, e.reshape(-1, 4).amax(0))
+                abs_sum += float(e[hit].sum().item())
             for i in range(args.warmup):
                 pv.launch(prep[i % n_cam], stream)
         torch.cuda.synchronize()
@@ -417,6 +435,9 @@ def run_variants(args, ds, cams, prepared_f32, samples, stream, flush, fb_f32):
                     "bytes": int(pv.data.numel()) +
                     (int(pv.scales.numel()) * 4 if pv.scales is not None else 0),
                     "lsb_vs_f32_mean": lsb_sum / max(1, npx), "lsb_vs_f32_max": lsb_max,
+                    "hit_px_over_1lsb_frac": over1 / max(1, nhit),
+                    "abs_vs_f32_max_rgba": [float(v) for v in abs_max.tolist()],
+                    "abs_vs_f32_mean": abs_sum / max(1, npx),
                     "steps": steps}
         del pv, prep
         torch.cuda.empty_cache()
@@ -821,7 +842,10 @@ def run_serving(args, ds, dev):
         span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
         px = sum(sizes[k][0] * sizes[k][1] for k in sch["size"])
         bs = np.array([r["batch_size"] for r in res])
+        sizes_seen, counts = np.unique(bs, return_counts=True)
         return {"offered_rate_per_s": sch["rate"], "requests": n,
+                "requests_by_batch_size": {int(k): int(v) for k, v in zip(sizes_seen, counts)},
+                "device_overlap": overlap_stats(res),
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p90": float(np.percentile(lat, 90)),
                                "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
@@ -842,6 +866,9 @@ def run_serving(args, ds, dev):
         main = run_open(srv, schedule(args.serve_rate, args.serve_seconds))
         stress = run_open(srv, schedule(args.serve_stress_rate, args.serve_stress_seconds)) \
             if args.serve_stress_seconds > 0 else None
+        # offered far beyond what the GPU serves: the queue stays long, batches fill up
+        overload = run_open(srv, schedule(args.serve_overload_rate, args.serve_overload_seconds)) \
+            if args.serve_overload_seconds > 0 else None
         # closed loop: keep every buffer in flight, 1080p only
         burst = []
         held = {}
@@ -870,7 +897,41 @@ def run_serving(args, ds, dev):
     }
     res.update(main)
     res["stress"] = stress
+    res["overload"] = overload
     return res
+
+
+def overlap_stats(results):
+    """From the device-clock intervals of the requests' batches: the time the
+    GPU held at least one request, the share of it with two or more requests
+    in flight (in one batch or in batches overlapping on several streams),
+    and the share with two or more batches overlapping."""
+    batches = {}
+    for r in results:
+        if r.get("t_gpu_start", -1.0) < 0:
+            continue
+        key = (r["stream"], r["t_gpu_start"], r["t_gpu_end"])
+        batches[key] = r["batch_size"]
+    ev = []
+    for (_, a, b), n in batches.items():
+        ev += [(a, n, 1), (b, -n, -1)]
+    ev.sort(key=lambda e: (e[0], e[1]))
+    busy = ge2_req = ge2_batch = 0.0
+    inflight = nb = 0
+    for i, (t, dn, db) in enumerate(ev):
+        if i:
+            dt = t - ev[i - 1][0]
+            if inflight >= 1:
+                busy += dt
+            if inflight >= 2:
+                ge2_req += dt
+            if nb >= 2:
+                ge2_batch += dt
+        inflight += dn
+        nb += db
+    return {"busy_s": busy, "share_two_or_more_requests": ge2_req / busy if busy else 0.0,
+            "share_two_or_more_batches": ge2_batch / busy if busy else 0.0,
+            "batches": len(batches)}
 
 
 def _l2_peak(dev):
@@ -895,14 +956,35 @@ def _l2_peak(dev):
     return 20 * buf.numel() * 4 / (best * 1e-3) / 1e9
 
 
+# Source files that define the plain march kernel: a traffic figure taken by
+# ncu applies to the build it was captured from only.
+MARCH_SOURCES = ("paper_1611_09048_b300/csrc/raycast.cuh", "paper_1611_09048_b300/csrc/raycast_kernels.cu",
+                 "paper_1611_09048_b300/csrc/ff.cuh")
+
+
+def march_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in MARCH_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _ncu_traffic(workload):
-    """Per-launch ncu counters of the march kernel from the committed summary, if any."""
+    """Per-launch ncu counters of the march kernel from the committed capture
+    summary (profiles/traffic.json), when it was taken from the march sources
+    of this build; else None with the reason."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return None, "no ncu capture summary"
     with open(path) as f:
-        d = json.load(f)
-    return d.get(workload)
+        d = json.load(f).get(workload)
+    if d is None:
+        return None, "no ncu capture of this workload"
+    if d.get("kernel_source_sha256") != march_source_sha256():
+        return None, "stale: the march kernel's sources changed since the ncu capture"
+    return d, "ncu capture, profiles/traffic.json: " + d.get("command", "")
 
 
 # ------------------------------------------------------------ CPU oracle arm
@@ -995,6 +1077,9 @@ def main():
     ap.add_argument("--serve-stress-rate", type=float, default=3000.0,
                     help="second open-loop point, above what one request at a time sustains")
     ap.add_argument("--serve-stress-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-overload-rate", type=float, default=20000.0,
+                    help="a third open-loop point far beyond capacity (full batches)")
+    ap.add_argument("--serve-overload-seconds", type=float, default=1.0)
     ap.add_argument("--serve-burst", type=int, default=400)
     ap.add_argument("--preroll", type=float, default=1.0,
                     help="seconds of untimed frames inside the clock-sampling window")

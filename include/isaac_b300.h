@@ -556,6 +556,10 @@ typedef struct {
     double t_submit;            /* seconds since isaac_server_create: queued, */
     double t_launch;            /* its batch enqueued on the GPU, */
     double t_done;              /* its image in `out` (completion seen by the worker) */
+    double t_gpu_start;         /* device clock (CUDA events, seconds since create): its batch's */
+    double t_gpu_end;           /* work began on its stream, and its images were copied; -1 on error */
+    int32_t stream;             /* the server stream that ran its batch (-1: none) */
+    int32_t reserved;
 } isaac_result;
 
 /*

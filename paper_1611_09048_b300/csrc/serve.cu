@@ -237,7 +237,9 @@ struct isaac_server {
     char *arena_dev = nullptr;
     Arena arena;
     std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> events;
+    std::vector<cudaEvent_t> events;        // a batch's end (after its image copies), per stream
+    std::vector<cudaEvent_t> events_start;  // a batch's start (before its header upload), per stream
+    cudaEvent_t ev_ref = nullptr;           // the device clock's origin, recorded at creation
     std::vector<char *> staging;  // pinned batch headers, one per stream
     size_t staging_bytes = 0;
     std::vector<Batch> slots;     // the batch in flight on each stream
@@ -251,16 +253,32 @@ struct isaac_server {
 };
 
 static void finish(isaac_server *s, const Request &r, int status, int batch_size, double t_launch,
-                   double t_done)
+                   double t_done, int stream = -1, double gpu_start = -1.0, double gpu_end = -1.0)
 {
     isaac_result res;
+    memset(&res, 0, sizeof res);
     res.tag = r.rq.tag;
     res.status = status;
     res.batch_size = batch_size;
     res.t_submit = r.t_submit - s->t0;
     res.t_launch = t_launch - s->t0;
     res.t_done = t_done - s->t0;
+    res.t_gpu_start = gpu_start;
+    res.t_gpu_end = gpu_end;
+    res.stream = stream;
     s->results.push_back(res);
+}
+
+// Device-clock time of a completed event, in seconds since the server's
+// reference event (-1 if it cannot be read).
+static double gpu_time(const isaac_server *s, cudaEvent_t ev)
+{
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, s->ev_ref, ev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    return 1e-3 * (double)ms;
 }
 
 // Lay out, upload and launch one batch on stream `si` (worker thread, lock held).
@@ -328,6 +346,7 @@ static int launch_batch(isaac_server *s, Batch &b, int si)
     kb.nreq = nreq;
     kb.ctr = reinterpret_cast<WsCounters *>(blk);
     kb.rays = reinterpret_cast<RayRec *>(blk + o_rays);
+    cudaEventRecord(s->events_start[si], st);
     cudaMemcpyAsync(blk + o_tiles, stg + o_tiles, o_fb - o_tiles, cudaMemcpyHostToDevice, st);
     int maxpix = 1;
     for (const Request &r : b.reqs) maxpix = std::max(maxpix, r.rq.camera.width * r.rq.camera.height);
@@ -367,8 +386,11 @@ static void worker_loop(isaac_server *s)
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) cudaGetLastError();
             const double t = now_s();
+            const double g0 = q == cudaSuccess ? gpu_time(s, s->events_start[si]) : -1.0;
+            const double g1 = q == cudaSuccess ? gpu_time(s, s->events[si]) : -1.0;
             for (const Request &r : b.reqs)
-                finish(s, r, q == cudaSuccess ? ISAAC_OK : ISAAC_ECUDA, (int)b.reqs.size(), b.t_launch, t);
+                finish(s, r, q == cudaSuccess ? ISAAC_OK : ISAAC_ECUDA, (int)b.reqs.size(), b.t_launch, t,
+                       (int)si, g0, g1);
             s->arena.release(b.off, b.bytes);
             b = Batch();
             retired = true;
@@ -520,14 +542,21 @@ extern "C" int isaac_server_create(const isaac_source *sources, const isaac_chai
     s->slots.resize(cfg->n_streams);
     for (int i = 0; i < cfg->n_streams; ++i) {
         cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev = nullptr, ev0 = nullptr;
         char *stg = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaEventCreate(&ev);      // timed: the results carry device-clock intervals
+        cudaEventCreate(&ev0);
         cudaHostAlloc(reinterpret_cast<void **>(&stg), s->staging_bytes, cudaHostAllocDefault);
         s->streams.push_back(st);
         s->events.push_back(ev);
+        s->events_start.push_back(ev0);
         s->staging.push_back(stg);
+    }
+    cudaEventCreate(&s->ev_ref);
+    if (s->ev_ref && !s->streams.empty() && s->streams[0]) {
+        cudaEventRecord(s->ev_ref, s->streams[0]);
+        cudaEventSynchronize(s->ev_ref);
     }
     rc = check_cuda("isaac_server_create");
     if (rc) {
@@ -625,6 +654,9 @@ extern "C" int isaac_server_destroy(isaac_server *s)
         if (st) cudaStreamDestroy(st);
     for (cudaEvent_t ev : s->events)
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : s->events_start)
+        if (ev) cudaEventDestroy(ev);
+    if (s->ev_ref) cudaEventDestroy(s->ev_ref);
     for (char *p : s->staging)
         if (p) cudaFreeHost(p);
     if (s->arena_dev) cudaFree(s->arena_dev);

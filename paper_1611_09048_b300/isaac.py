@@ -116,7 +116,9 @@ class ServerRequest(C.Structure):
 
 class ServerResult(C.Structure):
     _fields_ = [("tag", C.c_int64), ("status", C.c_int32), ("batch_size", C.c_int32),
-                ("t_submit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double)]
+                ("t_submit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double),
+                ("t_gpu_start", C.c_double), ("t_gpu_end", C.c_double), ("stream", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 def pack_mlp_params(named) -> np.ndarray:
@@ -730,13 +732,15 @@ class PackedVolume:
         return out, f32, ns
 
     def render(self, mv=None, proj=None, out=None, stream=None, mask=None, want_f32=False,
-               want_nsamp=False, lanes=None):
+               want_nsamp=False, lanes=None, rgba32=None):
         import torch
         W, H = self.ds.scene.width, self.ds.scene.height
         dev = self.ds.device
         if out is None:
             out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
-        f32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev) if want_f32 else None
+        f32 = rgba32
+        if f32 is None and want_f32:
+            f32 = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
         ns = torch.empty((H, W), dtype=torch.int32, device=dev) if want_nsamp else None
         self.launch(self.prepare(mv, proj, out, f32, ns, mask, lanes), stream)
         return out, f32, ns
@@ -806,7 +810,9 @@ class Server:
 
     def poll(self, max_results=256, wait=0.0):
         """Finished requests as dicts (tag, status, batch_size, t_submit,
-        t_launch, t_done; times in seconds since the server started)."""
+        t_launch, t_done: host clock; t_gpu_start, t_gpu_end: device clock of
+        the request's batch; stream; times in seconds since the server
+        started)."""
         buf = (ServerResult * max_results)()
         n = load().isaac_server_poll(self.handle, buf, max_results, float(wait))
         if n < 0:
@@ -816,7 +822,9 @@ class Server:
             r = buf[i]
             self._live.pop(r.tag, None)
             out.append({"tag": r.tag, "status": r.status, "batch_size": r.batch_size,
-                        "t_submit": r.t_submit, "t_launch": r.t_launch, "t_done": r.t_done})
+                        "t_submit": r.t_submit, "t_launch": r.t_launch, "t_done": r.t_done,
+                        "t_gpu_start": r.t_gpu_start, "t_gpu_end": r.t_gpu_end,
+                        "stream": r.stream})
         return out
 
     def outstanding(self):

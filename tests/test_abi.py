@@ -201,7 +201,7 @@ def test_rejects_unknown_opts_flags():
 def test_server_struct_sizes():
     assert C.sizeof(isaac.ServerConfig) == 8 + 4 + 4
     assert C.sizeof(isaac.ServerRequest) == (256 + 8) + 8 + 8 + 8 + 8
-    assert C.sizeof(isaac.ServerResult) == 8 + 4 + 4 + 3 * 8
+    assert C.sizeof(isaac.ServerResult) == 8 + 4 + 4 + 5 * 8 + 4 + 4
 
 
 def _server_create(a, cfg, vol=None):

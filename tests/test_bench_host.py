@@ -68,3 +68,20 @@ def test_reduce_over_ranks_gloo_world2():
         assert p.exitcode == 0
     for rank, mx, sm in got:
         assert mx == [2.0, 10.0, 0.5] and sm == [300.0]
+
+
+def test_overlap_stats_sweep():
+    """Device-interval bookkeeping of the serving section: a batch of one on
+    stream 0 over [0, 1] s and a batch of two on stream 1 over [0.5, 2] s:
+    busy 2 s, two or more requests in flight over [0.5, 2] (3/4), two
+    batches at once over [0.5, 1] (1/4); failed requests (-1) are ignored."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = [{"stream": 0, "t_gpu_start": 0.0, "t_gpu_end": 1.0, "batch_size": 1},
+         {"stream": 1, "t_gpu_start": 0.5, "t_gpu_end": 2.0, "batch_size": 2},
+         {"stream": 1, "t_gpu_start": 0.5, "t_gpu_end": 2.0, "batch_size": 2},
+         {"stream": -1, "t_gpu_start": -1.0, "t_gpu_end": -1.0, "batch_size": 1}]
+    s = bench.overlap_stats(r)
+    assert s["batches"] == 2 and abs(s["busy_s"] - 2.0) < 1e-12
+    assert abs(s["share_two_or_more_requests"] - 0.75) < 1e-12
+    assert abs(s["share_two_or_more_batches"] - 0.25) < 1e-12
