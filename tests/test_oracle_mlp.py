@@ -243,3 +243,30 @@ def test_propose_widening_keeps_every_nonzero_sample():
             assert np.all((keep[r] >= kb[r]) & (keep[r] < ke[r]))
             if ke0[r] > kb0[r]:
                 assert kb[r] <= kb0[r] and ke0[r] <= ke[r]
+
+
+def test_huber_closed_form():
+    """huber(r) = r^2 / (2 delta) inside |r| < delta, |r| - delta/2 outside:
+    continuous with its slope at |r| = delta."""
+    d = 0.02
+    r = np.array([0.0, 0.01, -0.01, 0.05, -0.3125, 0.02])
+    np.testing.assert_allclose(mlp.huber(r, d), [0.0, 0.0025, 0.0025, 0.04, 0.3025, 0.01], rtol=1e-12)
+    np.testing.assert_allclose(mlp.dhuber(r, d), [0.0, 0.5, -0.5, 1.0, -1.0, 1.0], rtol=1e-12)
+
+
+def test_loss_closed_form():
+    """A constant network (te = tx = conf = 1/2) on two rays of 16 samples:
+    the span [3, 11] gives huber(1/2 - 3/16) + huber(1/2 - 12/16) and, as the
+    range [8 - 2, 8 + 2) does not cover it, BCE(1/2, 0) = ln 2; the empty ray
+    gives huber(1/2 - 1) + huber(1/2 - 0) and BCE(1/2, 1) = ln 2.  The batch
+    loss is the mean with the confidence term weighted 0.1."""
+    p = _const_params((0.0, 0.0, 0.0))
+    loss, g = mlp.loss_and_grads(p, np.zeros((2, mlp.N_IN)), [3, -1], [11, -1], [16, 16], margin=2)
+    ray0 = (0.3125 - 0.01) + (0.25 - 0.01) + 0.1 * math.log(2.0)
+    ray1 = (0.5 - 0.01) + (0.5 - 0.01) + 0.1 * math.log(2.0)
+    assert loss == pytest.approx((ray0 + ray1) / 2, rel=1e-12)
+    # output-bias gradient of the first ray alone: dhuber(te - ye) sigma'(0) =
+    # +1/4, dhuber(tx - yx) sigma'(0) = -1/4, 0.1 (conf - c) = 0.05
+    _, g = mlp.loss_and_grads(p, np.zeros((1, mlp.N_IN)), [3], [11], [16], margin=2)
+    np.testing.assert_allclose(g["b4"], [0.25, -0.25, 0.05], atol=1e-15)
+    assert np.all(g["W1"] == 0.0)        # zero inputs and zero hidden units
