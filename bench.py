@@ -249,32 +249,38 @@ def run_ours(args, rank, world, local_rank):
     rendered = [torch.cuda.Event() for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
     uploaded = [torch.cuda.Event() for _ in range(2)]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    upload_stream.wait_event(e0)
-    for i in range(args.steps):
-        b = i % 2
-        if i >= 2:
-            upload_stream.wait_event(rendered[b])
-        with torch.cuda.stream(upload_stream):
-            lut_bufs[b].copy_(luts_host, non_blocking=True)
-        uploaded[b].record(upload_stream)
-        stream.wait_event(uploaded[b])
-        if i >= 2:
+    def pipeline(steps, first):
+        """`steps` frames through the pipeline, cameras from `first` on;
+        returns the device time from its start to the last image read back."""
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        upload_stream.wait_event(e0)
+        for i in range(steps):
+            b = i % 2
+            if i >= 2:
+                upload_stream.wait_event(rendered[b])
+            with torch.cuda.stream(upload_stream):
+                lut_bufs[b].copy_(luts_host, non_blocking=True)
+            uploaded[b].record(upload_stream)
+            stream.wait_event(uploaded[b])
+            if i >= 2:
+                stream.wait_event(copied[b])
+            with torch.cuda.stream(stream):
+                ds.launch(preps[b][(first + i) % len(cams)], stream)
+            rendered[b].record(stream)
+            copy_stream.wait_event(rendered[b])
+            with torch.cuda.stream(copy_stream):
+                imgs[b].copy_(fbs[b], non_blocking=True)
+            copied[b].record(copy_stream)
+        for b in range(min(2, steps)):
             stream.wait_event(copied[b])
-        with torch.cuda.stream(stream):
-            ds.launch(preps[b][(args.warmup + i) % len(cams)], stream)
-        rendered[b].record(stream)
-        copy_stream.wait_event(rendered[b])
-        with torch.cuda.stream(copy_stream):
-            imgs[b].copy_(fbs[b], non_blocking=True)
-        copied[b].record(copy_stream)
-    for b in range(min(2, args.steps)):
-        stream.wait_event(copied[b])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    pipeline(args.warmup, 0)                 # untimed: the streams' and buffers' first use
+    e2e_ms = pipeline(args.steps, args.warmup)
 
     variants = {} if args.no_variants else \
         run_variants(args, ds, cams, prepared, samples, stream, flush, fb)
@@ -638,8 +644,8 @@ def run_learned(args, dev, stream, flush):
     grid_ms, grid16_ms, range_ms = [], [], []
     stats = torch.zeros(2, dtype=torch.int32, device=dev)
     stats_off = torch.zeros(2, dtype=torch.int32, device=dev)
-    # BASELINE c4's protocol: consecutive frames of the moving bubble, one
-    # unseen camera and transfer function each
+    # the test protocol: consecutive frames of the moving bubble (100 by
+    # default), one unseen camera and transfer function each
     for f in range(args.learned_frames):
         field = synth.bubble_field(n, f, 0, noise=noise, device=dev)
         sc = synth.scene_bubble(n, frame=f, seed=77000 + f, width=W, height=H,
