@@ -760,11 +760,9 @@ struct KPropose {
 // an SM; with 4 warps per block the weights limited it to 8 warps.
 constexpr int kPropWarps = 8;
 constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + kPropWarps * 16 * LD_IN;
-// The widening walk tests macro cells in a per-block bitmask of the grid
-// when it has at most this many words (32^3 cells; with the 106 KB above two
-// blocks still fit an SM), else it reads the grid (L2: the L1 left beside
-// this much shared memory is small).
-constexpr int kPropBitWords = 1024;
+// RayRec::reserved of a confident ray whose range k_mlp_widen has yet to widen
+// (its network range is in jf, jl meanwhile).
+constexpr int kWidenPending = 1;
 
 // Persistent warps take 16 rays of the frame's ray list at a time: inputs
 // (2 lanes per ray) into the warp's shared tile, the MLP forward pass, then
@@ -778,16 +776,6 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
     load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    const long long cells = (long long)p.gx * p.gy * p.gz;
-    unsigned *s_bits = nullptr;
-    if (p.widen && cells <= 32LL * kPropBitWords) {
-        s_bits = reinterpret_cast<unsigned *>(xs_all + kPropWarps * 16 * LD_IN);
-        for (long long b0 = 32LL * warp; b0 < cells; b0 += 32LL * kPropWarps) {
-            const bool on = b0 + lane < cells && __ldg(p.grid + b0 + lane) > 0.0f;
-            const unsigned word = __ballot_sync(0xffffffffu, on);
-            if (lane == 0) s_bits[b0 >> 5] = word;
-        }
-    }
     __syncthreads();
     __half *xs = xs_all + warp * 16 * LD_IN;
     const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
@@ -811,49 +799,6 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
         mlp_forward_warp(xs, 0, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr, nullptr, 0);
         const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1);
         const float u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
-        // the network's range of rays g and g + 8 (lanes t == 0), unclipped
-        int nkb[2] = {0, 0}, nke[2] = {0, 0}, sure[2] = {0, 0};
-        if (t == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned r = base + g + 8 * h;
-                if (r >= n) continue;
-                if (sigmoidf(h ? u2b : u2a) >= p.threshold) {
-                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
-                    const int ns = p.rays[r].nsteps;
-                    nkb[h] = (int)floorf(te * (float)ns) - p.margin;
-                    nke[h] = (int)ceilf(tx * (float)ns) + p.margin;
-                    sure[h] = 1;
-                }
-            }
-        }
-        // Widening: lane 4g + 2h walks ray g + 8h forward over the samples
-        // before its range for the first one in a macro cell with a nonzero
-        // grid value, lane 4g + 2h + 1 backward over those after it for the
-        // last one (the whole ray when the range is empty).
-        int found = -1;
-        {
-            const int src = lane & ~3, hh = t >> 1;
-            const int kb0 = __shfl_sync(0xffffffffu, nkb[0], src), kb1 = __shfl_sync(0xffffffffu, nkb[1], src);
-            const int ke0 = __shfl_sync(0xffffffffu, nke[0], src), ke1 = __shfl_sync(0xffffffffu, nke[1], src);
-            const int s0 = __shfl_sync(0xffffffffu, sure[0], src), s1 = __shfl_sync(0xffffffffu, sure[1], src);
-            const unsigned r = base + g + 8 * hh;
-            if (p.widen && r < n && (hh ? s1 : s0)) {
-                const RayRec rec = p.rays[r];
-                const int kb = hh ? kb1 : kb0, ke = hh ? ke1 : ke0;
-                const bool open = ke > kb;
-                // forward from the ray's start to the range, or backward from
-                // its end to the range (the whole ray when the range is empty)
-                const int from = (t & 1) == 0 ? 0 : rec.nsteps - 1;
-                const int to = (t & 1) == 0 ? (open ? min(max(kb, 0), rec.nsteps) : rec.nsteps)
-                                            : (open ? min(max(ke, 0), rec.nsteps) : 0) - 1;
-                found = walk_to_nonzero(rec, p.step, p.grid, s_bits, p.cell, p.gx, p.gy, p.gz, from, to);
-            }
-        }
-        const int first0 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 0);
-        const int last0 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 1);
-        const int first1 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 2);
-        const int last1 = __shfl_sync(0xffffffffu, found, (lane & ~3) + 3);
         if (t == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -862,22 +807,21 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
                 ++seen;
                 const int ns = p.rays[r].nsteps;
                 int kb = 0, ke = ns;
-                if (sure[h]) {
-                    kb = nkb[h];
-                    ke = nke[h];
-                    const int first = h ? first1 : first0, last = h ? last1 : last0;
-                    if (ke > kb) {          // the hull of the range and the nonzero samples
-                        if (first >= 0) kb = min(kb, first);
-                        if (last >= 0) ke = max(ke, last + 1);
-                    } else if (first >= 0) {
-                        kb = first;
-                        ke = max(last, first) + 1;
+                if (sigmoidf(h ? u2b : u2a) >= p.threshold) {
+                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
+                    kb = (int)floorf(te * (float)ns) - p.margin;
+                    ke = (int)ceilf(tx * (float)ns) + p.margin;
+                    ++restricted;
+                    if (p.widen) {   // k_mlp_widen finishes the ray
+                        p.rays[r].jf = kb;
+                        p.rays[r].jl = ke;
+                        p.rays[r].reserved = kWidenPending;
+                        continue;
                     }
                     kb = min(max(kb, 0), ns);
                     ke = min(max(ke, kb), ns);
                     p.rays[r].kbeg = kb;
                     p.rays[r].nsteps = ke;
-                    ++restricted;
                 }
                 if (p.longs && ke - kb > kLongRaySamples) {
                     p.rays[r].jf = kLongRay;
@@ -890,6 +834,48 @@ static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __
     if (p.stats && t == 0 && (seen | restricted)) {
         atomicAdd(p.stats, seen);
         atomicAdd(p.stats + 1, restricted);
+    }
+}
+
+// The widening of the confident rays k_mlp_propose marked (network range in
+// jf/jl, unclipped): one thread per ray walks from the ray's start forward to
+// the range for the first sample in a macro cell with a nonzero grid value,
+// and from its end backward for the last one (the whole ray when the range is
+// empty); the range becomes the hull of both, clipped to the ray.  A separate
+// kernel, so that these dependent walks run at full occupancy rather than in
+// the shared-memory-heavy proposal kernel.
+static __global__ void __launch_bounds__(128) k_mlp_widen(const __grid_constant__ KPropose p)
+{
+    const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
+    for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        RayRec rec = p.rays[r];
+        if (rec.reserved != kWidenPending) continue;
+        int kb = rec.jf, ke = rec.jl;
+        const int ns = rec.nsteps;
+        const bool open = ke > kb;
+        const int first = walk_to_nonzero(rec, p.step, p.grid, nullptr, p.cell, p.gx, p.gy, p.gz, 0,
+                                          open ? min(max(kb, 0), ns) : ns);
+        const int last = walk_to_nonzero(rec, p.step, p.grid, nullptr, p.cell, p.gx, p.gy, p.gz,
+                                         ns - 1, (open ? min(max(ke, 0), ns) : 0) - 1);
+        if (open) {              // the hull of the range and the nonzero samples
+            if (first >= 0) kb = min(kb, first);
+            if (last >= 0) ke = max(ke, last + 1);
+        } else if (first >= 0) {
+            kb = first;
+            ke = max(last, first) + 1;
+        }
+        kb = min(max(kb, 0), ns);
+        ke = min(max(ke, kb), ns);
+        p.rays[r].kbeg = kb;
+        p.rays[r].nsteps = ke;
+        p.rays[r].reserved = 0;
+        p.rays[r].jl = -1;
+        if (p.longs && ke - kb > kLongRaySamples) {
+            p.rays[r].jf = kLongRay;
+            p.longs[atomicAdd(&p.ctr->n_long, 1u)] = r;
+        } else {
+            p.rays[r].jf = -1;
+        }
     }
 }
 
@@ -917,13 +903,17 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     p.margin = pr->margin;
     p.widen = pr->widen != 0;
     p.stats = pr->stats;
-    const int smem = kPropSmemHalves * 2 + kPropBitWords * 4;
+    const int smem = kPropSmemHalves * 2;
     cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int sms = sm_count();
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
     const long long blocks = std::max(1LL, std::min<long long>((rect + 16 * kPropWarps - 1) / (16 * kPropWarps),
                                                               (long long)sms * 2));
     k_mlp_propose<<<(unsigned)blocks, kPropWarps * 32, smem, st>>>(p);
+    if (p.widen) {
+        const long long wb = std::max(1LL, std::min<long long>((rect + 127) / 128, (long long)sms * 16));
+        k_mlp_widen<<<(unsigned)wb, 128, 0, st>>>(p);
+    }
     return check_cuda("interval proposal launch");
 }
 
