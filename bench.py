@@ -1009,9 +1009,20 @@ def cpu_baseline(sc, cams, budget_s):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    # one thread, on the centre rows of the first camera (a bounded sample)
+    H, W = sc.height, sc.width
+    rows = max(1, H // 16)
+    pix = (np.arange(rows)[:, None] + (H - rows) // 2) * W + np.arange(W)[None, :]
+    t1 = time.perf_counter()
+    r1 = oracle.render(sc.with_camera(*cams[0]), pixels=pix.reshape(-1), threads=1)
+    dt1 = time.perf_counter() - t1
+    n1 = int(r1["nsamp"].sum())
     return {"value": total / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
             "sample": f"{frames} full {sc.width}x{sc.height} frame(s) of the same workload "
-                      f"({total} samples, {dt:.1f} s)"}
+                      f"({total} samples, {dt:.1f} s)",
+            "single_thread": {"value": n1 / dt1, "unit": "samples/s",
+                              "sample": f"the centre {rows} rows of camera 0 ({n1} samples, "
+                                        f"{dt1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
