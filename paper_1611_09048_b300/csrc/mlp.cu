@@ -695,49 +695,64 @@ extern "C" int isaac_mlp_train_step(isaac_mlp *m, const uint16_t *X, const isaac
 
 namespace isaac {
 
-// Whether macro cell idx has a nonzero grid value: from the block's bitmask
-// of the grid (shared memory) when there is one, else from the grid.
-__device__ __forceinline__ bool cell_on(const unsigned *bits, const float *grid, int idx)
-{
-    return bits ? ((bits[idx >> 5] >> (idx & 31)) & 1u) != 0u : __ldg(grid + idx) > 0.0f;
-}
-
-// One end of a ray's widening: the first sample in a macro cell with a
-// nonzero grid value met walking the samples from k_from towards k_to
-// (exclusive; either direction), or -1.  Every step tests the cell of the
-// current sample (indexed as the grid features index it: floor(p / cell),
-// clamped) and jumps to the first sample past that cell's faces along the
-// walk, so each cell the samples fall in is tested once (a sample within
-// FP32 rounding of a face may count on either side).  Both ends share this
-// code, so the two lanes of a ray do not diverge.
-__device__ __forceinline__ int walk_to_nonzero(const RayRec &r, float step, const float *grid,
-                                               const unsigned *bits, int cell, int gx, int gy,
-                                               int gz, int k_from, int k_to)
+// One end of a ray's widening: the first sample met walking the samples from
+// k_from towards k_to (exclusive; either direction) that lies in a macro cell
+// with a nonzero grid value, or -1.  A 3D-DDA over the macro cells
+// (Amanatides & Woo 1987) along the walking direction: for each cell the
+// samples inside it are those with j * step in [entry, exit) of the cell
+// (distances from sample k_from), so a nonzero cell is tested once and
+// yields its first sample, if it holds any.  Cells are indexed as the grid
+// features index them (floor(p / cell), clamped); an edge cell reaches to
+// infinity beyond the grid.  A sample within FP32 rounding of a face may
+// count on either side.
+__device__ __forceinline__ int walk_to_nonzero(const RayRec &r, float step, const float *grid, int cell,
+                                               int gx, int gy, int gz, int k_from, int k_to)
 {
     const int dir = k_to >= k_from ? 1 : -1;
-    const float sg = (float)dir;
-    const float inv_cell = 1.0f / (float)cell, c = (float)cell, inv_step = 1.0f / step;
-    // per-axis reciprocals of the walking direction (+-inf for a zero component)
-    const float ix = sg / r.dx, iy = sg / r.dy, iz = sg / r.dz;
-    for (int k = k_from; k != k_to;) {
-        const float s = (float)k * step;
-        const float x = fmaf(s, r.dx, r.ex), y = fmaf(s, r.dy, r.ey), z = fmaf(s, r.dz, r.ez);
-        const int cx = min(max((int)floorf(x * inv_cell), 0), gx - 1);
-        const int cy = min(max((int)floorf(y * inv_cell), 0), gy - 1);
-        const int cz = min(max((int)floorf(z * inv_cell), 0), gz - 1);
-        if (cell_on(bits, grid, (cz * gy + cy) * gx + cx)) return k;
-        // faces of the cell along the walk; an edge cell reaches to infinity
-        // on the side it was clamped from
-        const float inf = __int_as_float(0x7f800000);
-        const float fx = ix > 0.0f ? (cx == gx - 1 ? inf : (float)(cx + 1) * c) : (cx == 0 ? -inf : (float)cx * c);
-        const float fy = iy > 0.0f ? (cy == gy - 1 ? inf : (float)(cy + 1) * c) : (cy == 0 ? -inf : (float)cy * c);
-        const float fz = iz > 0.0f ? (cz == gz - 1 ? inf : (float)(cz + 1) * c) : (cz == 0 ? -inf : (float)cz * c);
-        const float e = fminf((fx - x) * ix, fminf((fy - y) * iy, (fz - z) * iz));
-        const int j = e > 0.0f ? max(1, (int)ceilf(fminf(e * inv_step, 1.0e9f))) : 1;
-        // the walk never steps over k_to
-        k = dir > 0 ? min(k + j, k_to) : max(k - j, k_to);
+    const int J = (k_to - k_from) * dir;          // samples j = 0 .. J-1
+    if (J <= 0) return -1;
+    const float inf = __int_as_float(0x7f800000);
+    const float c = (float)cell, inv_cell = 1.0f / c, inv_step = 1.0f / step;
+    const float s0 = (float)k_from * step;
+    const float px = fmaf(s0, r.dx, r.ex), py = fmaf(s0, r.dy, r.ey), pz = fmaf(s0, r.dz, r.ez);
+    const float vx = dir > 0 ? r.dx : -r.dx, vy = dir > 0 ? r.dy : -r.dy, vz = dir > 0 ? r.dz : -r.dz;
+    int cx = min(max((int)floorf(px * inv_cell), 0), gx - 1);
+    int cy = min(max((int)floorf(py * inv_cell), 0), gy - 1);
+    int cz = min(max((int)floorf(pz * inv_cell), 0), gz - 1);
+    const int sx = vx > 0.0f ? 1 : -1, sy = vy > 0.0f ? 1 : -1, sz = vz > 0.0f ? 1 : -1;
+    // distance to the next face per axis and between faces (inf: never, or
+    // the cell is the grid's last one that way)
+    const auto first_face = [&](float pa, float va, int ca, int sa, int ga) {
+        if (va == 0.0f || (sa > 0 && ca == ga - 1) || (sa < 0 && ca == 0)) return inf;
+        return ((float)(sa > 0 ? ca + 1 : ca) * c - pa) / va;
+    };
+    float tx = first_face(px, vx, cx, sx, gx), ty = first_face(py, vy, cy, sy, gy);
+    float tz = first_face(pz, vz, cz, sz, gz);
+    const float dtx = vx != 0.0f ? c / fabsf(vx) : inf, dty = vy != 0.0f ? c / fabsf(vy) : inf;
+    const float dtz = vz != 0.0f ? c / fabsf(vz) : inf;
+    float s_in = 0.0f;
+    // every pass crosses one face; the bound only guards against rounding
+    for (int it = 0; it < 3 * (gx + gy + gz) + 8; ++it) {
+        const float s_out = fminf(tx, fminf(ty, tz));
+        const int j_out = (int)ceilf(fminf(s_out * inv_step, 1.0e9f));   // first sample past the cell
+        if (__ldg(grid + ((cz * gy + cy) * gx + cx)) > 0.0f) {
+            const int j_in = s_in > 0.0f ? (int)ceilf(s_in * inv_step) : 0;
+            if (j_in < min(j_out, J)) return k_from + dir * j_in;
+        }
+        if (j_out >= J) return -1;
+        if (tx <= ty && tx <= tz) {
+            cx += sx;
+            tx = (sx > 0 ? cx == gx - 1 : cx == 0) ? inf : tx + dtx;
+        } else if (ty <= tz) {
+            cy += sy;
+            ty = (sy > 0 ? cy == gy - 1 : cy == 0) ? inf : ty + dty;
+        } else {
+            cz += sz;
+            tz = (sz > 0 ? cz == gz - 1 : cz == 0) ? inf : tz + dtz;
+        }
+        s_in = s_out;
     }
-    return -1;
+    return k_from;   // not reached; widening to the walk's start is always safe
 }
 
 struct KPropose {
@@ -853,9 +868,9 @@ static __global__ void __launch_bounds__(128) k_mlp_widen(const __grid_constant_
         int kb = rec.jf, ke = rec.jl;
         const int ns = rec.nsteps;
         const bool open = ke > kb;
-        const int first = walk_to_nonzero(rec, p.step, p.grid, nullptr, p.cell, p.gx, p.gy, p.gz, 0,
+        const int first = walk_to_nonzero(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, 0,
                                           open ? min(max(kb, 0), ns) : ns);
-        const int last = walk_to_nonzero(rec, p.step, p.grid, nullptr, p.cell, p.gx, p.gy, p.gz,
+        const int last = walk_to_nonzero(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz,
                                          ns - 1, (open ? min(max(ke, 0), ns) : 0) - 1);
         if (open) {              // the hull of the range and the nonzero samples
             if (first >= 0) kb = min(kb, first);

@@ -78,3 +78,52 @@ def test_unknown_flag_bits_are_rejected(cuda_ok):
     lib = isaac.load()
     assert lib.isaac_render(*args, C.c_void_p(0)) == isaac.EINVAL
     assert "flags" in lib.isaac_last_error().decode()
+
+
+def _with_host_luts(args, lut_index, opts_index, host):
+    """The same call's arguments with the LUT pointer replaced by a host array
+    and ISAAC_LUTS_HOST set in its options."""
+    a = list(args)
+    a[lut_index] = host.ctypes.data
+    a[opts_index]._obj.flags = isaac.LUTS_HOST
+    return a
+
+
+def test_host_luts_in_skip_iso_learned_and_packed_frames(cuda_ok):
+    """Every other frame entry point that reads LUTs gives the device-LUT image
+    bit for bit with host LUTs: empty-space skipping (whose empty flags read
+    the LUTs before the march), iso surfaces, the learned frame (widened
+    proposal) and the packed BF16 frame."""
+    import torch
+    sc = _scene()
+    ds = isaac.DeviceScene(sc)
+    host = np.ascontiguousarray(sc.luts, np.float32).copy()
+    lib = isaac.load()
+    H, W = sc.height, sc.width
+
+    def pair(prep_fn, launch, lut_i, opts_i):
+        outs = []
+        for use_host in (False, True):
+            o8 = torch.zeros((H, W, 4), dtype=torch.uint8, device=ds.device)
+            f32 = torch.zeros((H, W, 4), dtype=torch.float32, device=ds.device)
+            args, keep = prep_fn(o8, f32)
+            if use_host:
+                args = _with_host_luts(args, lut_i, opts_i, host)
+            assert launch(*args, C.c_void_p(0)) == 0, lib.isaac_last_error().decode()
+            torch.cuda.synchronize()
+            outs.append((o8.cpu().numpy(), f32.cpu().numpy()))
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
+        np.testing.assert_array_equal(outs[0][1], outs[1][1])
+        return outs[0]
+
+    ranges = ds.range_grid(8)
+    pair(lambda o8, f32: ds.prepare_skip(ranges, 8, out=o8, rgba32=f32), lib.isaac_render_skip, 3, 8)
+    iso = [0.6, 0.55, 0.5]
+    pair(lambda o8, f32: ds.prepare_iso(iso, out=o8, rgba32=f32), lib.isaac_render_iso, 3, 8)
+    grid = ds.opacity_grid(8)
+    model = isaac.MLPModel(isaac.pack_mlp_params(synth.mlp_params(2, bias_scale=0.3)), train=False)
+    prop = model.proposal(grid, 8, threshold=0.5, margin=2)
+    img = pair(lambda o8, f32: ds.prepare_learned(prop, out=o8, rgba32=f32), lib.isaac_render_learned, 3, 8)
+    assert (img[1][..., 3] > 0).sum() > 300
+    pv = ds.pack("bf16")
+    pair(lambda o8, f32: pv.prepare(out=o8, rgba32=f32), lib.isaac_render_packed, 2, 7)
