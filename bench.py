@@ -638,7 +638,7 @@ def run_learned(args, dev, stream, flush):
     t_train = time.perf_counter() - t1
 
     kinds = ("plain_f32", "skip_f32", "learned_f32", "plain_bf16", "learned_bf16",
-             "learned_bf16_nowiden")
+             "learned_bf16_nowiden", "gridhull_f32", "gridhull_bf16")
     acc = {k: {"ms": [], "march_ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0,
                "px_over1": 0, "hit_px": 0} for k in kinds}
     grid_ms, grid16_ms, range_ms = [], [], []
@@ -658,19 +658,24 @@ def run_learned(args, dev, stream, flush):
                               margin=args.learned_margin, stats=stats)
         prop_off = model.proposal(grid, cell, threshold=args.learned_threshold,
                                   margin=args.learned_margin, stats=stats_off, widen=False)
+        # the grid's part of the learned frame without the network: every ray
+        # keeps the hull of its samples in nonzero macro cells
+        prop_hull = isaac.grid_proposal(grid, cell)
         ranges = ds.range_grid(cell)
         outs = {k: torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for k in kinds}
         nss = {}
 
         def run(kind, count=None):
-            if kind == "learned_f32":
+            if kind in ("learned_f32", "gridhull_f32"):
                 ds.opacity_grid(cell, out=grid, stream=stream)
-            if kind.startswith("learned_bf16"):     # the grid of the copy the frame marches
+            if kind.startswith("learned_bf16") or kind == "gridhull_bf16":   # the copy's grid
                 pv.opacity_grid(cell, out=grid, stream=stream)
             if kind.startswith("skip"):
                 ds.range_grid(cell, out=ranges, stream=stream)
             tgt = ds if kind.endswith("f32") else pv
             kw = dict(out=outs[kind], stream=stream)
+            if kind.startswith("gridhull"):
+                return tgt.render_learned(prop_hull, want_nsamp=count is not None, **kw)
             if kind.startswith("learned"):
                 return tgt.render_learned(prop_off if kind.endswith("nowiden") else prop,
                                           want_nsamp=count is not None, **kw)
@@ -762,12 +767,15 @@ def run_learned(args, dev, stream, flush):
         res["skip_f32"]["ms_per_frame"]
     res["speedup_learned_bf16_vs_skip_f32"] = res["skip_f32"]["ms_per_frame"] / \
         res["learned_bf16"]["ms_per_frame"]
+    res["speedup_gridhull_bf16_vs_plain_f32"] = res["plain_f32"]["ms_per_frame"] / \
+        res["gridhull_bf16"]["ms_per_frame"]
     res["note"] = ("learned_* include the per-frame max-opacity grid (learned_bf16* computes it "
                    "from its BF16 copy), skip_f32 the per-frame "
                    "value-range grid (the field changes every frame); skip_f32 is exact "
                    "(bit-identical to plain_f32), learned_* within the stated LSB; "
-                   "learned_bf16_nowiden: the same proposal without keeping the grid's nonzero "
-                   "chord segments")
+                   "learned_bf16_nowiden: the same proposal without widening by the grid; "
+                   "gridhull_*: the widening alone, without a network (each ray keeps the "
+                   "hull of its samples in macro cells with a nonzero max-opacity grid value)")
     return res
 
 

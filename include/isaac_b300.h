@@ -452,14 +452,23 @@ int isaac_mlp_train_step(isaac_mlp *model, const uint16_t *X, const isaac_ray *r
                          int64_t n_rays, float lr, int32_t margin, float *loss_sum, void *stream);
 
 /* The interval proposal applied to one frame.
- * widen != 0: a confident ray's range is widened to keep every chord segment
- * whose grid feature is nonzero -- segment i of 32 covers samples
- * [floor(i*nsteps/32), ceil((i+1)*nsteps/32)) and its feature is the grid at
- * its midpoint -- i.e. the range becomes the hull of the network's range
- * (when not empty) and those segments.  The network may tighten a range
- * within what the grid marks as possibly visible, never cut such a part. */
+ * widen != 0: a confident ray's range becomes the hull of the network's
+ * range (when not empty) and every sample of the ray whose position lies in a
+ * macro cell (floor(p / cell), clamped to the grid) with a nonzero grid
+ * value, then is clipped to the ray; two 3D-DDA walks over the macro cells
+ * per ray find the first and the last such sample (a kernel after the
+ * network's; a sample within FP32 rounding of a cell face may count on either
+ * side).  The network may tighten a range within what the grid marks as
+ * possibly visible, never cut such a part.  The grid holds the max opacity at
+ * the cells' values, so a sample whose LUT opacity is nonzero while that of
+ * every cell around it is zero (a transfer function zero around a nonzero
+ * bump) can still be cut; where the opacity is nonzero exactly above (or
+ * below) a threshold, nothing can.
+ * model == NULL with widen != 0: no network runs; every ray's range is the
+ * hull of its samples in nonzero macro cells (empty-space skipping by the
+ * max-opacity grid alone); `stats` is not updated. */
 typedef struct {
-    const isaac_mlp *model;   /* params + half_w are read */
+    const isaac_mlp *model;   /* params + half_w are read (NULL: see above) */
     const float *grid;        /* device max-opacity grid of this frame (isaac_opacity_grid) */
     int32_t cell;             /* its macro-cell size */
     float threshold;          /* confidence needed to restrict a ray (e.g. 0.9) */

@@ -767,6 +767,7 @@ struct KPropose {
     float threshold;
     int margin;
     int widen;
+    int hull_only;            // no network: every ray's range is its grid hull
     int *stats;
 };
 
@@ -864,8 +865,8 @@ static __global__ void __launch_bounds__(128) k_mlp_widen(const __grid_constant_
     const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
     for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         RayRec rec = p.rays[r];
-        if (rec.reserved != kWidenPending) continue;
-        int kb = rec.jf, ke = rec.jl;
+        if (!p.hull_only && rec.reserved != kWidenPending) continue;
+        int kb = p.hull_only ? 0 : rec.jf, ke = p.hull_only ? 0 : rec.jl;   // hull only: empty
         const int ns = rec.nsteps;
         const bool open = ke > kb;
         const int first = walk_to_nonzero(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, 0,
@@ -901,8 +902,9 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     p.ctr = fp.ctr;
     p.rays = fp.rays;
     p.longs = fp.longs;
-    p.hw = reinterpret_cast<const __half *>(pr->model->half_w);
-    p.params = pr->model->params;
+    p.hw = pr->model ? reinterpret_cast<const __half *>(pr->model->half_w) : nullptr;
+    p.params = pr->model ? pr->model->params : nullptr;
+    p.hull_only = pr->model == nullptr;
     p.grid = pr->grid;
     p.cell = pr->cell;
     p.gx = (fp.nx + pr->cell - 1) / pr->cell;
@@ -924,7 +926,7 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
     const long long blocks = std::max(1LL, std::min<long long>((rect + 16 * kPropWarps - 1) / (16 * kPropWarps),
                                                               (long long)sms * 2));
-    k_mlp_propose<<<(unsigned)blocks, kPropWarps * 32, smem, st>>>(p);
+    if (!p.hull_only) k_mlp_propose<<<(unsigned)blocks, kPropWarps * 32, smem, st>>>(p);
     if (p.widen) {
         const long long wb = std::max(1LL, std::min<long long>((rect + 127) / 128, (long long)sms * 16));
         k_mlp_widen<<<(unsigned)wb, 128, 0, st>>>(p);
@@ -937,8 +939,10 @@ int proposal_hook(const isaac_proposal *pr, const isaac_render_opts *opts, Frame
     hook->fn = nullptr;
     hook->arg = nullptr;
     if (!pr) return ISAAC_OK;
-    int rc = check_model(pr->model, false);
-    if (rc) return rc;
+    if (pr->model || !pr->widen) {   // no model: the grid's hull alone (needs widen)
+        const int rc = check_model(pr->model, false);
+        if (rc) return rc;
+    }
     if (!pr->grid || pr->cell < 1) return fail(ISAAC_EINVAL, "proposal needs a grid and a cell size >= 1");
     if (!(pr->threshold >= 0.0f) || pr->margin < 0)
         return fail(ISAAC_EINVAL, "proposal threshold must be >= 0 and margin >= 0");

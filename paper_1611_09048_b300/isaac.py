@@ -918,6 +918,15 @@ class MLPModel:
         return p
 
 
+def grid_proposal(grid, cell, stats=None):
+    """A proposal without a network: every ray marches the hull of its samples
+    in macro cells whose max-opacity grid value is nonzero."""
+    p = Proposal(None, grid.data_ptr(), int(cell), 0.0, 0,
+                 stats.data_ptr() if stats is not None else None, 1)
+    p._keep = (grid, stats)
+    return p
+
+
 def checkpoint_save(desc, tag=0, stream=None) -> bytes:
     lib = load()
     n = lib.isaac_mlp_checkpoint_bytes(1 if desc.adam_m and desc.adam_v else 0)

@@ -308,3 +308,47 @@ def test_proposal_windows_match_oracle_rule(cuda_ok, margin, widen):
         keep = omlp.nonzero_samples(e, d, ns, sc.step, g_np, 8)
         assert np.mean([len(k) > 0 for k in keep]) > 0.1      # the widening has work to do
     assert np.all(ok | tie), np.flatnonzero(~ok & ~tie)[:10]
+
+
+def test_grid_hull_windows_and_exact_frame(cuda_ok):
+    """A proposal without a network: every ray's range is the hull of its
+    samples in macro cells with a nonzero max-opacity grid value (the oracle's
+    nonzero_samples, up to a sample within 1e-3 voxel of a macro-cell face);
+    with the bubble's transfer function (zero below a threshold, nonzero above)
+    no visible sample lies outside it, so the frame equals the plain one bit
+    for bit while far fewer samples are marched."""
+    import torch
+    sc = synth.scene_bubble(64, frame=6, seed=7, width=160, height=120, dist_factor=1.2)
+    ds = isaac.DeviceScene(sc)
+    grid = ds.opacity_grid(8)
+    rays, count, p8, p32, pns = ds.trace(want_f32=True, want_nsamp=True)
+    h_rays, h_cnt, h8, h32, hns = ds.trace(proposal=isaac.grid_proposal(grid, 8), want_f32=True,
+                                          want_nsamp=True)
+    torch.cuda.synchronize()
+    k = int(count.item())
+    assert int(h_cnt.item()) == k and k > 3000
+    base = rays[:k].cpu().numpy()
+    got = h_rays[:k].cpu().numpy()
+    base, got = base[np.argsort(base[:, 7])], got[np.argsort(got[:, 7])]
+    fl = base.view(np.float32)
+    e, d = fl[:, 0:3].astype(np.float64), fl[:, 4:7].astype(np.float64)
+    keep = omlp.nonzero_samples(e, d, base[:, 3], sc.step, grid.cpu().numpy(), 8)
+    kb = np.array([kk[0] if len(kk) else 0 for kk in keep])
+    ke = np.array([kk[-1] + 1 if len(kk) else 0 for kk in keep])
+    empty = np.array([len(kk) == 0 for kk in keep])
+
+    def near_face(r, s):
+        p = e[r] + s * sc.step * d[r]
+        f = p / 8.0 - np.floor(p / 8.0)
+        return bool(np.any(np.minimum(f, 1.0 - f) * 8.0 < 1e-3))
+
+    for r in range(k):
+        if empty[r]:
+            assert got[r, 3] <= got[r, 8] or near_face(r, got[r, 8]), r
+            continue
+        db, de = got[r, 8] - kb[r], got[r, 3] - ke[r]
+        assert (db == 0 or (abs(db) <= 1 and near_face(r, min(got[r, 8], kb[r])))), (r, db)
+        assert (de == 0 or (abs(de) <= 1 and near_face(r, min(got[r, 3], ke[r])))), (r, de)
+    assert empty.mean() > 0.2 and (~empty).mean() > 0.1
+    assert torch.equal(p8, h8) and torch.equal(p32, h32)
+    assert hns.sum().item() < 0.5 * pns.sum().item()
