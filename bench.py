@@ -577,30 +577,40 @@ def run_closeup(args, ds, stream, flush, count=4, dist=0.9):
     W, H = sc.width, sc.height
     cams = synth.fibonacci_cameras(tuple(sc.n), W, H, count=count, seed=7, dist_factor=dist)
     out = torch.empty((H, W, 4), dtype=torch.uint8, device=ds.device)
+    out_staged = torch.empty((H, W, 4), dtype=torch.uint8, device=ds.device)
     ns = torch.empty((H, W), dtype=torch.int32, device=ds.device)
-    samples, ms, rays = 0, [], 0
+    samples, rays, same = 0, 0, True
+    ms = {False: [], True: []}
     for mv, proj in cams:
         with torch.cuda.stream(stream):
             ds.render(mv, proj, out=out, nsamples=ns, stream=stream)
+            ds.render(mv, proj, out=out_staged, stream=stream, staged=True)
         torch.cuda.synchronize()
         samples += int(ns.sum(dtype=torch.int64).item())
         rays += int((ns > 0).sum().item())
-        prep = ds.prepare(mv, proj, out)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-        with torch.cuda.stream(stream):
-            ds.launch(prep, stream)
-            for a, b in ev:
-                flush.zero_()
-                a.record(stream)
+        same &= bool(torch.equal(out, out_staged))
+        # the default gather march, then the staged march (ISAAC_MARCH_STAGED)
+        for staged in (False, True):
+            prep = ds.prepare(mv, proj, out, staged=staged)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+            with torch.cuda.stream(stream):
                 ds.launch(prep, stream)
-                b.record(stream)
-        torch.cuda.synchronize()
-        ms += [a.elapsed_time(b) for a, b in ev]
-    per_frame = statistics.mean(ms)
+                for a, b in ev:
+                    flush.zero_()
+                    a.record(stream)
+                    ds.launch(prep, stream)
+                    b.record(stream)
+            torch.cuda.synchronize()
+            ms[staged] += [a.elapsed_time(b) for a, b in ev]
+    per_frame, staged_frame = statistics.mean(ms[False]), statistics.mean(ms[True])
     return {"cameras": count, "camera_distance": f"{dist}x box diagonal",
             "ms_per_frame": per_frame, "samples_per_frame": samples / count,
             "hit_rays_per_frame": rays / count,
-            "samples_per_s": (samples / count) / (per_frame * 1e-3)}
+            "samples_per_s": (samples / count) / (per_frame * 1e-3),
+            "staged_ms_per_frame": staged_frame, "staged_speedup": per_frame / staged_frame,
+            "staged_bitwise_equal": same,
+            "staged_note": "ISAAC_MARCH_STAGED: one thread per ray, per-warp shared-memory boxes of the "
+                           "field (opt-in; the default is the gather march)"}
 
 
 def run_learned(args, dev, stream, flush):

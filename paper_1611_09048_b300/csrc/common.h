@@ -57,6 +57,10 @@ int choose_lanes(long long rect_pixels, int hint, int corner_bytes = 0);
 // Bytes a trilinear corner gathers over the first `nact` sources of p (4 per
 // component), the corner_bytes of choose_lanes for a zero-copy frame.
 int zc_corner_bytes(const KParams &p, int nact);
+// Whether a zero-copy plain frame may use the staged march (opts asks for it,
+// trilinear, 32-bit offsets, no footprint, every source with the same readable
+// range); the caller still needs a compiled staged kernel for the signature.
+bool staging_allowed(const KParams &p, int nact, const isaac_render_opts *opts, bool wide);
 // Most march chunks a warp takes per atomic (KParams::grab, guided
 // self-scheduling): 16; the environment variable ISAAC_MARCH_GRAB (1..64)
 // overrides it, 1 = one chunk per atomic.  Scheduling only: the image does not

@@ -797,7 +797,7 @@ extern "C" int isaac_opacity_grid(const isaac_source *sources, const isaac_chain
         return fail(ISAAC_EINVAL, "n_sources %d outside 1..%d", n_sources, ISAAC_MAX_SOURCES);
     if (cell < 2 || cell > 1024) return fail(ISAAC_EINVAL, "cell %d outside 2..1024", cell);
     if (opts->active_mask >> n_sources) return fail(ISAAC_EINVAL, "active_mask beyond n_sources");
-    if (opts->flags & ~ISAAC_LUTS_HOST) return fail(ISAAC_EINVAL, "unknown opts.flags bits");
+    if (opts->flags & ~(ISAAC_LUTS_HOST | ISAAC_MARCH_STAGED)) return fail(ISAAC_EINVAL, "unknown opts.flags bits");
     if (!(opts->flags & ISAAC_LUTS_HOST) && ((uintptr_t)luts) % 16)
         return fail(ISAAC_EINVAL, "luts must be 16-byte aligned");
     KGrid p;

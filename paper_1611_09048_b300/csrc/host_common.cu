@@ -276,7 +276,7 @@ int prepare_frame(const isaac_camera *cam, const isaac_plane *clip, int32_t n_cl
                         (long long)opt->offset[a], (long long)(opt->offset[a] + opt->n[a]),
                         (long long)gn[a], a);
     }
-    if (opt->flags & ~ISAAC_LUTS_HOST) return fail(ISAAC_EINVAL, "unknown opts.flags bits 0x%x", opt->flags);
+    if (opt->flags & ~(ISAAC_LUTS_HOST | ISAAC_MARCH_STAGED)) return fail(ISAAC_EINVAL, "unknown opts.flags bits 0x%x", opt->flags);
     if (!(opt->step > 0.0f) || !std::isfinite(opt->step))
         return fail(ISAAC_EINVAL, "step must be positive and finite");
     if (opt->interp != 0 && opt->interp != 1) return fail(ISAAC_EINVAL, "interp must be 0 or 1");

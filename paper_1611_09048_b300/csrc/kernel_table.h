@@ -24,6 +24,12 @@ struct ZcEntry {
 extern const ZcEntry *const k_zc_entries;
 extern const int k_n_zc_entries;
 
+// Mode of the staged march (raycast_staged.cu), after the march modes of
+// raycast.cuh; its kernels have their own table.
+constexpr int kModeStaged = 6;
+extern const ZcEntry *const k_staged_entries;
+extern const int k_n_staged_entries;
+
 void launch_fill(const KParams &p, cudaStream_t st);
 void launch_setup(const KParams &p, cudaStream_t st);
 void launch_copy_rays(const KParams &p, RayRec *out, long long cap, int *count, cudaStream_t st);

@@ -163,6 +163,14 @@ int zc_corner_bytes(const KParams &p, int nact)
     return b;
 }
 
+bool staging_allowed(const KParams &p, int nact, const isaac_render_opts *opts, bool wide)
+{
+    if (!(opts->flags & ISAAC_MARCH_STAGED) || opts->interp != 1 || wide || p.touched) return false;
+    for (int a = 1; a < nact; ++a)   // one staged box serves every source
+        if (p.src[a].lo != p.src[0].lo || p.src[a].hi_pad != p.src[0].hi_pad) return false;
+    return true;
+}
+
 int march_grab()
 {
     static const int env = [] {
@@ -211,10 +219,13 @@ FrameLaunch find_zc(int nact, unsigned sig, int interp, bool wide, int mode, int
                     int *rl_used)
 {
     const ZcEntry *best = nullptr;
+    const bool staged = mode == kModeStaged;
+    const ZcEntry *table = staged ? k_staged_entries : k_zc_entries;
+    const int n_table = staged ? k_n_staged_entries : k_n_zc_entries;
     for (int pass = 0; pass < 2 && !best; ++pass) {
         const unsigned want = pass == 0 ? sig : 0u;
-        for (int i = 0; i < k_n_zc_entries; ++i) {
-            const ZcEntry &e = k_zc_entries[i];
+        for (int i = 0; i < n_table; ++i) {
+            const ZcEntry &e = table[i];
             if (e.nact != nact || e.sig != want || e.interp != interp || e.wide != wide ||
                 e.mode != mode)
                 continue;
@@ -295,8 +306,11 @@ extern "C" int isaac_render(const isaac_source *sources, const isaac_chain *chai
     int rl = 1;
     if (nact > 0) {
         const long long rect = (long long)(p.rx1 - p.rx0) * (long long)(p.ry1 - p.ry0);
-        const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact));
-        fn = find_zc(nact, sig, opts->interp, wide, p.touched ? MODE_TOUCH : MODE_PLAIN, want, &rl);
+        if (staging_allowed(p, nact, opts, wide)) fn = find_zc(nact, sig, 1, false, kModeStaged, 1, &rl);
+        if (!fn) {
+            const int want = p.touched ? 1 : choose_lanes(rect, opts->lanes_per_ray, zc_corner_bytes(p, nact));
+            fn = find_zc(nact, sig, opts->interp, wide, p.touched ? MODE_TOUCH : MODE_PLAIN, want, &rl);
+        }
         if (!fn)
             return fail(ISAAC_ENOTSUP, "no kernel for %d sources (footprint with 64-bit offsets?)",
                         nact);

@@ -23,6 +23,7 @@ MAX_CLIP = 6
 OK, EINVAL, EGUARD, ENOMEM, ECUDA, ENOTSUP = 0, -1, -2, -3, -4, -5
 F32, BF16, F16, E4M3 = 0, 1, 2, 3
 LUTS_HOST = 1   # isaac_render_opts.flags: `luts` is a host array
+MARCH_STAGED = 2   # isaac_render_opts.flags: staged march where the frame allows it
 OPS = {"add": 1, "mul": 2, "length": 3, "sum": 4, "pow": 5, "log": 6}
 
 # every C symbol declared in include/isaac_b300.h
@@ -441,12 +442,12 @@ class DeviceScene:
         return ((nx + 2) * (ny + 2) * (nz + 2) + 31) // 32
 
     def prepare(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, mask=None,
-                touched=None, lanes=None, depth=None, luts=None):
+                touched=None, lanes=None, depth=None, luts=None, staged=False):
         """Marshal one frame's arguments (camera, opts, framebuffer) once; the
         returned tuple can be launched repeatedly with ``launch``.  ``luts``: a
         device float32 tensor shaped like ``self.luts`` to read the transfer
         functions from instead (e.g. one of two buffers a pipeline uploads into
-        in turn)."""
+        in turn).  ``staged``: set ISAAC_MARCH_STAGED."""
         sc = self.scene
         cam = make_camera(sc.modelview if mv is None else mv,
                           sc.projection if proj is None else proj, sc.width, sc.height)
@@ -469,6 +470,8 @@ class DeviceScene:
             raise ValueError("luts must be a contiguous float32 tensor shaped like the scene's, on its device")
         else:
             lut_ptr = luts.data_ptr()
+        if staged:
+            opts.flags |= MARCH_STAGED
         keep = (cam, planes, fb, opts, luts)
         return (self.sources, self.chains, len(sc.sources), lut_ptr,
                 C.cast(self.weights, C.c_void_p), C.byref(cam), planes, n_clip, C.byref(opts),
@@ -481,7 +484,7 @@ class DeviceScene:
 
     def render(self, mv=None, proj=None, out=None, rgba32=None, nsamples=None, stream=None,
                mask=None, want_f32=False, want_nsamp=False, touched=None, lanes=None,
-               depth=None, luts=None):
+               depth=None, luts=None, staged=False):
         """Enqueue one frame; returns (rgba8, rgba32 or None, nsamples or None)
         as device tensors (``depth``: optional (H, W) float32 output; ``luts``:
         a device tensor, or a host float32 array copied by the call)."""
@@ -493,8 +496,8 @@ class DeviceScene:
             rgba32 = torch.empty((H, W, 4), dtype=torch.float32, device=self.device)
         if nsamples is None and want_nsamp:
             nsamples = torch.empty((H, W), dtype=torch.int32, device=self.device)
-        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes, depth, luts),
-                    stream)
+        self.launch(self.prepare(mv, proj, out, rgba32, nsamples, mask, touched, lanes, depth, luts,
+                                 staged), stream)
         return out, rgba32, nsamples
 
 
