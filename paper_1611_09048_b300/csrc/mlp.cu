@@ -10,6 +10,7 @@
 
 #include "common.h"
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace isaac {
 
@@ -76,37 +77,51 @@ struct KFwd {
     float *U;
 };
 
-constexpr int kFwdSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + 64 * LD_IN;
-
-static __global__ void __launch_bounds__(128) k_mlp_forward(const __grid_constant__ KFwd p)
+// Inference on the tensor cores (tcgen05): persistent CTAs take tiles of 128
+// rays; the inputs of a tile are copied into its K-major activation tile, the
+// network runs as in tc_forward_tile, and threads 0..127 write the outputs of
+// their row.  A tile whose tensor-core wait ran out (and every later tile of
+// the CTA) gets NaN outputs.
+static __global__ void __launch_bounds__(kTcThreads) k_mlp_forward(const __grid_constant__ KFwd p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __half *sT1 = reinterpret_cast<__half *>(smem_raw);
-    __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
-    __half *xs = sT4 + 8 * LD_W;
-    load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    for (long long base = blockIdx.x * 64LL; base < p.n; base += gridDim.x * 64LL) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 64 * MLP_IN; i += blockDim.x) {
-            const long long r = base + i / MLP_IN;
-            xs[(i / MLP_IN) * LD_IN + i % MLP_IN] = r < p.n ? p.X[r * MLP_IN + i % MLP_IN] : __float2half_rn(0.0f);
+    TcState s = tc_begin(p.hw, p.params, smem_raw);
+    unsigned char *tile = smem_raw + kTcOffX;
+    long long base = blockIdx.x * (long long)kTcRows;
+    bool alive = true;
+    for (; base < p.n; base += gridDim.x * (long long)kTcRows) {
+        for (int i = threadIdx.x; i < kTcRows * (MLP_IN / 8); i += blockDim.x) {
+            const int row = i / (MLP_IN / 8), c = i % (MLP_IN / 8);
+            const long long r = base + row;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (r < p.n) {   // X is 4-byte aligned: four 4-byte loads per 8 inputs
+                const unsigned *src = reinterpret_cast<const unsigned *>(p.X + r * MLP_IN + 8 * c);
+                w = make_uint4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+            }
+            *reinterpret_cast<uint4 *>(tile + tc_off(row, 8 * c, kTcLboX)) = w;
         }
+        fence_async_smem();
+        tc_fence_before();
         __syncthreads();
         float u[4];
-        mlp_forward_warp(xs, warp * 16, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr,
-                         nullptr, 0);
-        const long long r0 = base + warp * 16 + g, r1 = r0 + 8;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int col = 2 * t + j;
-            if (col < MLP_OUT) {
-                if (r0 < p.n) p.U[r0 * MLP_OUT + col] = u[j];
-                if (r1 < p.n) p.U[r1 * MLP_OUT + col] = u[2 + j];
-            }
+        if (!tc_forward_tile(s, smem_raw, u)) {
+            alive = false;
+            break;
+        }
+        const long long r = base + threadIdx.x;
+        if (threadIdx.x < kTcRows && r < p.n)
+            for (int j = 0; j < MLP_OUT; ++j) p.U[r * MLP_OUT + j] = u[j];
+    }
+    if (!alive) {
+        tc_wait(s.bar, (s.phase - 1u) & 1u);   // let an MMA still in flight finish (bounded)
+        const float nan = __int_as_float(0x7fc00000);
+        for (; base < p.n; base += gridDim.x * (long long)kTcRows) {
+            const long long r = base + threadIdx.x;
+            if (threadIdx.x < kTcRows && r < p.n)
+                for (int j = 0; j < MLP_OUT; ++j) p.U[r * MLP_OUT + j] = nan;
         }
     }
+    tc_end(s);
 }
 
 // ---------------------------------------------------------------- training
@@ -642,10 +657,9 @@ extern "C" int isaac_mlp_forward(const isaac_mlp *m, const uint16_t *X, int64_t 
     p.X = reinterpret_cast<const __half *>(X);
     p.n = n_rays;
     p.U = U;
-    const int smem = kFwdSmemHalves * 2;
-    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    const long long blocks = std::min<long long>((n_rays + 63) / 64, 148LL * 2);
-    k_mlp_forward<<<(unsigned)blocks, 128, smem, (cudaStream_t)stream>>>(p);
+    cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    const long long blocks = std::min<long long>((n_rays + kTcRows - 1) / kTcRows, (long long)sm_count() * 2);
+    k_mlp_forward<<<(unsigned)blocks, kTcThreads, kTcSmemBytes, (cudaStream_t)stream>>>(p);
     return check_cuda("isaac_mlp_forward");
 }
 
@@ -771,86 +785,82 @@ struct KPropose {
     int *stats;
 };
 
-// 8 warps per block share one copy of the FP16 weights (~48 KB) and keep a
-// 16-ray input tile each (~7.4 KB): ~106 KB, so two blocks (16 warps) fit on
-// an SM; with 4 warps per block the weights limited it to 8 warps.
-constexpr int kPropWarps = 8;
-constexpr int kPropSmemHalves = MLP_W * LD_IN + 2 * MLP_W * LD_W + 8 * LD_W + kPropWarps * 16 * LD_IN;
 // RayRec::reserved of a confident ray whose range k_mlp_widen has yet to widen
 // (its network range is in jf, jl meanwhile).
 constexpr int kWidenPending = 1;
 
-// Persistent warps take 16 rays of the frame's ray list at a time: inputs
-// (2 lanes per ray) into the warp's shared tile, the MLP forward pass, then
-// the decision on lanes holding (u0, u1) of rays g and g+8.
-static __global__ void __launch_bounds__(kPropWarps * 32) k_mlp_propose(const __grid_constant__ KPropose p)
+// The decision for ray r from its network outputs u (Sec. 3.2's marcher is the
+// fallback: an unsure ray keeps its whole range).
+__device__ __forceinline__ void propose_decide(const KPropose &p, unsigned r, const float (&u)[4], int &seen,
+                                               int &restricted)
+{
+    ++seen;
+    const int ns = p.rays[r].nsteps;
+    int kb = 0, ke = ns;
+    if (sigmoidf(u[2]) >= p.threshold) {
+        const float te = sigmoidf(u[0]), tx = sigmoidf(u[1]);
+        kb = (int)floorf(te * (float)ns) - p.margin;
+        ke = (int)ceilf(tx * (float)ns) + p.margin;
+        ++restricted;
+        if (p.widen) {   // k_mlp_widen finishes the ray
+            p.rays[r].jf = kb;
+            p.rays[r].jl = ke;
+            p.rays[r].reserved = kWidenPending;
+            return;
+        }
+        kb = min(max(kb, 0), ns);
+        ke = min(max(ke, kb), ns);
+        p.rays[r].kbeg = kb;
+        p.rays[r].nsteps = ke;
+    }
+    if (p.longs && ke - kb > kLongRaySamples) {
+        p.rays[r].jf = kLongRay;
+        p.longs[atomicAdd(&p.ctr->n_long, 1u)] = r;
+    }
+}
+
+// Persistent CTAs take tiles of 128 rays of the frame's ray list: the inputs
+// (two threads per ray) into the K-major activation tile, the network on the
+// tensor cores (tc_forward_tile), then one thread per ray decides.  If a
+// tensor-core wait runs out, the rays of that tile and the CTA's later tiles
+// keep their whole range (the plain march).
+static __global__ void __launch_bounds__(kTcThreads) k_mlp_propose(const __grid_constant__ KPropose p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __half *sT1 = reinterpret_cast<__half *>(smem_raw);
-    __half *sT2 = sT1 + MLP_W * LD_IN, *sT3 = sT2 + MLP_W * LD_W, *sT4 = sT3 + MLP_W * LD_W;
-    __half *xs_all = sT4 + 8 * LD_W;
-    load_weights_smem(p.hw, sT1, sT2, sT3, sT4, nullptr, nullptr, nullptr);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    __syncthreads();
-    __half *xs = xs_all + warp * 16 * LD_IN;
+    TcState s = tc_begin(p.hw, p.params, smem_raw);
+    unsigned char *tile = smem_raw + kTcOffX;
     const unsigned n = *(volatile unsigned *)&p.ctr->n_rays;
+    const int row = threadIdx.x >> 1, half = threadIdx.x & 1;
     int seen = 0, restricted = 0;
-    // every ray costs the same here, so warps take fixed strides of the list
-    const unsigned stride = 16u * gridDim.x * (blockDim.x >> 5);
-    for (unsigned base = 16u * (blockIdx.x * (blockDim.x >> 5) + warp); base < n; base += stride) {
-        {
-            const unsigned r = base + (lane >> 1);
-            __half *row = xs + (lane >> 1) * LD_IN;
-            if (r < n) {
-                const RayRec rec = p.rays[r];
-                ray_features_half(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, p.nx, p.ny, p.nz,
-                                  lane & 1, row);
-            } else {
-                for (int i = (lane & 1); i < MLP_IN; i += 2) row[i] = __float2half_rn(0.0f);
-            }
+    bool alive = true;
+    for (unsigned base = blockIdx.x * kTcRows; base < n; base += gridDim.x * kTcRows) {
+        const unsigned r = base + row;
+        if (r < n) {
+            const RayRec rec = p.rays[r];
+            ray_features_tc(rec, p.step, p.grid, p.cell, p.gx, p.gy, p.gz, p.nx, p.ny, p.nz, half, tile, row);
+        } else {   // an empty row: zero inputs
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            for (int c = 0; c < 12; ++c)
+                *reinterpret_cast<uint4 *>(tile + tc_off(row, (half * 12 + c) * 8, kTcLboX)) = z;
+            for (int c = 0; c < 2; ++c)
+                *reinterpret_cast<uint4 *>(tile + tc_off(row, (24 + half * 2 + c) * 8, kTcLboX)) = z;
         }
-        __syncwarp();
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
         float u[4];
-        mlp_forward_warp(xs, 0, sT1, sT2, sT3, sT4, p.params, u, nullptr, nullptr, nullptr, nullptr, 0);
-        const float u2a = __shfl_down_sync(0xffffffffu, u[0], 1);
-        const float u2b = __shfl_down_sync(0xffffffffu, u[2], 1);
-        if (t == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned r = base + g + 8 * h;
-                if (r >= n) continue;
-                ++seen;
-                const int ns = p.rays[r].nsteps;
-                int kb = 0, ke = ns;
-                if (sigmoidf(h ? u2b : u2a) >= p.threshold) {
-                    const float te = sigmoidf(u[2 * h]), tx = sigmoidf(u[2 * h + 1]);
-                    kb = (int)floorf(te * (float)ns) - p.margin;
-                    ke = (int)ceilf(tx * (float)ns) + p.margin;
-                    ++restricted;
-                    if (p.widen) {   // k_mlp_widen finishes the ray
-                        p.rays[r].jf = kb;
-                        p.rays[r].jl = ke;
-                        p.rays[r].reserved = kWidenPending;
-                        continue;
-                    }
-                    kb = min(max(kb, 0), ns);
-                    ke = min(max(ke, kb), ns);
-                    p.rays[r].kbeg = kb;
-                    p.rays[r].nsteps = ke;
-                }
-                if (p.longs && ke - kb > kLongRaySamples) {
-                    p.rays[r].jf = kLongRay;
-                    p.longs[atomicAdd(&p.ctr->n_long, 1u)] = r;
-                }
-            }
+        if (!tc_forward_tile(s, smem_raw, u)) {
+            alive = false;
+            break;
         }
-        __syncwarp();
+        if (threadIdx.x < kTcRows && base + threadIdx.x < n) propose_decide(p, base + threadIdx.x, u, seen, restricted);
     }
-    if (p.stats && t == 0 && (seen | restricted)) {
+    if (!alive) tc_wait(s.bar, (s.phase - 1u) & 1u);   // let an MMA still in flight finish (bounded)
+    if (p.stats && (seen | restricted)) {
         atomicAdd(p.stats, seen);
         atomicAdd(p.stats + 1, restricted);
     }
+    tc_end(s);
 }
 
 // The widening of the confident rays k_mlp_propose marked (network range in
@@ -920,13 +930,11 @@ static int launch_propose(const KParams &fp, const void *arg, cudaStream_t st)
     p.margin = pr->margin;
     p.widen = pr->widen != 0;
     p.stats = pr->stats;
-    const int smem = kPropSmemHalves * 2;
-    cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_mlp_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
     const int sms = sm_count();
     const long long rect = (long long)(fp.rx1 - fp.rx0) * (fp.ry1 - fp.ry0);
-    const long long blocks = std::max(1LL, std::min<long long>((rect + 16 * kPropWarps - 1) / (16 * kPropWarps),
-                                                              (long long)sms * 2));
-    if (!p.hull_only) k_mlp_propose<<<(unsigned)blocks, kPropWarps * 32, smem, st>>>(p);
+    const long long blocks = std::max(1LL, std::min<long long>((rect + kTcRows - 1) / kTcRows, (long long)sms * 2));
+    if (!p.hull_only) k_mlp_propose<<<(unsigned)blocks, kTcThreads, kTcSmemBytes, st>>>(p);
     if (p.widen) {
         const long long wb = std::max(1LL, std::min<long long>((rect + 127) / 128, (long long)sms * 16));
         k_mlp_widen<<<(unsigned)wb, 128, 0, st>>>(p);

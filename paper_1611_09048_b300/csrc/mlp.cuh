@@ -1,7 +1,10 @@
 // mlp.cuh -- device code of the learned ray-interval proposal (sm_103a).
 //
 // A 224 -> 64 -> 64 -> 64 -> 3 MLP with ReLU, FP16 operands and FP32
-// accumulation on the tensor cores (mma.sync m16n8k16).  One warp owns 16 rays:
+// accumulation.  Inference runs on the tcgen05 tensor cores (mlp_tc.cuh).
+// Training's fused forward and backward pass, whose per-warp fragments feed
+// the gradient products, uses the warp-level mma.sync m16n8k16 below: one warp
+// owns 16 rays:
 // layer 1 reads its A operand (16 rays x 224 inputs) from shared memory; every
 // later layer takes the previous layer's accumulator fragments, repacked to
 // FP16, directly as its A operand (the m16n8 accumulator layout of two

@@ -88,7 +88,9 @@ def test_forward_matches_oracle(cuda_ok):
     p16 = {k: _fp16(v) if k.startswith("W") else v.astype(np.float64) for k, v in params.items()}
     want = omlp.forward(p16, X.astype(np.float64))["u"]
     err = np.abs(U.cpu().numpy() - want).max()
-    assert err <= 2e-2 * max(1.0, np.abs(want).max()), err
+    # FP16 hidden activations (rounded once per layer) against FP64: measured
+    # <= 1.5e-3 at |u| <= 3.7
+    assert err <= 5e-3 * max(1.0, np.abs(want).max()), err
 
 
 def test_gradients_match_oracle(cuda_ok):
