@@ -93,6 +93,26 @@ def test_forward_matches_oracle(cuda_ok):
     assert err <= 5e-3 * max(1.0, np.abs(want).max()), err
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 4099])
+def test_forward_tiles_of_any_size(cuda_ok, n):
+    """The tensor-core forward pass works on tiles of 128 rays: a single ray,
+    one short of a tile, exactly one tile, one past it, and many tiles with a
+    ragged tail all match the oracle row by row (no row of a partial tile is
+    lost or taken from a neighbour)."""
+    import torch
+    params = synth.mlp_params(9, bias_scale=0.2)
+    model = isaac.MLPModel(isaac.pack_mlp_params(params), train=False)
+    X = _random_X(n, 100 + n)
+    U = model.forward(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    p16 = {k: _fp16(v) if k.startswith("W") else v.astype(np.float64) for k, v in params.items()}
+    want = omlp.forward(p16, X.astype(np.float64))["u"]
+    got = U.cpu().numpy()
+    assert got.shape == (n, 3)
+    err = np.abs(got - want).max(axis=1)
+    assert np.all(err <= 5e-3 * np.maximum(1.0, np.abs(want).max(axis=1))), err.max()
+
+
 def test_gradients_match_oracle(cuda_ok):
     import torch
     params = synth.mlp_params(7, bias_scale=0.1)
