@@ -657,7 +657,7 @@ def run_learned(args, dev, stream, flush):
              "learned_bf16_nowiden", "gridhull_f32", "gridhull_bf16")
     acc = {k: {"ms": [], "march_ms": [], "samples": 0, "lsb_sum": 0.0, "lsb_max": 0, "px": 0,
                "px_over1": 0, "hit_px": 0} for k in kinds}
-    grid_ms, grid16_ms, range_ms = [], [], []
+    grid_ms, grid16_ms, range_ms, conv_ms = [], [], [], []
     stats = torch.zeros(2, dtype=torch.int32, device=dev)
     stats_off = torch.zeros(2, dtype=torch.int32, device=dev)
     # the test protocol: consecutive frames of the moving bubble (100 by
@@ -682,6 +682,9 @@ def run_learned(args, dev, stream, flush):
         nss = {}
 
         def run(kind, count=None):
+            if kind.endswith("bf16") or kind.endswith("nowiden"):
+                # every frame is a new simulation step: its BF16 copy is made per frame
+                pv.repack(stream=stream)
             if kind in ("learned_f32", "gridhull_f32"):
                 ds.opacity_grid(cell, out=grid, stream=stream)
             if kind.startswith("learned_bf16") or kind == "gridhull_bf16":   # the copy's grid
@@ -742,7 +745,8 @@ def run_learned(args, dev, stream, flush):
         if f % 10 == 0:   # the per-frame grids alone (part of the learned / skip frames above)
             for fn, sink in ((lambda: ds.opacity_grid(cell, out=grid, stream=stream), grid_ms),
                              (lambda: pv.opacity_grid(cell, out=grid, stream=stream), grid16_ms),
-                             (lambda: ds.range_grid(cell, out=ranges, stream=stream), range_ms)):
+                             (lambda: ds.range_grid(cell, out=ranges, stream=stream), range_ms),
+                             (lambda: pv.repack(stream=stream), conv_ms)):
                 gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                        for _ in range(3)]
                 with torch.cuda.stream(stream):
@@ -766,7 +770,11 @@ def run_learned(args, dev, stream, flush):
                             "one timed frame per kind per frame, L2 flushed before it",
            "opacity_grid_ms": statistics.mean(grid_ms),
            "opacity_grid_bf16_ms": statistics.mean(grid16_ms),
-           "range_grid_ms": statistics.mean(range_ms)}
+           "range_grid_ms": statistics.mean(range_ms),
+           "bf16_conversion_ms": statistics.mean(conv_ms),
+           # the field read once, the copy's records over [-1, n]^3 written once
+           "bf16_conversion_gb_per_s": (n ** 3 * 4 + (n + 2) ** 3 * 2)
+           / (statistics.mean(conv_ms) * 1e-3) / 1e9}
     for kind in kinds:
         a = acc[kind]
         ms = statistics.mean(a["ms"])
@@ -785,7 +793,10 @@ def run_learned(args, dev, stream, flush):
         res["learned_bf16"]["ms_per_frame"]
     res["speedup_gridhull_bf16_vs_plain_f32"] = res["plain_f32"]["ms_per_frame"] / \
         res["gridhull_bf16"]["ms_per_frame"]
-    res["note"] = ("learned_* include the per-frame max-opacity grid (learned_bf16* computes it "
+    res["note"] = ("every frame is a new simulation step: the *_bf16 frames include the "
+                   "per-frame BF16 conversion of the float32 field (isaac_pack, "
+                   "bf16_conversion_ms alone); "
+                   "learned_* include the per-frame max-opacity grid (learned_bf16* computes it "
                    "from its BF16 copy), skip_f32 the per-frame "
                    "value-range grid (the field changes every frame); skip_f32 is exact "
                    "(bit-identical to plain_f32), learned_* within the stated LSB; "

@@ -162,6 +162,9 @@ struct KPackSrc {
 struct KPack {
     KPackSrc src[ISAAC_MAX_ACTIVE];
     int nsrc;
+    int ncomp;           // record slots in use: 0 .. ncomp-1
+    int slot_src[8];     // source of record slot k (slots follow the sources in order)
+    int slot_comp[8];    // its component
     int nx, ny, nz;      // interior cells
     int px, py, pz;      // packed box = n + 2
     int bx, by, bz;      // bricks per axis
@@ -169,123 +172,289 @@ struct KPack {
     float *scales;
 };
 
-// All components of packed cell (x, y, z) in [-1, n]^3 (float32).
+// Source index along one axis for packed coordinate q (cell q - 1 of [-1, n]):
+// the guard cell itself where the source has guards, else the border cell
+// repeated (exactly what clamping reads).
+__device__ __forceinline__ int pack_axis(int q, int n, int guard)
+{
+    return guard ? q - 1 : min(max(q - 1, 0), n - 1);
+}
+
+// One (y, z) row of the packed box: per record slot, the address of its
+// component in source cell x = 0 of that row, the source's x stride and
+// guard flag.  Rows are warp-uniform, so this is set up once per row.
 template <int PAD>
-__device__ __forceinline__ void gather_cell(const KPack &p, int x, int y, int z, float (&v)[PAD])
+struct PackRow {
+    const float *p[PAD];
+    long long sx[PAD];
+    int guard[PAD];
+};
+
+template <int PAD>
+__device__ __forceinline__ void pack_row(const KPack &p, int y, int z, PackRow<PAD> &r)
 {
 #pragma unroll
-    for (int c = 0; c < PAD; ++c) v[c] = 0.0f;
-    int c0 = 0;
-#pragma unroll
-    for (int s = 0; s < ISAAC_MAX_ACTIVE; ++s) {
-        if (s >= p.nsrc) break;
-        const KPackSrc &q = p.src[s];
-        int xi = x, yi = y, zi = z;
-        if (q.guard == 0) {    // no neighbour data: repeat the border cell
-            xi = min(max(xi, 0), p.nx - 1);
-            yi = min(max(yi, 0), p.ny - 1);
-            zi = min(max(zi, 0), p.nz - 1);
+    for (int k = 0; k < PAD; ++k) {
+        if (k < p.ncomp) {
+            const KPackSrc &q = p.src[p.slot_src[k]];
+            const int yi = pack_axis(y, p.ny, q.guard), zi = pack_axis(z, p.nz, q.guard);
+            r.p[k] = q.base + ((long long)yi * q.sy + (long long)zi * q.sz + (long long)p.slot_comp[k] * q.sc);
+            r.sx[k] = q.sx;
+            r.guard[k] = q.guard;
+        } else {
+            r.p[k] = nullptr;
+            r.sx[k] = 0;
+            r.guard[k] = 0;
         }
-        const float *b = q.base + ((long long)xi * q.sx + (long long)yi * q.sy + (long long)zi * q.sz);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (c < q.fdim) {
-                const int slot = c0 + c;
-#pragma unroll
-                for (int k = 0; k < PAD; ++k)
-                    if (k == slot) v[k] = __ldg(b + (long long)c * q.sc);
-            }
-        c0 += q.fdim;
     }
 }
 
+// All record slots of packed cell x of the row (float32; unused slots 0).
+template <int PAD>
+__device__ __forceinline__ void pack_cell(const KPack &p, const PackRow<PAD> &r, int x, float (&v)[PAD])
+{
+#pragma unroll
+    for (int k = 0; k < PAD; ++k)
+        v[k] = k < p.ncomp ? __ldg(r.p[k] + (long long)pack_axis(x, p.nx, r.guard[k]) * r.sx[k]) : 0.0f;
+}
+
+__device__ __forceinline__ unsigned short to16(float v, int dt)
+{
+    return dt == ISAAC_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v))
+                            : __half_as_ushort(__float2half_rn(v));
+}
+
+// Record i of the copy in one store as wide as the record (2 to 32 bytes;
+// records are aligned to their size: the copy starts 16-byte aligned).
 template <int DT, int PAD>
 __device__ __forceinline__ void store_record(unsigned char *rec, long long i, const float (&v)[PAD])
 {
     if constexpr (DT == ISAAC_F32) {
         float *o = reinterpret_cast<float *>(rec) + i * PAD;
+        if constexpr (PAD == 1) {
+            o[0] = v[0];
+        } else if constexpr (PAD == 2) {
+            *reinterpret_cast<float2 *>(o) = make_float2(v[0], v[1]);
+        } else {
 #pragma unroll
-        for (int c = 0; c < PAD; ++c) o[c] = v[c];
+            for (int q = 0; q < PAD / 4; ++q)
+                reinterpret_cast<float4 *>(o)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
     } else {
         unsigned short h[PAD];
 #pragma unroll
-        for (int c = 0; c < PAD; ++c) {
-            if constexpr (DT == ISAAC_BF16)
-                h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(v[c]));
-            else
-                h[c] = __half_as_ushort(__float2half_rn(v[c]));
-        }
+        for (int c = 0; c < PAD; ++c) h[c] = to16(v[c], DT);
         unsigned short *o = reinterpret_cast<unsigned short *>(rec) + i * PAD;
+        if constexpr (PAD == 1) {
+            o[0] = h[0];
+        } else {
+            unsigned w[PAD / 2];
 #pragma unroll
-        for (int c = 0; c < PAD; ++c) o[c] = h[c];
+            for (int c = 0; c < PAD / 2; ++c) w[c] = (unsigned)h[2 * c] | ((unsigned)h[2 * c + 1] << 16);
+            if constexpr (PAD == 2)
+                *reinterpret_cast<unsigned *>(o) = w[0];
+            else if constexpr (PAD == 4)
+                *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+            else
+                *reinterpret_cast<uint4 *>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
-// float32 / bfloat16 / float16: one thread per packed cell.
+// float32 / bfloat16 / float16: a warp per (y, z) row of the packed box, its
+// lanes along x (coalesced source reads, contiguous record stores); rows are
+// spread over the warps of the grid.
 template <int DT, int PAD>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ KPack p)
 {
-    const long long total = (long long)p.px * p.py * p.pz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % p.px);
-        const long long r = i / p.px;
-        const int y = (int)(r % p.py);
-        const int z = (int)(r / p.py);
-        float v[PAD];
-        gather_cell<PAD>(p, x - 1, y - 1, z - 1, v);
-        store_record<DT, PAD>(const_cast<unsigned char *>(p.rec), i, v);
+    const int lane = threadIdx.x & 31;
+    const int rows = p.py * p.pz;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += nwarps) {
+        const int z = r / p.py, y = r - z * p.py;
+        PackRow<PAD> row;
+        pack_row<PAD>(p, y, z, row);
+        const long long i0 = (long long)r * p.px;
+        if constexpr (PAD == 1 && DT != ISAAC_F32) {
+            if ((p.px & 1) == 0) {
+                // 2-byte records, rows of an even length: each lane converts
+                // the cell pairs (x, x + 1), x even, and stores a pair as one
+                // 4-byte word (rows start 4-byte aligned), 8 pairs' loads in
+                // flight per lane
+                constexpr int U2 = 8;
+                unsigned *rec32 = reinterpret_cast<unsigned *>(p.rec);
+                for (int xb = 2 * lane; xb < p.px; xb += 64 * U2) {
+                    float v[U2][2];
+#pragma unroll
+                    for (int u = 0; u < U2; ++u) {
+                        const int x = xb + 64 * u;
+                        if (x < p.px) {
+                            float a[1], b[1];
+                            pack_cell<1>(p, row, x, a);
+                            pack_cell<1>(p, row, x + 1, b);
+                            v[u][0] = a[0];
+                            v[u][1] = b[0];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U2; ++u) {
+                        const int x = xb + 64 * u;
+                        if (x < p.px)
+                            rec32[(i0 + x) >> 1] = (unsigned)to16(v[u][0], DT) | ((unsigned)to16(v[u][1], DT) << 16);
+                    }
+                }
+                continue;
+            }
+        }
+        // U cells per lane are loaded before any is stored, so that a lane
+        // keeps U * ncomp loads in flight (the stores may alias the sources
+        // as far as the compiler knows)
+        constexpr int U = PAD <= 2 ? 8 : (PAD == 4 ? 4 : 2);
+        for (int xb = lane; xb < p.px; xb += 32 * U) {
+            float v[U][PAD];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (xb + 32 * u < p.px) pack_cell<PAD>(p, row, xb + 32 * u, v[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (xb + 32 * u < p.px) store_record<DT, PAD>(p.rec, i0 + xb + 32 * u, v[u]);
+        }
     }
 }
 
-// E4M3: one 512-thread block per 8^3 brick; block-wide absmax per component,
-// scale = absmax / 448 (1 for an all-zero brick), code = E4M3_sat(v / scale).
+constexpr int kPackBricksX = 4;   // bricks along x per E4M3 pack block (32 lanes)
+
+// The (x, y) column of one thread through the packed box: per record slot,
+// the address of its component in source cell (x, y, z = 0), the source's z
+// stride and guard flag.
 template <int PAD>
-__global__ void __launch_bounds__(512) k_pack_e4m3(const __grid_constant__ KPack p)
+struct PackColumn {
+    const float *p[PAD];
+    long long sz[PAD];
+    int guard[PAD];
+};
+
+template <int PAD>
+__device__ __forceinline__ void pack_column(const KPack &p, int x, int y, PackColumn<PAD> &c)
 {
-    __shared__ float s_max[16][PAD];
-    const int b = blockIdx.x;
-    const int bxi = b % p.bx, byi = (b / p.bx) % p.by, bzi = b / (p.bx * p.by);
-    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    const int x = bxi * 8 + lx, y = byi * 8 + ly, z = bzi * 8 + lz;   // packed coordinates
-    const bool inside = x < p.px && y < p.py && z < p.pz;
-    float v[PAD];
-    if (inside) {
-        gather_cell<PAD>(p, x - 1, y - 1, z - 1, v);
-    } else {
 #pragma unroll
-        for (int c = 0; c < PAD; ++c) v[c] = 0.0f;
+    for (int k = 0; k < PAD; ++k) {
+        if (k < p.ncomp) {
+            const KPackSrc &q = p.src[p.slot_src[k]];
+            const int xi = pack_axis(x, p.nx, q.guard), yi = pack_axis(y, p.ny, q.guard);
+            c.p[k] = q.base + ((long long)xi * q.sx + (long long)yi * q.sy + (long long)p.slot_comp[k] * q.sc);
+            c.sz[k] = q.sz;
+            c.guard[k] = q.guard;
+        } else {
+            c.p[k] = nullptr;
+            c.sz[k] = 0;
+            c.guard[k] = 0;
+        }
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+}
+
+template <int PAD>
+__device__ __forceinline__ void column_cell(const KPack &p, const PackColumn<PAD> &c, int z, float (&v)[PAD])
+{
 #pragma unroll
-    for (int c = 0; c < PAD; ++c) {
-        float m = fabsf(v[c]);
+    for (int k = 0; k < PAD; ++k)
+        v[k] = k < p.ncomp ? __ldg(c.p[k] + (long long)pack_axis(z, p.nz, c.guard[k]) * c.sz[k]) : 0.0f;
+}
+
+// E4M3: a 256-thread block per 4 x 1 x 1 bricks: lane = x (8 lanes per brick),
+// warp = y, each thread down its column through the brick's 8 z layers, ZB
+// layers' loads in flight at a time.  First pass: per thread the absmax of
+// each slot over its 8 cells, reduced over the brick's 8 lanes by shuffles and
+// over the 8 warps in shared memory; scale = absmax / 448 (1 for an all-zero
+// brick).  Second pass: the same cells again (now in L1/L2), code =
+// E4M3_sat(v / scale) with v / scale rounded once to float32, one store of the
+// cell's PAD codes.
+template <int PAD>
+__global__ void __launch_bounds__(256) k_pack_e4m3(const __grid_constant__ KPack p)
+{
+    constexpr int ZB = PAD <= 2 ? 8 : (PAD == 4 ? 4 : 2);
+    __shared__ float s_max[8][kPackBricksX][PAD];
+    __shared__ float s_scale[kPackBricksX][PAD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx = (p.bx + kPackBricksX - 1) / kPackBricksX;
+    const int b = blockIdx.x;
+    const int bxi = (b % gx) * kPackBricksX, byi = (b / gx) % p.by, bzi = b / (gx * p.by);
+    const int x = bxi * 8 + lane, y = byi * 8 + warp;   // packed coordinates
+    const bool in_xy = x < p.px && y < p.py;
+    const int z0 = bzi * 8, nzb = min(8, p.pz - z0);
+    PackColumn<PAD> col;
+    pack_column<PAD>(p, in_xy ? x : 0, in_xy ? y : 0, col);
+    float m[PAD];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) s_max[warp][c] = m;
+    for (int k = 0; k < PAD; ++k) m[k] = 0.0f;
+    if (in_xy) {
+        for (int zb = 0; zb < nzb; zb += ZB) {
+            float v[ZB][PAD];
+#pragma unroll
+            for (int u = 0; u < ZB; ++u)
+                if (zb + u < nzb) column_cell<PAD>(p, col, z0 + zb + u, v[u]);
+#pragma unroll
+            for (int u = 0; u < ZB; ++u)
+                if (zb + u < nzb) {
+#pragma unroll
+                    for (int k = 0; k < PAD; ++k) m[k] = fmaxf(m[k], fabsf(v[u][k]));
+                }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PAD; ++k) {
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) m[k] = fmaxf(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+        if ((lane & 7) == 0) s_max[warp][lane >> 3][k] = m[k];
     }
     __syncthreads();
-    float scale[PAD];
+    if (threadIdx.x < kPackBricksX * PAD) {
+        const int j = threadIdx.x / PAD, k = threadIdx.x - j * PAD;
+        float a = 0.0f;
 #pragma unroll
-    for (int c = 0; c < PAD; ++c) {
-        float m = 0.0f;
-#pragma unroll
-        for (int w = 0; w < 16; ++w) m = fmaxf(m, s_max[w][c]);
-        scale[c] = m > 0.0f ? __fdiv_rn(m, 448.0f) : 1.0f;
+        for (int w = 0; w < 8; ++w) a = fmaxf(a, s_max[w][j][k]);
+        const float sc = a > 0.0f ? __fdiv_rn(a, 448.0f) : 1.0f;
+        s_scale[j][k] = sc;
+        if (bxi + j < p.bx)
+            p.scales[(((long long)bzi * p.by + byi) * p.bx + bxi + j) * PAD + k] = sc;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if (!in_xy) return;
+    float sc[PAD];
 #pragma unroll
-        for (int c = 0; c < PAD; ++c) p.scales[(long long)b * PAD + c] = scale[c];
+    for (int k = 0; k < PAD; ++k) sc[k] = s_scale[lane >> 3][k];
+    for (int zb = 0; zb < nzb; zb += ZB) {
+        float v[ZB][PAD];
+#pragma unroll
+        for (int u = 0; u < ZB; ++u)
+            if (zb + u < nzb) column_cell<PAD>(p, col, z0 + zb + u, v[u]);
+#pragma unroll
+        for (int u = 0; u < ZB; ++u) {
+            if (zb + u >= nzb) continue;
+            const int z = z0 + zb + u;
+            unsigned code[PAD];
+#pragma unroll
+            for (int k = 0; k < PAD; ++k)
+                code[k] = k < p.ncomp ? (unsigned)__nv_cvt_float_to_fp8(__fdiv_rn(v[u][k], sc[k]),
+                                                                        __NV_SATFINITE, __NV_E4M3)
+                                      : 0u;
+            unsigned char *o = p.rec + (((long long)z * p.py + y) * p.px + x) * PAD;
+            if constexpr (PAD == 1) {
+                *o = (unsigned char)code[0];
+            } else if constexpr (PAD == 2) {
+                *reinterpret_cast<unsigned short *>(o) = (unsigned short)(code[0] | (code[1] << 8));
+            } else {
+                unsigned w[PAD / 4];
+#pragma unroll
+                for (int q = 0; q < PAD / 4; ++q)
+                    w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
+                if constexpr (PAD == 4)
+                    *reinterpret_cast<unsigned *>(o) = w[0];
+                else
+                    *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+            }
+        }
     }
-    if (!inside) return;
-    const long long i = ((long long)z * p.py + y) * p.px + x;
-    unsigned char code[PAD];
-#pragma unroll
-    for (int c = 0; c < PAD; ++c)
-        code[c] = (unsigned char)__nv_cvt_float_to_fp8(__fdiv_rn(v[c], scale[c]), __NV_SATFINITE, __NV_E4M3);
-    unsigned char *o = const_cast<unsigned char *>(p.rec) + i * PAD;
-#pragma unroll
-    for (int c = 0; c < PAD; ++c) o[c] = code[c];
 }
 
 // ---------------------------------------------------------- render kernel

@@ -132,6 +132,11 @@ extern "C" int isaac_pack(const isaac_source *sources, int32_t n_sources, uint32
         q.sc = ks.sc;
         q.fdim = ks.fdim;
         q.guard = sources[s].guard;
+        for (int c = 0; c < ks.fdim; ++c) {
+            kp.slot_src[kp.ncomp] = kp.nsrc - 1;
+            kp.slot_comp[kp.ncomp] = c;
+            ++kp.ncomp;
+        }
     }
     kp.nx = (int)n[0];
     kp.ny = (int)n[1];

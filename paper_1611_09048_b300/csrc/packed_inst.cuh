@@ -1,6 +1,7 @@
 // packed_inst.cuh -- kernel table of the packed path for one storage format.
 // Included by packed_<format>.cu with ISAAC_DT and ISAAC_TABLE defined, so
 // the formats compile as separate translation units.
+#include "common.h"
 #include "packed.cuh"
 
 namespace isaac {
@@ -15,10 +16,11 @@ template <int DT, int PAD>
 static void launch_pack(const KPack &p, cudaStream_t st)
 {
     if constexpr (DT == ISAAC_E4M3) {
-        k_pack_e4m3<PAD><<<(unsigned)(p.bx * p.by * p.bz), 512, 0, st>>>(p);
+        const long long gx = (p.bx + kPackBricksX - 1) / kPackBricksX;
+        k_pack_e4m3<PAD><<<(unsigned)(gx * p.by * p.bz), 256, 0, st>>>(p);
     } else {
-        const long long total = (long long)p.px * p.py * p.pz;
-        const long long blocks = std::min<long long>((total + 255) / 256, 148LL * 16);
+        const long long rows = (long long)p.py * p.pz;   // a warp per row, 8 per block
+        const long long blocks = std::min<long long>((rows + 7) / 8, (long long)sm_count() * 16);
         k_pack<DT, PAD><<<(unsigned)blocks, 256, 0, st>>>(p);
     }
 }
