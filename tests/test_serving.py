@@ -184,16 +184,33 @@ def test_requests_on_two_streams_overlap_on_the_device(cuda_ok):
     """Two 1080p requests submitted together to a server with two streams and
     batches of one: they run as two batches on different streams whose
     device-clock intervals (CUDA events around each batch) overlap, and each
-    image is bitwise the one the request gets when it is served alone."""
+    image is bitwise the one the request gets when it is served alone.
+
+    "Together" means the second request is queued while the first is still on
+    the GPU (a few ms).  The submits are two host calls, so a pause of the
+    host thread between them (a garbage collection in a long test process)
+    can let the first batch finish first; the second then reuses its stream,
+    which is correct serving but not this case.  The collector is off across
+    the submits and the case gets up to three attempts."""
+    import gc
     sc = small_pic_scene(n=48, guard=2, width=64, height=64, seed=31, dist_factor=1.0)
     ds = isaac.DeviceScene(sc)
     reqs = []
     for k in range(2):
         mv, proj = synth.orbit_camera(sc.n, 1920, 1080, 0.4 + 1.3 * k, 0.2, dist_factor=0.9)
         reqs.append((np.asarray(mv, np.float64), np.asarray(proj, np.float64), 1920, 1080, None, None))
-    together, res = _serve(ds, reqs, [0, 1], True, n_streams=2, max_batch=1)
-    a, b = res[0], res[1]
-    assert a["batch_size"] == 1 and b["batch_size"] == 1 and a["stream"] != b["stream"]
+    for attempt in range(3):
+        gc.collect()
+        gc.disable()
+        try:
+            together, res = _serve(ds, reqs, [0, 1], True, n_streams=2, max_batch=1)
+        finally:
+            gc.enable()
+        a, b = res[0], res[1]
+        assert a["batch_size"] == 1 and b["batch_size"] == 1, (a, b)
+        if a["stream"] != b["stream"]:
+            break
+    assert a["stream"] != b["stream"], (a, b)
     assert 0.0 <= a["t_gpu_start"] < a["t_gpu_end"] and 0.0 <= b["t_gpu_start"] < b["t_gpu_end"]
     assert max(a["t_gpu_start"], b["t_gpu_start"]) < min(a["t_gpu_end"], b["t_gpu_end"]), (a, b)
     for i in range(2):
