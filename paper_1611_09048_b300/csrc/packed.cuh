@@ -588,12 +588,19 @@ template <int NACT, unsigned SIG, int DT, int PAD, int INTERP, int RL, bool LONG
 __global__ void __launch_bounds__(kMarchThreads, kMarchBlocksPerSM) k_raycast_packed(const __grid_constant__ KParams p)
 {
     __shared__ float4 s_lut[NACT * 256];
-    load_luts<NACT>(p, s_lut);
+    // the empty-group vote in single-source kernels only (as in k_raycast)
+    const bool zskip = load_luts<NACT>(p, s_lut);
     using Shader = PackedShader<NACT, SIG, DT, PAD, INTERP>;
-    if constexpr (LONG)
-        march_long<Shader>(p, s_lut);
-    else
-        march<NACT, Shader, RL>(p, s_lut);
+    if constexpr (LONG) {
+        if (NACT == 1 && zskip)
+            march_long<Shader, NACT == 1>(p, s_lut);
+        else
+            march_long<Shader, false>(p, s_lut);
+    } else if (NACT == 1 && zskip) {
+        march<NACT, Shader, RL, false, false, NACT == 1>(p, s_lut);
+    } else {
+        march<NACT, Shader, RL, false, false, false>(p, s_lut);
+    }
 }
 
 // ------------------------------------------------------------- dispatch
