@@ -912,8 +912,11 @@ __device__ __forceinline__ void march(const KParams &p, const float4 *s_lut,
 // same order as march_ray, so the pixel is bit-identical to the plain march.
 // A ray that terminates or ends is written and its slot refilled from the
 // list at the next step.  In-order compositing thus costs one lane per ray,
-// not every lane of a group.
-constexpr int kStreamRays = 2, kStreamU = 4, kStreamT = 32 * kStreamU / kStreamRays;
+// not every lane of a group, and a window with nothing to composite (ZSKIP)
+// costs none.  Since such windows are skipped, one ray per warp with 64-sample
+// windows (twice the warps in flight for the few long rays) is the fastest
+// shape: 2 rays x 64 samples and 1 ray x 128 samples measured slower.
+constexpr int kStreamRays = 1, kStreamU = 2, kStreamT = 32 * kStreamU / kStreamRays;
 
 template <class Shader, bool ZSKIP = false>
 __device__ __forceinline__ void march_long(const KParams &p, const float4 *s_lut)
