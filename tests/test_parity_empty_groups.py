@@ -97,3 +97,22 @@ def test_infinite_colour_at_zero_opacity_poisons_the_pixel(cuda_ok):
         assert np.array_equal(np.isnan(g32[..., 0])[keep], hit[keep])
         assert not g32[..., 1:].any()
         np.testing.assert_array_equal(gns[keep], ref["nsamp"][keep])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3"])
+def test_sparse_bubble_packed_matches_oracle_on_dequantised_copy(cuda_ok, fmt):
+    """The packed single-source kernels take the same vote: the sparse bubble
+    from its BF16 / E4M3 copy against the oracle run on the oracle's own
+    dequantised copy of the field (one-cell apron as guard cells)."""
+    import torch
+    sc = _bubble()
+    pv = isaac.DeviceScene(sc).pack(fmt)
+    vals, _ = oracle.lowp_copy(sc.sources[0], sc.n, fmt)
+    deq = dataclasses.replace(sc, sources=[synth.source_from_zyx(vals[..., 0], 1)])
+    ref = oracle.render(deq)
+    for lanes in (4, 16):
+        out, f32, ns = pv.render(want_f32=True, want_nsamp=True, lanes=lanes)
+        torch.cuda.synchronize()
+        rep = compare(f32.cpu().numpy(), out.cpu().numpy(), ns.cpu().numpy(), ref)
+        assert_parity(rep, 1e-3, f"sparse bubble {fmt}, {lanes} lanes per ray")
+        assert rep.hit > 5000
