@@ -66,6 +66,32 @@ def _serve(target, reqs, order, together, **cfg):
     return {i: o.numpy().copy() for i, o in outs.items()}, res
 
 
+def _serve_batched(target, sc, reqs, n_streams, max_batch):
+    """Serve ``reqs`` submitted together so that they are batched: first one
+    1920x1080 request per stream (a few ms each on the GPU), then ``reqs``,
+    which queue while the large ones render and are admitted max_batch at a
+    time as streams free up.  The submits are host calls, so a host pause
+    between them could still let the queue drain; the collector is off
+    across them and the case gets up to three attempts.  Returns the images
+    and results of ``reqs`` (the large requests are left out)."""
+    import gc
+    mv, proj = synth.orbit_camera(sc.n, 1920, 1080, 0.7, 0.25, dist_factor=0.8)
+    big = (np.asarray(mv, np.float64), np.asarray(proj, np.float64), 1920, 1080, None, None)
+    allr = [big] * n_streams + list(reqs)
+    order = list(range(len(allr)))
+    for attempt in range(3):
+        gc.collect()
+        gc.disable()
+        try:
+            outs, res = _serve(target, allr, order, True, n_streams=n_streams, max_batch=max_batch)
+        finally:
+            gc.enable()
+        mine = {i - n_streams: res[i] for i in range(n_streams, len(allr))}
+        if max(r["batch_size"] for r in mine.values()) > 1:
+            break
+    return {i - n_streams: outs[i] for i in range(n_streams, len(allr))}, mine
+
+
 def _direct(sc, req, packed=None):
     """The same request through isaac_render (or isaac_render_packed)."""
     import torch
@@ -106,7 +132,7 @@ def test_alone_equals_mix_zero_copy(cuda_ok, pic):
     reqs = _requests(pic)
     order = list(range(len(reqs)))
     alone, _ = _serve(ds, reqs, order, together=False, n_streams=2, max_batch=8)
-    mix, res = _serve(ds, reqs, order[::-1], together=True, n_streams=1, max_batch=8)
+    mix, res = _serve_batched(ds, pic, reqs, n_streams=1, max_batch=8)
     assert max(r["batch_size"] for r in res.values()) > 1
     for i in order:
         np.testing.assert_array_equal(alone[i], mix[i], err_msg=f"request {i}")
@@ -127,7 +153,7 @@ def test_alone_equals_mix_packed_bf16(cuda_ok, pic):
     reqs = _requests(pic, seed=5)
     order = list(range(len(reqs)))
     alone, _ = _serve(pv, reqs, order, together=False, n_streams=1, max_batch=4)
-    mix, res = _serve(pv, reqs, order, together=True, n_streams=3, max_batch=3)
+    mix, res = _serve_batched(pv, pic, reqs, n_streams=3, max_batch=3)
     assert max(r["batch_size"] for r in res.values()) > 1
     for i in order:
         np.testing.assert_array_equal(alone[i], mix[i], err_msg=f"request {i}")
@@ -216,3 +242,42 @@ def test_requests_on_two_streams_overlap_on_the_device(cuda_ok):
     for i in range(2):
         alone, _ = _serve(ds, reqs, [i], False, n_streams=2, max_batch=1)
         np.testing.assert_array_equal(together[i], alone[i])
+
+
+def test_host_side_faults(cuda_ok, pic):
+    """Faults injected on the host, none on the GPU: a poll that waits on an
+    empty server times out with no result; a steering update with a malformed
+    functor chain is refused at submit and leaves the queue as it was; a
+    server destroyed with requests still queued finishes them and returns
+    (their results are dropped), and a new server then serves normally."""
+    import time
+    ds = isaac.DeviceScene(pic)
+    mv, proj = synth.orbit_camera(pic.n, 64, 48, 0.3, 0.2)
+    with isaac.Server(ds, budget=8 << 20, n_streams=2, max_batch=4) as srv:
+        t0 = time.perf_counter()
+        assert srv.poll(wait=0.05) == []
+        assert 0.04 <= time.perf_counter() - t0 < 5.0
+        assert srv.outstanding() == 0
+        bad = [list(c) for c in pic.chains]
+        bad[0] = [("pow", (0.5, 1.0))]                     # pow takes one argument
+        with pytest.raises(isaac.IsaacError) as e:
+            srv.submit(mv, proj, 64, 48, _pinned(64, 48), chains=bad)
+        assert e.value.code == isaac.EINVAL
+        assert srv.outstanding() == 0
+        out = _pinned(64, 48)
+        srv.submit(mv, proj, 64, 48, out)
+        (r,) = srv.drain()
+        assert r["status"] == 0
+    srv = isaac.Server(ds, budget=8 << 20, n_streams=1, max_batch=1)
+    outs = [_pinned(64, 48) for _ in range(6)]
+    for o in outs:
+        srv.submit(mv, proj, 64, 48, o)
+    srv.close()                                              # six queued, none polled
+    with isaac.Server(ds, budget=8 << 20, n_streams=2, max_batch=4) as srv2:
+        again = _pinned(64, 48)
+        srv2.submit(mv, proj, 64, 48, again)
+        (r,) = srv2.drain()
+        assert r["status"] == 0
+    direct, _ = _direct(pic, (mv, proj, 64, 48, None, None))
+    np.testing.assert_array_equal(again.numpy(), direct)
+    np.testing.assert_array_equal(out.numpy(), direct)
