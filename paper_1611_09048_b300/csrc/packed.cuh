@@ -279,9 +279,9 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ KPack p)
             if ((p.px & 1) == 0) {
                 // 2-byte records, rows of an even length: each lane converts
                 // the cell pairs (x, x + 1), x even, and stores a pair as one
-                // 4-byte word (rows start 4-byte aligned), 8 pairs' loads in
+                // 4-byte word (rows start 4-byte aligned), 9 pairs' loads in
                 // flight per lane
-                constexpr int U2 = 8;
+                constexpr int U2 = 9;
                 unsigned *rec32 = reinterpret_cast<unsigned *>(p.rec);
                 for (int xb = 2 * lane; xb < p.px; xb += 64 * U2) {
                     float v[U2][2];
