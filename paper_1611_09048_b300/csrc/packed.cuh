@@ -361,20 +361,65 @@ __device__ __forceinline__ void column_cell(const KPack &p, const PackColumn<PAD
         v[k] = k < p.ncomp ? __ldg(c.p[k] + (long long)pack_axis(z, p.nz, c.guard[k]) * c.sz[k]) : 0.0f;
 }
 
+// v / s rounded once to float32 (round to nearest even), given y = RN(1/s)
+// and s in [2^-60, 2^60], by Markstein's method (P. Markstein, IBM J. Res.
+// Dev. 34(1), 1990): q0 = RN(v y) lies within 1.5 ulp of v / s; one step
+// with the fused multiply-add residual v - s q0 makes q1 faithful (within an
+// ulp); the residual of a faithful quotient is exact, and Markstein's theorem
+// makes RN(q1 + (v - s q1) y) the correctly rounded quotient.  The range of s
+// keeps that residual in the normal range for every v with |v / s| >= 2^-11;
+// smaller quotients stay below 2^-10, half of E4M3's smallest subnormal, so
+// they quantise to a zero of v's sign either way, as the correctly rounded
+// quotient does.  The residual is formed negated, s q - v, and subtracted:
+// for v = -0 that keeps the quotient -0 (q + (+0) y would round to +0).
+__device__ __forceinline__ float quot_rn(float v, float s, float y)
+{
+    const float q0 = v * y;
+    const float q1 = fmaf(-fmaf(s, q0, -v), y, q0);
+    return fmaf(-fmaf(s, q1, -v), y, q1);
+}
+
+template <int PAD, bool FAST>
+__device__ __forceinline__ void store_e4m3(const KPack &p, const float (&v)[PAD], const float (&sc)[PAD],
+                                           const float (&rc)[PAD], unsigned char *o)
+{
+    unsigned code[PAD];
+#pragma unroll
+    for (int k = 0; k < PAD; ++k) {
+        const float q = FAST ? quot_rn(v[k], sc[k], rc[k]) : __fdiv_rn(v[k], sc[k]);
+        code[k] = k < p.ncomp ? (unsigned)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3) : 0u;
+    }
+    if constexpr (PAD == 1) {
+        *o = (unsigned char)code[0];
+    } else if constexpr (PAD == 2) {
+        *reinterpret_cast<unsigned short *>(o) = (unsigned short)(code[0] | (code[1] << 8));
+    } else {
+        unsigned w[PAD / 4];
+#pragma unroll
+        for (int q = 0; q < PAD / 4; ++q)
+            w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
+        if constexpr (PAD == 4)
+            *reinterpret_cast<unsigned *>(o) = w[0];
+        else
+            *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+    }
+}
+
 // E4M3: a 256-thread block per 4 x 1 x 1 bricks: lane = x (8 lanes per brick),
-// warp = y, each thread down its column through the brick's 8 z layers, ZB
-// layers' loads in flight at a time.  First pass: per thread the absmax of
-// each slot over its 8 cells, reduced over the brick's 8 lanes by shuffles and
-// over the 8 warps in shared memory; scale = absmax / 448 (1 for an all-zero
-// brick).  Second pass: the same cells again (now in L1/L2), code =
-// E4M3_sat(v / scale) with v / scale rounded once to float32, one store of the
-// cell's PAD codes.
+// warp = y, each thread down its column through the brick's 8 z layers.  The
+// column's cells are read once, all their loads in flight together, and stay
+// in registers: per thread the absmax of each slot over its cells, reduced
+// over the brick's 8 lanes by shuffles and over the 8 warps in shared memory;
+// scale = absmax / 448 (1 for an all-zero brick); then, from the registers,
+// code = E4M3_sat(v / scale) with v / scale rounded once to float32 (by
+// quot_rn when every scale of the block lies in [2^-60, 2^60], else by the
+// division), one store of the cell's PAD codes.
 template <int PAD>
 __global__ void __launch_bounds__(256) k_pack_e4m3(const __grid_constant__ KPack p)
 {
-    constexpr int ZB = PAD <= 2 ? 8 : (PAD == 4 ? 4 : 2);
     __shared__ float s_max[8][kPackBricksX][PAD];
     __shared__ float s_scale[kPackBricksX][PAD];
+    __shared__ float s_rcp[kPackBricksX][PAD];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gx = (p.bx + kPackBricksX - 1) / kPackBricksX;
     const int b = blockIdx.x;
@@ -384,22 +429,20 @@ __global__ void __launch_bounds__(256) k_pack_e4m3(const __grid_constant__ KPack
     const int z0 = bzi * 8, nzb = min(8, p.pz - z0);
     PackColumn<PAD> col;
     pack_column<PAD>(p, in_xy ? x : 0, in_xy ? y : 0, col);
+    float v[8][PAD];
     float m[PAD];
 #pragma unroll
     for (int k = 0; k < PAD; ++k) m[k] = 0.0f;
     if (in_xy) {
-        for (int zb = 0; zb < nzb; zb += ZB) {
-            float v[ZB][PAD];
 #pragma unroll
-            for (int u = 0; u < ZB; ++u)
-                if (zb + u < nzb) column_cell<PAD>(p, col, z0 + zb + u, v[u]);
+        for (int u = 0; u < 8; ++u)
+            if (u < nzb) column_cell<PAD>(p, col, z0 + u, v[u]);
 #pragma unroll
-            for (int u = 0; u < ZB; ++u)
-                if (zb + u < nzb) {
+        for (int u = 0; u < 8; ++u)
+            if (u < nzb) {
 #pragma unroll
-                    for (int k = 0; k < PAD; ++k) m[k] = fmaxf(m[k], fabsf(v[u][k]));
-                }
-        }
+                for (int k = 0; k < PAD; ++k) m[k] = fmaxf(m[k], fabsf(v[u][k]));
+            }
     }
 #pragma unroll
     for (int k = 0; k < PAD; ++k) {
@@ -408,52 +451,37 @@ __global__ void __launch_bounds__(256) k_pack_e4m3(const __grid_constant__ KPack
         if ((lane & 7) == 0) s_max[warp][lane >> 3][k] = m[k];
     }
     __syncthreads();
+    bool in_range = true;
     if (threadIdx.x < kPackBricksX * PAD) {
         const int j = threadIdx.x / PAD, k = threadIdx.x - j * PAD;
         float a = 0.0f;
 #pragma unroll
         for (int w = 0; w < 8; ++w) a = fmaxf(a, s_max[w][j][k]);
         const float sc = a > 0.0f ? __fdiv_rn(a, 448.0f) : 1.0f;
+        in_range = sc >= 0x1p-60f && sc <= 0x1p60f;
         s_scale[j][k] = sc;
+        s_rcp[j][k] = in_range ? __frcp_rn(sc) : 0.0f;
         if (bxi + j < p.bx)
             p.scales[(((long long)bzi * p.by + byi) * p.bx + bxi + j) * PAD + k] = sc;
     }
-    __syncthreads();
+    const bool fast = __syncthreads_and(in_range) != 0;
     if (!in_xy) return;
-    float sc[PAD];
+    float sc[PAD], rc[PAD];
 #pragma unroll
-    for (int k = 0; k < PAD; ++k) sc[k] = s_scale[lane >> 3][k];
-    for (int zb = 0; zb < nzb; zb += ZB) {
-        float v[ZB][PAD];
+    for (int k = 0; k < PAD; ++k) {
+        sc[k] = s_scale[lane >> 3][k];
+        rc[k] = s_rcp[lane >> 3][k];
+    }
+    unsigned char *o = p.rec + (((long long)z0 * p.py + y) * p.px + x) * PAD;
+    const long long zstep = (long long)p.py * p.px * PAD;
+    if (fast) {
 #pragma unroll
-        for (int u = 0; u < ZB; ++u)
-            if (zb + u < nzb) column_cell<PAD>(p, col, z0 + zb + u, v[u]);
+        for (int u = 0; u < 8; ++u)
+            if (u < nzb) store_e4m3<PAD, true>(p, v[u], sc, rc, o + u * zstep);
+    } else {
 #pragma unroll
-        for (int u = 0; u < ZB; ++u) {
-            if (zb + u >= nzb) continue;
-            const int z = z0 + zb + u;
-            unsigned code[PAD];
-#pragma unroll
-            for (int k = 0; k < PAD; ++k)
-                code[k] = k < p.ncomp ? (unsigned)__nv_cvt_float_to_fp8(__fdiv_rn(v[u][k], sc[k]),
-                                                                        __NV_SATFINITE, __NV_E4M3)
-                                      : 0u;
-            unsigned char *o = p.rec + (((long long)z * p.py + y) * p.px + x) * PAD;
-            if constexpr (PAD == 1) {
-                *o = (unsigned char)code[0];
-            } else if constexpr (PAD == 2) {
-                *reinterpret_cast<unsigned short *>(o) = (unsigned short)(code[0] | (code[1] << 8));
-            } else {
-                unsigned w[PAD / 4];
-#pragma unroll
-                for (int q = 0; q < PAD / 4; ++q)
-                    w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
-                if constexpr (PAD == 4)
-                    *reinterpret_cast<unsigned *>(o) = w[0];
-                else
-                    *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
-            }
-        }
+        for (int u = 0; u < 8; ++u)
+            if (u < nzb) store_e4m3<PAD, false>(p, v[u], sc, rc, o + u * zstep);
     }
 }
 

@@ -168,3 +168,75 @@ def test_pack_bubble512_sampled(cuda_ok):
         got = codes[sel].cpu().view(torch.float8_e4m3fn).float().numpy().reshape(8, 8, 8)
         got = got * scales[bz, by, bx]
         np.testing.assert_array_equal(got.astype(np.float32), want[..., 0])
+
+
+def _e4m3_rounding_points():
+    """The positive E4M3 values up to 416 and the midpoints between
+    neighbours (subnormals k 2^-9, normals (1 + j/8) 2^e, e = -6..8), plus
+    2^-11 and 2^-12 below the smallest midpoint; all exact in float32."""
+    vals = [k * 2.0 ** -9 for k in range(8)]
+    vals += [(1 + j / 8) * 2.0 ** e for e in range(-6, 9) for j in range(8)]
+    vals = sorted(v for v in vals if v <= 448.0)
+    mids = [(a + b) / 2 for a, b in zip(vals[:-1], vals[1:])]
+    return [v for v in vals + mids + [2.0 ** -11, 2.0 ** -12] if v <= 432.0]
+
+
+def test_e4m3_quotients_at_rounding_points(cuda_ok):
+    """E4M3 codes where v / scale falls on, or one or two float32 ulps from,
+    a rounding point of the format (its values and the midpoints between
+    them, where ties go to even), over scales from 2^-61 to 2^61, with signed
+    zeros, the smallest subnormal float and an all-zero brick.  A block of
+    four bricks whose scales all lie in [2^-60, 2^60] takes the reciprocal
+    and residual quotient, the others the division; both must give the
+    oracle's float32 division and rounding bit for bit, signs of zero
+    included."""
+    import torch
+    n = (30, 14, 14)                     # packed box 32 x 16 x 16: 4 x 2 x 2 bricks
+    P = (n[0] + 2, n[1] + 2, n[2] + 2)
+    targets = {                          # (bz, by): scales of the row's 4 bricks
+        (0, 0): [1 / 448, 2.0 ** -20, 2.0 ** -59.5, 2.0 ** 59.5],
+        (0, 1): [3.7e-3, 0.37, 1234.5, 2.0 ** -59.99],
+        (1, 0): [2.0 ** -61, 1.0, 2.0 ** 61, 5e-7],      # two scales out of range
+        (1, 1): [7.77e-12, 2.0 ** 40, 9.1e9, 0.0],        # 0: an all-zero brick
+    }
+    pts = np.array(_e4m3_rounding_points(), np.float32)
+    rng = np.random.default_rng(5)
+    Q = np.zeros((P[2], P[1], P[0]), np.float32)         # packed (z, y, x)
+    for (bz, by), row in targets.items():
+        for bx, t in enumerate(row):
+            blk = np.zeros((8, 8, 8), np.float32)
+            if t == 0.0:
+                blk[:] = np.where(rng.random((8, 8, 8)) < 0.5, np.float32(-0.0), np.float32(0.0))
+            else:
+                A = np.float32(t * 448.0)
+                s = np.float32(A) / np.float32(448.0)
+                base = pts * s
+                cand = [base]
+                for direction in (np.float32(np.inf), np.float32(-np.inf)):
+                    c = base
+                    for _ in range(2):
+                        c = np.nextafter(c, direction)
+                        cand.append(c)
+                cand = np.concatenate(cand)
+                cand = np.concatenate([cand, -cand, np.float32([0.0, -0.0, 1e-45, -1e-45])])
+                cand = cand[np.abs(cand) <= A]
+                blk.reshape(-1)[:] = rng.choice(cand, 512, replace=len(cand) < 512)
+                blk[3, 3, 3] = A                          # the brick's absmax
+            Q[bz * 8: bz * 8 + 8, by * 8: by * 8 + 8, bx * 8: bx * 8 + 8] = blk
+    field = np.ascontiguousarray(Q[1:-1, 1:-1, 1:-1])   # cells [-1, n] of the source
+    src = synth.source_from_zyx(field, 0)
+    mv, proj = synth.orbit_camera(n, 32, 32, 0.4, 0.3, dist_factor=1.0)
+    sc = synth.Scene(n=n, sources=[src], chains=[[]], luts=np.zeros((1, 256, 4), np.float32),
+                     weights=np.ones(1, np.float32), modelview=mv, projection=proj,
+                     width=32, height=32)
+    pv = isaac.DeviceScene(sc).pack("e4m3")
+    torch.cuda.synchronize()
+    got, got_scales = _decode(pv, "e4m3", n)
+    want, want_scales = oracle.lowp_copy(src, n, "e4m3")
+    np.testing.assert_array_equal(got_scales, want_scales)
+    full = np.repeat(np.repeat(np.repeat(got_scales, 8, 0), 8, 1), 8, 2)
+    deq = (got * full).astype(np.float32)
+    np.testing.assert_array_equal(deq, want)
+    np.testing.assert_array_equal(np.signbit(deq), np.signbit(want))
+    # the cases are really there: codes on both sides of many midpoints
+    assert len(np.unique(got)) > 200
