@@ -434,9 +434,21 @@ __global__ void __launch_bounds__(256) k_pack_e4m3(const __grid_constant__ KPack
 #pragma unroll
     for (int k = 0; k < PAD; ++k) m[k] = 0.0f;
     if (in_xy) {
+        if (z0 >= 1 && z0 + 8 <= p.nz) {
+            // a brick inside the source along z: source layer z - 1 for every
+            // slot, guards or not, so each slot's address advances by its z
+            // stride from one cell to the next
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (u < nzb) column_cell<PAD>(p, col, z0 + u, v[u]);
+            for (int k = 0; k < PAD; ++k) {
+                const float *a = col.p[k] + (long long)(z0 - 1) * col.sz[k];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u][k] = k < p.ncomp ? __ldg(a + u * col.sz[k]) : 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < nzb) column_cell<PAD>(p, col, z0 + u, v[u]);
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
             if (u < nzb) {
