@@ -704,6 +704,9 @@ __device__ __forceinline__ void write_pixel(const KParams &p, int pix, float C0,
 // at most 2^30, so pixel indices fit an int).
 static __global__ void k_fill_background(const __grid_constant__ KParams p)
 {
+    // the ray setup that follows may start now: it computes its rays while
+    // this fill runs and waits for the fill's writes before its own
+    asm volatile("griddepcontrol.launch_dependents;");
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.ctr) {
         p.ctr->n_rays = 0u;
         p.ctr->next = 0u;
@@ -735,6 +738,10 @@ static __global__ void __launch_bounds__(128) k_setup_rays(const __grid_constant
     r.nsteps = 0;
     float tf = 0.0f;
     if (inside) r = setup_ray(p, px, py, &tf);
+    // launched as a programmatic dependent of the background fill: the ray
+    // arithmetic above overlaps the fill; the counters the fill resets and
+    // every write below wait for its completion
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const bool hit = inside && r.nsteps > 0;
     const unsigned m = __ballot_sync(0xffffffffu, hit);
     unsigned base = 0;

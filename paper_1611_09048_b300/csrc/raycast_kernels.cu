@@ -1,5 +1,6 @@
 // raycast_kernels.cu -- instantiations of the zero-copy frame kernel and the
 // table the host dispatches from.
+#include "common.h"
 #include "kernel_table.h"
 #include "raycast.cuh"
 
@@ -57,16 +58,30 @@ extern const ZcEntry *const k_zc_entries = k_entries;
 extern const int k_n_zc_entries = (int)(sizeof(k_entries) / sizeof(k_entries[0]));
 
 // The setup, background and copy kernels are launched from this translation unit.
+// Two fill blocks per SM leave room for the setup blocks that start beside them.
 void launch_fill(const KParams &p, cudaStream_t st)
 {
-    const int blocks = std::max(1, std::min(p.H, 148 * 8));
+    const int blocks = std::max(1, std::min(p.H, sm_count() * 2));
     k_fill_background<<<blocks, 256, 0, st>>>(p);
 }
 
+// The setup is a programmatic dependent launch of the fill before it in the
+// stream: its blocks may start once every fill block has started, and wait in
+// the kernel (griddepcontrol.wait) for the fill's completion before they write.
 void launch_setup(const KParams &p, cudaStream_t st)
 {
     const int tiles = ((p.rx1 - p.rx0 + 15) / 16) * ((p.ry1 - p.ry0 + 7) / 8);
-    k_setup_rays<<<tiles, 128, 0, st>>>(p);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)tiles);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_setup_rays, p);
 }
 
 void launch_copy_rays(const KParams &p, RayRec *out, long long cap, int *count, cudaStream_t st)
