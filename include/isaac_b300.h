@@ -207,7 +207,8 @@ int isaac_render(const isaac_source *sources, const isaac_chain *chains, int32_t
  *   ISAAC_F32   float32;
  *   ISAAC_BF16  bfloat16, round to nearest even;
  *   ISAAC_F16   IEEE binary16, round to nearest even;
- *   ISAAC_E4M3  FP8 E4M3 codes of value / scale, round to nearest even,
+ *   ISAAC_E4M3  FP8 E4M3 codes of value / scale (the quotient correctly
+ *               rounded to float32, then to E4M3 with ties to even),
  *               saturating at +-448, with one float32 scale per 8^3 brick of
  *               the [-1, n]^3 box (bricks counted from cell -1) and component:
  *               scale = absmax / 448 over the brick, 1 for an all-zero brick.
