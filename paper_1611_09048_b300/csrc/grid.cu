@@ -488,10 +488,20 @@ static __global__ void __launch_bounds__(256) k_grid_reduce_tiled(const __grid_c
     const float *base = p.cols + (long long)k * plane;
     // padded column xx = x + 1: the tile's columns x in [64 tx - 1, 64 tx + 64]
     const int x0 = tx * TM * CELL, y0 = ty * TM * CELL;
-    for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
-        const int r = i / R, c = i - r * R;
+    // every thread's NL loads issued before any is stored (the column maxima
+    // sit in L2: the stage is bound by load latency)
+    constexpr int NL = (R * R + 255) / 256;
+    float v[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+        const int i = threadIdx.x + 256 * u, r = i / R, c = i - r * R;
         const int xx = x0 + c, yy = y0 + r;
-        s_col[r][c] = (xx < p.W && yy < p.H) ? __ldg(base + (long long)yy * p.W + xx) : 0.0f;
+        v[u] = (i < R * R && xx < p.W && yy < p.H) ? __ldg(base + (long long)yy * p.W + xx) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+        const int i = threadIdx.x + 256 * u, r = i / R, c = i - r * R;
+        if (i < R * R) s_col[r][c] = v[u];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < R * TM; i += blockDim.x) {
