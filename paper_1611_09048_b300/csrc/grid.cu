@@ -680,20 +680,22 @@ static __global__ void __launch_bounds__(256) k_range_reduce(const __grid_consta
         float2 r[FD];
 #pragma unroll
         for (int c = 0; c < FD; ++c) r[c] = make_float2(inf, -inf);
-        // lanes along x, 4 rows' loads issued together (L2 latency bound)
+        // lanes along x, 6 rows' loads issued together (L2 latency bound; a
+        // 16-cell macro cell spans 18 rows)
+        constexpr int Q = 6;
         for (int x0 = xs; x0 <= xe; x0 += 32) {
             const int xx = x0 + lane;
-            for (int y0 = ys; y0 <= ye; y0 += 4) {
-                float2 v[4][FD];
+            for (int y0 = ys; y0 <= ye; y0 += Q) {
+                float2 v[Q][FD];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < Q; ++q)
 #pragma unroll
                     for (int c = 0; c < FD; ++c)
                         v[q][c] = (xx <= xe && y0 + q <= ye)
                                       ? __ldg(base + ((long long)(y0 + q) * p.W + xx) * FD + c)
                                       : make_float2(inf, -inf);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < Q; ++q)
 #pragma unroll
                     for (int c = 0; c < FD; ++c) r[c] = range_join(r[c], v[q][c]);
             }
