@@ -20,26 +20,30 @@ struct KCopy {
 
 constexpr int kCopyThreads = 256, kCopyUnroll = 8;
 
-// One block per (y, z) row of the copied region at a time (persistent, rows
-// strided by the grid).  A row is (nx+2g)*fdim contiguous destination
-// elements; each thread issues up to kCopyUnroll strided reads before its
-// writes, so a block keeps 8 KB of loads in flight.  FD = fdim (1..4), so the
-// element -> (cell, component) split is a division by a constant.
+// One warp per (y, z) row of the copied region at a time (rows strided over
+// every warp of the grid), its lanes along the row: a row is (nx+2g)*fdim
+// contiguous destination elements, and each lane issues up to kCopyUnroll
+// strided reads (32 elements apart) before its writes, so even the short
+// rows of a scalar source keep 8 loads per lane in flight.  FD = fdim (1..4),
+// so the element -> (cell, component) split is a division by a constant.
 template <int FD>
 static __global__ void __launch_bounds__(kCopyThreads) k_copy_source(const __grid_constant__ KCopy p)
 {
     const int X = p.nx + 2 * p.g, Y = p.ny + 2 * p.g, Z = p.nz + 2 * p.g;
     const int row_len = X * FD;
     const long long rows = (long long)Y * Z;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (kCopyThreads / 32);
+    for (long long row = blockIdx.x * (long long)(kCopyThreads / 32) + (threadIdx.x >> 5); row < rows;
+         row += nwarps) {
         const int y = (int)(row % Y) - p.g, z = (int)(row / Y) - p.g;
         const float *srow = p.src + (long long)y * p.sy + (long long)z * p.sz;
         float *drow = p.dst + row * row_len;
-        for (int i0 = 0; i0 < row_len; i0 += kCopyThreads * kCopyUnroll) {
+        for (int i0 = lane; i0 < row_len; i0 += 32 * kCopyUnroll) {
             float v[kCopyUnroll];
 #pragma unroll
             for (int u = 0; u < kCopyUnroll; ++u) {
-                const int i = i0 + u * kCopyThreads + threadIdx.x;
+                const int i = i0 + 32 * u;
                 if (i < row_len) {
                     const int x = i / FD - p.g, c = i - (i / FD) * FD;
                     v[u] = __ldg(srow + (long long)x * p.sx + (long long)c * p.sc);
@@ -47,7 +51,7 @@ static __global__ void __launch_bounds__(kCopyThreads) k_copy_source(const __gri
             }
 #pragma unroll
             for (int u = 0; u < kCopyUnroll; ++u) {
-                const int i = i0 + u * kCopyThreads + threadIdx.x;
+                const int i = i0 + 32 * u;
                 if (i < row_len) drow[i] = v[u];
             }
         }
@@ -101,7 +105,8 @@ extern "C" int isaac_copy_source(const isaac_source *src, const int64_t n[3], vo
     p.dst = static_cast<float *>(dst);
     if ((long long)X * p.fdim > 0x7fffffffLL) return fail(ISAAC_ENOTSUP, "a row of the copy is too long");
     const long long rows = Y * Z;
-    const unsigned blocks = (unsigned)std::max(1LL, std::min(rows, (long long)sm_count() * 8));
+    const long long wpb = kCopyThreads / 32;   // a warp per row
+    const unsigned blocks = (unsigned)std::max(1LL, std::min((rows + wpb - 1) / wpb, (long long)sm_count() * 8));
     const cudaStream_t st = (cudaStream_t)stream;
     switch (p.fdim) {
     case 1: k_copy_source<1><<<blocks, kCopyThreads, 0, st>>>(p); break;
