@@ -224,6 +224,20 @@ __device__ __forceinline__ unsigned short to16(float v, int dt)
                             : __half_as_ushort(__float2half_rn(v));
 }
 
+// Two values rounded to 16 bits (nearest even) in one 4-byte word, lo in the
+// low half: one paired conversion instead of two and a shift.
+template <int DT>
+__device__ __forceinline__ unsigned pack16x2(float lo, float hi)
+{
+    if constexpr (DT == ISAAC_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+}
+
 // Record i of the copy in one store as wide as the record (2 to 32 bytes;
 // records are aligned to their size: the copy starts 16-byte aligned).
 template <int DT, int PAD>
@@ -241,16 +255,13 @@ __device__ __forceinline__ void store_record(unsigned char *rec, long long i, co
                 reinterpret_cast<float4 *>(o)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
     } else {
-        unsigned short h[PAD];
-#pragma unroll
-        for (int c = 0; c < PAD; ++c) h[c] = to16(v[c], DT);
         unsigned short *o = reinterpret_cast<unsigned short *>(rec) + i * PAD;
         if constexpr (PAD == 1) {
-            o[0] = h[0];
+            o[0] = to16(v[0], DT);
         } else {
             unsigned w[PAD / 2];
 #pragma unroll
-            for (int c = 0; c < PAD / 2; ++c) w[c] = (unsigned)h[2 * c] | ((unsigned)h[2 * c + 1] << 16);
+            for (int c = 0; c < PAD / 2; ++c) w[c] = pack16x2<DT>(v[2 * c], v[2 * c + 1]);
             if constexpr (PAD == 2)
                 *reinterpret_cast<unsigned *>(o) = w[0];
             else if constexpr (PAD == 4)
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ KPack p)
                     for (int u = 0; u < U2; ++u) {
                         const int x = xb + 64 * u;
                         if (x < p.px)
-                            rec32[(i0 + x) >> 1] = (unsigned)to16(v[u][0], DT) | ((unsigned)to16(v[u][1], DT) << 16);
+                            rec32[(i0 + x) >> 1] = pack16x2<DT>(v[u][0], v[u][1]);
                     }
                 }
                 continue;
