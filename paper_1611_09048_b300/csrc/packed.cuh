@@ -394,25 +394,26 @@ template <int PAD, bool FAST>
 __device__ __forceinline__ void store_e4m3(const KPack &p, const float (&v)[PAD], const float (&sc)[PAD],
                                            const float (&rc)[PAD], unsigned char *o)
 {
-    unsigned code[PAD];
+    // quotients of unused slots are 0, which converts to the code 0
+    float q[PAD];
 #pragma unroll
-    for (int k = 0; k < PAD; ++k) {
-        const float q = FAST ? quot_rn(v[k], sc[k], rc[k]) : __fdiv_rn(v[k], sc[k]);
-        code[k] = k < p.ncomp ? (unsigned)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3) : 0u;
-    }
+    for (int k = 0; k < PAD; ++k)
+        q[k] = k < p.ncomp ? (FAST ? quot_rn(v[k], sc[k], rc[k]) : __fdiv_rn(v[k], sc[k])) : 0.0f;
     if constexpr (PAD == 1) {
-        *o = (unsigned char)code[0];
-    } else if constexpr (PAD == 2) {
-        *reinterpret_cast<unsigned short *>(o) = (unsigned short)(code[0] | (code[1] << 8));
+        *o = (unsigned char)__nv_cvt_float_to_fp8(q[0], __NV_SATFINITE, __NV_E4M3);
     } else {
-        unsigned w[PAD / 4];
+        // slots 2c and 2c + 1 in one paired conversion (2c in the low byte)
+        unsigned h[PAD / 2];
 #pragma unroll
-        for (int q = 0; q < PAD / 4; ++q)
-            w[q] = code[4 * q] | (code[4 * q + 1] << 8) | (code[4 * q + 2] << 16) | (code[4 * q + 3] << 24);
-        if constexpr (PAD == 4)
-            *reinterpret_cast<unsigned *>(o) = w[0];
+        for (int c = 0; c < PAD / 2; ++c)
+            h[c] = (unsigned)__nv_cvt_float2_to_fp8x2(make_float2(q[2 * c], q[2 * c + 1]), __NV_SATFINITE,
+                                                      __NV_E4M3);
+        if constexpr (PAD == 2)
+            *reinterpret_cast<unsigned short *>(o) = (unsigned short)h[0];
+        else if constexpr (PAD == 4)
+            *reinterpret_cast<unsigned *>(o) = h[0] | (h[1] << 16);
         else
-            *reinterpret_cast<uint2 *>(o) = make_uint2(w[0], w[1]);
+            *reinterpret_cast<uint2 *>(o) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
     }
 }
 
